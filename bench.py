@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Benchmark of the preconditioned LSMR hot path on one GB300.
+
+Workload (default): the single large sparse problem -- A is 2,000,000 x
+1,000,000 with 8 random N(0,1) nonzeros per row plus a +-4 entry on a hidden
+n-row subset (seed 1), b = A x_true + 1e-3 noise -- preconditioned by the
+row-splitting ILUP(p=10, tau=1e-2, mu=1) with the CG(2) correction.
+
+One step = one preconditioned LSMR iteration (A and A^T products, the full
+preconditioner application, the scalar recurrences and vector updates).
+`value` = iterations per second over K device-timed steps (CUDA events on the
+library's stream, inputs resident in HBM, working set ~1.5 GB >> 129 MB L2).
+`e2e` = the same metric through rlsq_solve with host buffers (b in, x out).
+Also reported: time to ||A^T r|| / (||A|| ||r||) < 1e-8 in float64 and with
+the float32 apply, the per-kernel-class breakdown, the roofline of the
+dominant kernel class against the measured HBM copy bandwidth, and the CPU
+oracle timed on a bounded sample.
+
+`--impl reference` times the CPU oracle alone on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FACTOR = dict(p=10, tau=1e-2, mu=1.0, small=1e-10, correction=2, cg_steps=2)
+WORKLOAD = ("sparse LS m=2,000,000 n=1,000,000, 8 N(0,1) nnz/row + hidden +-4 diagonal (seed 1); "
+            "ILUP(p=10, tau=1e-2, mu=1) row split, CG(2) correction; LSMR, atol 1e-8")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
+    ap.add_argument("--cpu-scale", type=float, default=0.1, help="oracle sample size")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(cpu_scale: float, full_nnz: int, iters_target_s: float = 12.0):
+    """The oracle as it stands (single thread) on the same recipe at a smaller
+    size; iterations/s scaled to the full workload by the nonzero ratio."""
+    import numpy as np
+
+    import oracle
+    from paper_2603_28642_gb300 import synth
+
+    prob = synth.config_problem(1, scale=cpu_scale)
+    f = oracle.Factor(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, p=FACTOR["p"],
+                      tau=FACTOR["tau"], mu=FACTOR["mu"], small=FACTOR["small"])
+    f.set_correction(oracle.CG, FACTOR["cg_steps"])
+    anorm = oracle.norm2(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals)
+    # calibrate, then time a run of ~iters_target_s seconds
+    t0 = time.perf_counter()
+    oracle.lsmr(f, prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, prob.b, anorm=anorm,
+                atol=0.0, maxit=2)
+    per = (time.perf_counter() - t0) / 3.0
+    its = max(3, int(iters_target_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    r = oracle.lsmr(f, prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, prob.b, anorm=anorm,
+                    atol=0.0, maxit=its)
+    dt = time.perf_counter() - t0
+    # r.its iterations plus one stopping check per iterate
+    its_per_s_sample = r.its / dt
+    factor = prob.nnz / full_nnz
+    del np
+    return {
+        "value": its_per_s_sample * factor,
+        "unit": "iter/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"config-1 recipe at scale {cpu_scale} (m={prob.m:,}, n={prob.n:,}, "
+                   f"nnz={prob.nnz:,}); {r.its} LSMR+CG(2) iterations in {dt:.1f}s on 1 of "
+                   f"{os.cpu_count()} host cores; iter/s scaled by nnz ratio {factor:.4f}"),
+    }
+
+
+def full_nnz_estimate(scale):
+    # nnz of the full workload (computed once, cheap relative to the factor)
+    from paper_2603_28642_gb300 import synth
+
+    return synth.config_problem(1, scale=scale).nnz
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    full = full_nnz_estimate(args.scale)
+    steps = []
+    for _ in range(max(1, args.steps)):
+        steps.append(cpu_oracle_sample(args.cpu_scale, full, iters_target_s=3.0))
+        if len(steps) >= 3:
+            break
+    v = statistics.median(s["value"] for s in steps)
+    cb = dict(steps[0])
+    cb["value"] = v
+    out = {
+        "impl": "reference", "metric": "preconditioned LSMR iterations/s", "value": v,
+        "unit": "iter/s", "n_gpus": args.gpus, "steps": len(steps), "warmup": 0,
+        "ms_per_step": 1000.0 / v if v else None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scale": args.scale},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2603_28642_gb300 import binding as B
+    from paper_2603_28642_gb300 import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    B.load()
+
+    # the single-problem path does not shard: every rank runs its own replica
+    prob = synth.config_problem(1, scale=args.scale)
+    P = B.Problem.from_problem(prob)
+    finfo = P.factor(**FACTOR, precision=B.PREC_FP64, autotune=1)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clk = Clocks(local)
+    prof = P.profile(prob.b, warmup=max(3, args.warmup), iters=args.steps)
+    clocks = clk.stop()
+    barrier()
+    total_ms = prof["total_ms"]
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # end to end through the public call with host buffers (b in, x out)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_res = P.solve(prob.b, atol=0.0, maxit=args.steps, check_every=8)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * e2e_res.info["iterations"] / e2e_s
+
+    # time to tolerance, float64 and float32 apply
+    tol64 = P.solve(prob.b)
+    P32 = B.Problem.from_problem(prob)
+    P32.factor(**FACTOR, precision=B.PREC_FP32, autotune=1)
+    tol32 = P32.solve(prob.b)
+    prof32 = P32.profile(prob.b, warmup=3, iters=args.steps)
+    x64 = tol64.x
+    err32 = float(np.linalg.norm(tol32.x - x64) / np.linalg.norm(x64))
+    plain = P.solve(prob.b, plain=True)
+
+    # roofline of the dominant kernel class
+    hbm, src = peaks()
+    cls = prof["classes"]
+    dom = max(cls, key=lambda k: cls[k]["ms"])
+    d = cls[dom]
+    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "iteration_achieved": prof["bytes_per_iter"] / (ms_per_step / 1000.0) / 1e9,
+            "iteration_frac": prof["bytes_per_iter"] / (ms_per_step / 1000.0) / 1e9 / hbm}
+    launches = sum(c["launches"] for c in cls.values())
+
+    out = {
+        "metric": "preconditioned LSMR iterations/s", "value": value, "unit": "iter/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scale": args.scale, "l2": "inputs larger than L2",
+                   "m": prob.m, "n": prob.n, "nnz_A": prob.nnz,
+                   "nnz_L1": finfo["nnz_L1"], "nnz_L2": finfo["nnz_L2"], "nnz_U": finfo["nnz_U"],
+                   "levels": [finfo["levels_L1"], finfo["levels_L1t"], finfo["levels_U"],
+                              finfo["levels_Ut"]],
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": 8 * prob.m / args.steps,
+                "d2h_bytes_per_step": 8 * prob.n / args.steps, "wall_s": e2e_s},
+        "time_to_tol": {
+            "fp64": {"iterations": tol64.info["iterations"], "seconds": tol64.info["solve_seconds"],
+                     "ratio": tol64.info["ratio"], "status": tol64.status},
+            "fp32_apply": {"iterations": tol32.info["iterations"],
+                           "seconds": tol32.info["solve_seconds"], "ratio": tol32.info["ratio"],
+                           "x_rel_diff_vs_fp64": err32, "status": tol32.status,
+                           "iter_per_s": 1000.0 / prof32["ms_per_iter"]},
+            "unpreconditioned": {"iterations": plain.info["iterations"],
+                                 "seconds": plain.info["solve_seconds"], "status": plain.status},
+        },
+        "factor_seconds": finfo["factor_seconds"],
+        "roofline": roof,
+        "kernel_classes": {k: {"ms": v["ms"], "launches": v["launches"],
+                               "GBps": v["bytes"] / (v["ms"] / 1000.0) / 1e9} for k, v in cls.items()},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_oracle_sample(args.cpu_scale, prob.nnz)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,126 @@
+// Autotuner for the kernel mappings of one problem: lanes per row (G) of the
+// A / A^T products and of the L2 / L2^T products, and, for each of the four
+// triangular systems, the schedule (one launch per level vs. sync-free) and
+// G.  Each candidate is timed with CUDA events on the problem's stream
+// (median of a few runs after a warm-up) on the problem's own matrices; the
+// fastest wins.  Results are cached on the handle until the next factor.
+#include <algorithm>
+#include <vector>
+
+#include "common.h"
+
+namespace rlsq {
+
+namespace {
+
+template <class F>
+void with_lanes(int G, F&& f) {
+    switch (G) {
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 16: f(std::integral_constant<int, 16>{}); break;
+        default: f(std::integral_constant<int, 32>{}); break;
+    }
+}
+
+template <class Body>
+float time_median(cudaStream_t st, Body&& body, int reps = 5) {
+    cudaEvent_t a, b;
+    RLSQ_CUDA(cudaEventCreate(&a));
+    RLSQ_CUDA(cudaEventCreate(&b));
+    body();  // warm-up
+    std::vector<float> ts;
+    for (int i = 0; i < reps; ++i) {
+        RLSQ_CUDA(cudaEventRecord(a, st));
+        body();
+        RLSQ_CUDA(cudaEventRecord(b, st));
+        RLSQ_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        RLSQ_CUDA(cudaEventElapsedTime(&ms, a, b));
+        ts.push_back(ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::sort(ts.begin(), ts.end());
+    return ts[ts.size() / 2];
+}
+
+int grid_for(const rlsq_problem_s* P, int64_t rows, int G) {
+    const int64_t g = (rows * G + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * 16))));
+}
+
+template <typename T>
+int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y) {
+    static const int cands[] = {2, 4, 8, 16, 32};
+    int best = 8;
+    float tbest = 1e30f;
+    for (int G : cands) {
+        const float t = time_median(P->stream, [&]() {
+            with_lanes(G, [&](auto g) {
+                k_csr_mv<T, decltype(g)::value><<<grid_for(P, M.rows, decltype(g)::value), kBlock, 0, P->stream>>>(
+                    M, x, y, nullptr);
+            });
+            RLSQ_CUDA(cudaGetLastError());
+        });
+        if (t < tbest) {
+            tbest = t;
+            best = G;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+int rlsq_trsv_time(rlsq_problem_s* P, int which, float* ms);
+
+template <typename T>
+static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
+    const int n = static_cast<int>(P->n);
+    // inputs: any finite vectors will do for timing
+    std::vector<T> ones(static_cast<size_t>(std::max<int64_t>(P->m, 1)), (T)1);
+    RLSQ_CUDA(cudaMemcpyAsync(F.vn[3].p, ones.data(), sizeof(T) * n, cudaMemcpyHostToDevice, P->stream));
+    RLSQ_CUDA(cudaMemcpyAsync(F.vm[0].p, ones.data(), sizeof(T) * F.vm[0].n, cudaMemcpyHostToDevice, P->stream));
+    RLSQ_CUDA(cudaStreamSynchronize(P->stream));
+    if (P->correction != RLSQ_CORR_NONE) {
+        P->map.G_L2 = best_mv_lanes<T>(P, F.L2.view(), F.vn[3].p, F.vm[1].p);
+        P->map.G_L2t = best_mv_lanes<T>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p);
+    }
+    static const int cands[] = {2, 4, 8, 16, 32};
+    for (int w = 0; w < 4; ++w) {
+        int bestG = P->map.G_tri[w], bestS = P->map.sched[w];
+        float tbest = 1e30f;
+        for (int sched : {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_LEVEL}) {
+            for (int G : cands) {
+                P->map.sched[w] = sched;
+                P->map.G_tri[w] = G;
+                float ms = 0.f;
+                if (rlsq_trsv_time(P, w, &ms) != RLSQ_OK) continue;
+                if (ms < tbest) {
+                    tbest = ms;
+                    bestG = G;
+                    bestS = sched;
+                }
+            }
+        }
+        P->map.G_tri[w] = bestG;
+        P->map.sched[w] = bestS;
+    }
+}
+
+void autotune(rlsq_problem_s* P) {
+    const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
+    std::vector<double> ones(static_cast<size_t>(m), 1.0);
+    RLSQ_CUDA(cudaMemcpyAsync(P->q.p, ones.data(), sizeof(double) * m, cudaMemcpyHostToDevice, P->stream));
+    RLSQ_CUDA(cudaMemcpyAsync(P->s.p, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, P->stream));
+    RLSQ_CUDA(cudaStreamSynchronize(P->stream));
+    P->map.G_A = best_mv_lanes<double>(P, P->dA.view(), P->s.p, P->r.p);
+    P->map.G_At = best_mv_lanes<double>(P, P->dAt.view(), P->q.p, P->t.p);
+    if (!P->factored) return;
+    if (P->precision == RLSQ_PREC_FP32) tune_factor<float>(P, P->f32);
+    else tune_factor<double>(P, P->f64);
+}
+
+}  // namespace rlsq

@@ -1,0 +1,174 @@
+// Shared host-side plumbing of the rlsq library: error reporting across the
+// C ABI, owning device arrays and the problem handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "host_setup.h"
+#include "kernels.cuh"
+#include "rlsq.h"
+
+namespace rlsq {
+
+// An error carrying an RLSQ_ERR_* code; caught at the C boundary.
+struct ApiError : std::runtime_error {
+    int code;
+    ApiError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] void throw_cuda(cudaError_t e, const char* what, int line);
+
+#define RLSQ_CUDA(call)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) ::rlsq::throw_cuda(e_, #call, __LINE__); \
+    } while (0)
+
+void set_last_error(const std::string& msg);
+
+// Runs f, mapping exceptions to status codes and the thread's last error.
+template <class F>
+int guarded(F&& f) {
+    try {
+        set_last_error("");
+        return f();
+    } catch (const ApiError& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return RLSQ_ERR_OOM;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return RLSQ_ERR_ARG;
+    }
+}
+
+template <typename T>
+struct DevArray {
+    T* p = nullptr;
+    size_t n = 0;
+    DevArray() = default;
+    DevArray(const DevArray&) = delete;
+    DevArray& operator=(const DevArray&) = delete;
+    ~DevArray() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        RLSQ_CUDA(cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T)));
+        n = count;
+    }
+    void upload(const T* host, size_t count, cudaStream_t s) {
+        alloc(count);
+        if (count) RLSQ_CUDA(cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+template <typename T>
+struct DevCsr {
+    int32_t rows = 0, cols = 0;
+    int64_t nnz = 0;
+    DevArray<int32_t> ptr, idx;
+    DevArray<T> val;
+    Csr<T> view() const { return Csr<T>{rows, cols, ptr.p, idx.p, val.p}; }
+    void upload(const HostCSR& h, cudaStream_t s);
+};
+
+// Kernel mapping choices for one problem (set by heuristics or the autotuner).
+struct Mapping {
+    int G_A = 8, G_At = 16;             // lanes per row of the A and A^T products
+    int G_tri[4] = {4, 4, 4, 4};        // lanes per row: L1, L1^T, U, U^T
+    int sched[4] = {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE};
+    int G_L2 = 4, G_L2t = 4;
+};
+
+template <typename T>
+struct DevFactor {
+    DevCsr<T> tri[4];          // strictly triangular parts: L1, L1^T, U, U^T
+    DevArray<T> diag[4];       // U diagonal for U and U^T (unit for L1, L1^T)
+    DevArray<int32_t> order[4];
+    std::vector<int32_t> level_ptr[4];
+    DevCsr<T> L2, L2t;
+    DevArray<T> d;
+    DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
+    DevArray<T> vn[5], vm[4];  // work vectors
+    void upload(const IlupResult& F, const std::vector<double>& sinv_h, cudaStream_t s);
+    void clear() {
+        for (int w = 0; w < 4; ++w) {
+            tri[w].ptr.release(); tri[w].idx.release(); tri[w].val.release();
+            diag[w].release(); order[w].release(); level_ptr[w].clear();
+        }
+        for (auto* c : {&L2, &L2t}) { c->ptr.release(); c->idx.release(); c->val.release(); }
+        d.release(); sinv.release();
+        for (auto& v : vn) v.release();
+        for (auto& v : vm) v.release();
+    }
+    Tri<T> tview(int which) const {
+        return Tri<T>{tri[which].view(), (which >= 2) ? diag[which].p : nullptr, order[which].p};
+    }
+};
+
+// Event pairs around launches, attributed to RLSQ_KCLASS_* (profiling only).
+struct Recorder {
+    struct Entry {
+        int cls;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    std::vector<Entry> entries;
+    ~Recorder() {
+        for (auto& e : entries) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+    }
+};
+
+}  // namespace rlsq
+
+struct rlsq_problem_s {
+    int64_t m = 0, n = 0, nnz = 0;
+    rlsq::HostCSR A;                 // host copy (the set-up runs on the host)
+    rlsq::DevCsr<double> dA, dAt;    // CSR and CSC (= CSR of A^T) of A
+    double anorm = 0.0;
+    cudaStream_t stream = nullptr;   // internal stream
+    int device = 0;
+    int num_sms = 0;
+
+    bool factored = false;
+    rlsq_factor_opts opts{};
+    int correction = RLSQ_CORR_NONE;
+    int precision = RLSQ_PREC_FP64;
+    double factor_seconds = 0.0;
+    std::unique_ptr<rlsq::IlupResult> F;
+    rlsq::DevFactor<double> f64;
+    rlsq::DevFactor<float> f32;
+    rlsq::Mapping map;
+
+    // LSMR work vectors (float64)
+    rlsq::DevArray<double> q, r, b, s, t, h, hb, x;
+    rlsq::DevArray<rlsq::LsmrState> S;   // [0] solve, [1] standalone calls
+    rlsq::DevArray<double> part;
+    rlsq::DevArray<unsigned> counter, tickets;
+    rlsq::DevArray<int> flags;
+    rlsq::LsmrState* pinned_state = nullptr;   // host-pinned mirror
+    int* pinned_done = nullptr;                // [2]
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+
+    rlsq::Recorder* rec = nullptr;                  // set while profiling one eager iteration
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [plain] iteration graphs
+    int graph_iters[2] = {0, 0};
+
+    ~rlsq_problem_s();
+};

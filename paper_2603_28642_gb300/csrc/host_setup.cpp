@@ -1,0 +1,431 @@
+// Host set-up of the row-splitting ILU preconditioner (see host_setup.h).
+//
+// The factorisation follows the column-wise ILUP(p, tau) of Algorithm 4 with
+// the pivot rule of Algorithm 5 and the pivot modification of Algorithm 6
+// (Scott & Tuma, Sec. 4).  Column j is computed left-looking, in the
+// Gilbert-Peierls manner the paper describes: a graph search over the
+// already computed columns of L finds the pivot positions reached from the
+// nonzeros of A(:, j) (the pattern of U(1:j-1, j)), the positions are sorted
+// ascending (a topological order because L is unit lower triangular in pivot
+// order), and the sparse triangular solve then updates the not-yet-pivoted
+// rows at the same time, which yields the L part of step 7.
+//
+// Readings of points the paper leaves open:
+//  * rc(i) at step j counts the nonzeros of the original scaled matrix in row
+//    i and columns j..n.
+//  * Algorithm 5 ties: smallest rc, then largest |L_qj|, then smallest row id.
+//  * empty column: pivot on the unpivoted row with the smallest rc (then id),
+//    value max(beta ||A_:,j||_inf, small); small pivot: the same magnitude
+//    with the pivot's sign.  beta = 10^(-2 (1 - j/n)), 1-based j.
+//  * dropping: |.| >= tau kept, then the p largest; ties keep the smaller
+//    pivot position (U) or the smaller row id (L); the U part is dropped
+//    after the L part has been computed from the undropped values.
+#include "host_setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+#include <thread>
+
+namespace rlsq {
+
+HostCSR transpose(const HostCSR& a) {
+    HostCSR t;
+    t.rows = a.cols;
+    t.cols = a.rows;
+    t.ptr.assign(static_cast<size_t>(a.cols) + 1, 0);
+    const int64_t nnz = a.nnz();
+    t.idx.resize(static_cast<size_t>(nnz));
+    t.val.resize(static_cast<size_t>(nnz));
+    for (int64_t e = 0; e < nnz; ++e) t.ptr[a.idx[e] + 1]++;
+    for (int64_t c = 0; c < a.cols; ++c) t.ptr[c + 1] += t.ptr[c];
+    std::vector<int64_t> pos(t.ptr.begin(), t.ptr.end() - 1);
+    for (int64_t r = 0; r < a.rows; ++r)
+        for (int64_t e = a.ptr[r]; e < a.ptr[r + 1]; ++e) {
+            const int64_t dst = pos[a.idx[e]]++;
+            t.idx[dst] = static_cast<int32_t>(r);
+            t.val[dst] = a.val[e];
+        }
+    return t;
+}
+
+bool column_scaling(const HostCSR& a, std::vector<double>& d) {
+    std::vector<double> ss(static_cast<size_t>(a.cols), 0.0);
+    for (int64_t r = 0; r < a.rows; ++r)
+        for (int64_t e = a.ptr[r]; e < a.ptr[r + 1]; ++e) {
+            const double v = a.val[e];
+            ss[a.idx[e]] = ss[a.idx[e]] + v * v;
+        }
+    d.resize(static_cast<size_t>(a.cols));
+    bool ok = true;
+    for (int64_t j = 0; j < a.cols; ++j) {
+        if (!(ss[j] > 0.0)) ok = false;
+        d[j] = 1.0 / std::sqrt(ss[j]);
+    }
+    return ok;
+}
+
+namespace {
+
+struct Entry {
+    double mag;
+    int32_t key;
+    double val;
+};
+
+// keep |v| >= tau, then the p largest (ties: smaller key); result sorted by key
+void dual_drop(std::vector<Entry>& c, int p, double tau) {
+    size_t w = 0;
+    for (size_t i = 0; i < c.size(); ++i)
+        if (c[i].mag >= tau && c[i].val != 0.0) c[w++] = c[i];
+    c.resize(w);
+    if (p >= 0 && c.size() > static_cast<size_t>(p)) {
+        auto better = [](const Entry& a, const Entry& b) {
+            return a.mag > b.mag || (a.mag == b.mag && a.key < b.key);
+        };
+        std::nth_element(c.begin(), c.begin() + p, c.end(), better);
+        c.resize(static_cast<size_t>(p));
+    }
+    std::sort(c.begin(), c.end(), [](const Entry& a, const Entry& b) { return a.key < b.key; });
+}
+
+}  // namespace
+
+Levels analyse_levels(const HostCSR& s, bool lower) {
+    Levels L;
+    const int64_t n = s.rows;
+    L.level.assign(static_cast<size_t>(n), 0);
+    int32_t nlev = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t i = lower ? t : n - 1 - t;
+        int32_t lv = 0;
+        for (int64_t e = s.ptr[i]; e < s.ptr[i + 1]; ++e) lv = std::max(lv, L.level[s.idx[e]] + 1);
+        L.level[i] = lv;
+        nlev = std::max(nlev, lv + 1);
+    }
+    if (n == 0) nlev = 0;
+    L.nlevels = nlev;
+    L.level_ptr.assign(static_cast<size_t>(nlev) + 1, 0);
+    for (int64_t i = 0; i < n; ++i) L.level_ptr[L.level[i] + 1]++;
+    for (int32_t l = 0; l < nlev; ++l) {
+        L.max_width = std::max(L.max_width, L.level_ptr[l + 1]);
+        L.level_ptr[l + 1] += L.level_ptr[l];
+    }
+    L.order.resize(static_cast<size_t>(n));
+    std::vector<int32_t> pos(L.level_ptr.begin(), L.level_ptr.end() - 1);
+    for (int64_t i = 0; i < n; ++i) L.order[pos[L.level[i]]++] = static_cast<int32_t>(i);
+    return L;
+}
+
+IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
+    const int64_t m = a.rows, n = a.cols;
+    if (!(m > n && n > 0)) throw std::runtime_error("need m > n > 0");
+    IlupResult R;
+    R.m = m;
+    R.n = n;
+    if (prm.scale) {
+        if (!column_scaling(a, R.d)) throw std::runtime_error("A has an empty column");
+    } else {
+        R.d.assign(static_cast<size_t>(n), 1.0);
+    }
+
+    // scaled matrix by columns, rows ascending in each column
+    HostCSR ac = transpose(a);
+    for (int64_t j = 0; j < n; ++j) {
+        if (ac.ptr[j + 1] == ac.ptr[j]) throw std::runtime_error("A has an empty column");
+        for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) ac.val[e] = ac.val[e] * R.d[j];
+    }
+
+    std::vector<int64_t> rc(static_cast<size_t>(m));
+    for (int64_t i = 0; i < m; ++i) rc[i] = a.ptr[i + 1] - a.ptr[i];
+
+    std::vector<int32_t> pivpos(static_cast<size_t>(m), -1);
+    R.prow.assign(static_cast<size_t>(n), -1);
+    R.Udiag.assign(static_cast<size_t>(n), 0.0);
+
+    // columns of L (original row id, multiplier) and of U (pivot position, value)
+    std::vector<int64_t> Lp(static_cast<size_t>(n) + 1, 0), Up(static_cast<size_t>(n) + 1, 0);
+    std::vector<int32_t> Li, Ui;
+    std::vector<double> Lv, Uv;
+    const size_t guess = static_cast<size_t>(n) * static_cast<size_t>(prm.p >= 0 ? prm.p : 16);
+    Li.reserve(guess);
+    Lv.reserve(guess);
+    Ui.reserve(guess);
+    Uv.reserve(guess);
+
+    std::vector<double> x(static_cast<size_t>(m));
+    std::vector<int32_t> xmark(static_cast<size_t>(m), -1);
+    std::vector<int32_t> vmark(static_cast<size_t>(n), -1);
+    std::vector<int32_t> touched, reach, stack;
+    std::vector<Entry> cand;
+
+    for (int64_t jj = 0; jj < n; ++jj) {
+        const int32_t j = static_cast<int32_t>(jj);
+        touched.clear();
+        reach.clear();
+        stack.clear();
+        double colinf = 0.0;
+        // scatter the scaled column and seed the graph search
+        for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) {
+            const int32_t i = ac.idx[e];
+            x[i] = ac.val[e];
+            xmark[i] = j;
+            touched.push_back(i);
+            colinf = std::max(colinf, std::fabs(ac.val[e]));
+            const int32_t k = pivpos[i];
+            if (k >= 0 && vmark[k] != j) {
+                vmark[k] = j;
+                stack.push_back(k);
+            }
+        }
+        // symbolic: every pivot position reachable through the columns of L
+        while (!stack.empty()) {
+            const int32_t k = stack.back();
+            stack.pop_back();
+            reach.push_back(k);
+            for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
+                const int32_t q = pivpos[Li[e]];
+                if (q >= 0 && vmark[q] != j) {
+                    vmark[q] = j;
+                    stack.push_back(q);
+                }
+            }
+        }
+        std::sort(reach.begin(), reach.end());
+        // numeric: unit lower solve in ascending pivot position
+        cand.clear();
+        for (const int32_t k : reach) {
+            const int32_t pr = R.prow[k];
+            const double ukj = (xmark[pr] == j) ? x[pr] : 0.0;
+            if (ukj == 0.0) continue;
+            cand.push_back({std::fabs(ukj), k, ukj});
+            for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
+                const int32_t i = Li[e];
+                if (xmark[i] != j) {
+                    xmark[i] = j;
+                    x[i] = 0.0;
+                    touched.push_back(i);
+                }
+                x[i] = x[i] - Lv[e] * ukj;
+            }
+        }
+        dual_drop(cand, prm.p, prm.tau);
+        for (const Entry& c : cand) {
+            Ui.push_back(c.key);
+            Uv.push_back(c.val);
+        }
+        Up[j + 1] = static_cast<int64_t>(Ui.size());
+
+        // pivot choice
+        const double beta = std::pow(10.0, -2.0 * (1.0 - static_cast<double>(jj + 1) / static_cast<double>(n)));
+        double modval = beta * colinf;
+        if (modval < prm.small) modval = prm.small;
+        double maxabs = 0.0;
+        bool any = false;
+        for (const int32_t i : touched)
+            if (pivpos[i] < 0 && x[i] != 0.0) {
+                any = true;
+                maxabs = std::max(maxabs, std::fabs(x[i]));
+            }
+        int32_t r = -1;
+        double piv;
+        if (!any) {
+            for (int64_t i = 0; i < m; ++i)
+                if (pivpos[i] < 0 && (r < 0 || rc[i] < rc[r])) r = static_cast<int32_t>(i);
+            piv = modval;
+            R.nmod++;
+        } else {
+            const double thr = prm.mu * maxabs;
+            double rmag = 0.0;
+            for (const int32_t i : touched) {
+                if (pivpos[i] >= 0 || x[i] == 0.0) continue;
+                const double mag = std::fabs(x[i]);
+                if (!(mag >= thr)) continue;
+                bool take = r < 0;
+                if (!take) {
+                    if (rc[i] != rc[r]) take = rc[i] < rc[r];
+                    else if (mag != rmag) take = mag > rmag;
+                    else take = i < r;
+                }
+                if (take) {
+                    r = i;
+                    rmag = mag;
+                }
+            }
+            piv = x[r];
+            if (std::fabs(piv) < prm.small) {
+                piv = (piv < 0.0) ? -modval : modval;
+                R.nmod++;
+            }
+        }
+        R.Udiag[j] = piv;
+        pivpos[r] = j;
+        R.prow[j] = r;
+
+        // L part: scale by the pivot, then drop
+        cand.clear();
+        for (const int32_t i : touched) {
+            if (pivpos[i] >= 0 || x[i] == 0.0) continue;
+            const double l = x[i] / piv;
+            cand.push_back({std::fabs(l), i, l});
+        }
+        dual_drop(cand, prm.p, prm.tau);
+        for (const Entry& c : cand) {
+            Li.push_back(c.key);
+            Lv.push_back(c.val);
+        }
+        Lp[j + 1] = static_cast<int64_t>(Li.size());
+
+        for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) rc[ac.idx[e]]--;
+    }
+
+    // split: pivot rows in pivot order form L1, the rest (ascending id) L2
+    const int64_t m2 = m - n;
+    std::vector<int32_t> a2idx(static_cast<size_t>(m), -1);
+    R.a2rows.reserve(static_cast<size_t>(m2));
+    for (int64_t i = 0; i < m; ++i)
+        if (pivpos[i] < 0) {
+            a2idx[i] = static_cast<int32_t>(R.a2rows.size());
+            R.a2rows.push_back(static_cast<int32_t>(i));
+        }
+    R.L1.rows = n; R.L1.cols = n;
+    R.L2.rows = m2; R.L2.cols = n;
+    R.L1.ptr.assign(static_cast<size_t>(n) + 1, 0);
+    R.L2.ptr.assign(static_cast<size_t>(m2) + 1, 0);
+    for (size_t e = 0; e < Li.size(); ++e) {
+        const int32_t i = Li[e];
+        if (pivpos[i] >= 0) R.L1.ptr[pivpos[i] + 1]++;
+        else R.L2.ptr[a2idx[i] + 1]++;
+    }
+    for (int64_t k = 0; k < n; ++k) R.L1.ptr[k + 1] += R.L1.ptr[k];
+    for (int64_t k = 0; k < m2; ++k) R.L2.ptr[k + 1] += R.L2.ptr[k];
+    R.L1.idx.resize(static_cast<size_t>(R.L1.ptr[n]));
+    R.L1.val.resize(static_cast<size_t>(R.L1.ptr[n]));
+    R.L2.idx.resize(static_cast<size_t>(R.L2.ptr[m2]));
+    R.L2.val.resize(static_cast<size_t>(R.L2.ptr[m2]));
+    {
+        std::vector<int64_t> f1(R.L1.ptr.begin(), R.L1.ptr.end() - 1);
+        std::vector<int64_t> f2(R.L2.ptr.begin(), R.L2.ptr.end() - 1);
+        for (int64_t k = 0; k < n; ++k)
+            for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
+                const int32_t i = Li[e];
+                if (pivpos[i] >= 0) {
+                    const int64_t dst = f1[pivpos[i]]++;
+                    R.L1.idx[dst] = static_cast<int32_t>(k);
+                    R.L1.val[dst] = Lv[e];
+                } else {
+                    const int64_t dst = f2[a2idx[i]]++;
+                    R.L2.idx[dst] = static_cast<int32_t>(k);
+                    R.L2.val[dst] = Lv[e];
+                }
+            }
+    }
+    R.U.rows = n; R.U.cols = n;
+    R.U.ptr.assign(static_cast<size_t>(n) + 1, 0);
+    for (const int32_t k : Ui) R.U.ptr[k + 1]++;
+    for (int64_t k = 0; k < n; ++k) R.U.ptr[k + 1] += R.U.ptr[k];
+    R.U.idx.resize(Ui.size());
+    R.U.val.resize(Ui.size());
+    {
+        std::vector<int64_t> fu(R.U.ptr.begin(), R.U.ptr.end() - 1);
+        for (int64_t jj = 0; jj < n; ++jj)
+            for (int64_t e = Up[jj]; e < Up[jj + 1]; ++e) {
+                const int64_t dst = fu[Ui[e]]++;
+                R.U.idx[dst] = static_cast<int32_t>(jj);
+                R.U.val[dst] = Uv[e];
+            }
+    }
+    R.L1t = transpose(R.L1);
+    R.L2t = transpose(R.L2);
+    R.Ut = transpose(R.U);
+    R.lev_L1 = analyse_levels(R.L1, true);
+    R.lev_L1t = analyse_levels(R.L1t, false);
+    R.lev_U = analyse_levels(R.U, false);
+    R.lev_Ut = analyse_levels(R.Ut, true);
+    return R;
+}
+
+bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads) {
+    const int64_t n = f.n, m2 = f.m - f.n;
+    if (m2 <= 0) {
+        sinv.clear();
+        return true;
+    }
+    if (threads < 1) threads = 1;
+    // Z(:, c) = L1^{-T} L2(c, :)^T, stored column-major (n x m2)
+    std::vector<double> Z(static_cast<size_t>(n * m2), 0.0);
+    auto zcols = [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c) {
+            double* z = Z.data() + c * n;
+            for (int64_t e = f.L2.ptr[c]; e < f.L2.ptr[c + 1]; ++e) z[f.L2.idx[e]] = f.L2.val[e];
+            // unit upper solve with L1^T: z_i -= sum_{k > i} L1t(i, k) z_k, i descending
+            for (int64_t i = n - 1; i >= 0; --i) {
+                double s = z[i];
+                for (int64_t e = f.L1t.ptr[i]; e < f.L1t.ptr[i + 1]; ++e) s -= f.L1t.val[e] * z[f.L1t.idx[e]];
+                z[i] = s;
+            }
+        }
+    };
+    auto par = [&](int64_t count, auto&& body) {
+        std::vector<std::thread> th;
+        const int64_t chunk = (count + threads - 1) / threads;
+        for (int t = 0; t < threads; ++t) {
+            const int64_t lo = t * chunk, hi = std::min(count, lo + chunk);
+            if (lo < hi) th.emplace_back(body, lo, hi);
+        }
+        for (auto& x : th) x.join();
+    };
+    par(m2, zcols);
+    // S = I + Z^T Z (lower triangle, row-major)
+    std::vector<double> S(static_cast<size_t>(m2 * m2), 0.0);
+    par(m2, [&](int64_t a0, int64_t a1) {
+        for (int64_t a = a0; a < a1; ++a) {
+            const double* za = Z.data() + a * n;
+            for (int64_t b = 0; b <= a; ++b) {
+                const double* zb = Z.data() + b * n;
+                double s = 0.0;
+                for (int64_t i = 0; i < n; ++i) s += za[i] * zb[i];
+                S[a * m2 + b] = (a == b) ? 1.0 + s : s;
+            }
+        }
+    });
+    Z.clear();
+    Z.shrink_to_fit();
+    // Cholesky S = G G^T in place (lower)
+    for (int64_t j = 0; j < m2; ++j) {
+        double s = S[j * m2 + j];
+        for (int64_t k = 0; k < j; ++k) s -= S[j * m2 + k] * S[j * m2 + k];
+        if (!(s > 0.0)) return false;
+        const double g = std::sqrt(s);
+        S[j * m2 + j] = g;
+        for (int64_t i = j + 1; i < m2; ++i) {
+            double t = S[i * m2 + j];
+            for (int64_t k = 0; k < j; ++k) t -= S[i * m2 + k] * S[j * m2 + k];
+            S[i * m2 + j] = t / g;
+        }
+    }
+    // W = G^{-1} (lower), then S^{-1} = W^T W
+    std::vector<double> W(static_cast<size_t>(m2 * m2), 0.0);
+    par(m2, [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c) {
+            // column c of G^{-1}: forward substitution with e_c
+            for (int64_t i = c; i < m2; ++i) {
+                double s = (i == c) ? 1.0 : 0.0;
+                for (int64_t k = c; k < i; ++k) s -= S[i * m2 + k] * W[k * m2 + c];
+                W[i * m2 + c] = s / S[i * m2 + i];
+            }
+        }
+    });
+    sinv.assign(static_cast<size_t>(m2 * m2), 0.0);
+    par(m2, [&](int64_t a0, int64_t a1) {
+        for (int64_t a = a0; a < a1; ++a)
+            for (int64_t b = 0; b < m2; ++b) {
+                double s = 0.0;
+                for (int64_t k = std::max(a, b); k < m2; ++k) s += W[k * m2 + a] * W[k * m2 + b];
+                sinv[a * m2 + b] = s;
+            }
+    });
+    return true;
+}
+
+}  // namespace rlsq

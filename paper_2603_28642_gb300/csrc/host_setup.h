@@ -1,0 +1,74 @@
+// Host-side set-up of the row-splitting ILU preconditioner: column scaling,
+// the rectangular threshold-pivoted ILUP(p, tau) factorisation (Algorithms
+// 4-6 of Scott & Tuma), the row split P A D ~ [L1; L2] U (eq. 3.8), level
+// analysis of the four triangular systems and the dense auxiliary matrix
+// S = I + Y Y^T (eq. 3.9) for the dense correction mode.
+//
+// Everything here runs once per matrix on the CPU.  Floating-point sums are
+// evaluated in a fixed order and this translation unit is compiled with
+// -ffp-contract=off, so the factor is reproducible bit for bit.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace rlsq {
+
+struct HostCSR {
+    int64_t rows = 0, cols = 0;
+    std::vector<int64_t> ptr;  // rows + 1
+    std::vector<int32_t> idx;  // column ids ascending within each row
+    std::vector<double> val;
+    int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+// Transpose (rows x cols -> cols x rows); entries of each output row keep
+// ascending column order.
+HostCSR transpose(const HostCSR& a);
+
+struct IlupParams {
+    int p = 10;          // max off-diagonal entries kept per column of L and U (< 0: all)
+    double tau = 1e-2;   // absolute drop tolerance
+    double mu = 0.1;     // threshold pivoting parameter (Algorithm 5)
+    double small = 1e-10;// smallest admissible |U_jj| (Algorithm 6)
+    bool scale = true;   // prescale columns to unit 2-norm
+};
+
+// Level structure of one triangular system: level of every row, rows sorted
+// by (level, row id), and the start of each level in that order.
+struct Levels {
+    std::vector<int32_t> level;
+    std::vector<int32_t> order;
+    std::vector<int32_t> level_ptr;  // nlevels + 1
+    int32_t nlevels = 0;
+    int32_t max_width = 0;
+};
+
+struct IlupResult {
+    int64_t m = 0, n = 0;
+    std::vector<double> d;          // column scaling
+    std::vector<int32_t> prow;      // prow[k]: original row pivoted at position k
+    std::vector<int32_t> a2rows;    // rows of A2 (unpivoted), ascending
+    HostCSR L1, L1t;                // strictly lower unit factor (rows = pivot positions) and its transpose
+    HostCSR L2, L2t;                // (m-n) x n and its transpose
+    HostCSR U, Ut;                  // strictly upper part of U and its transpose
+    std::vector<double> Udiag;
+    int64_t nmod = 0;
+    Levels lev_L1, lev_L1t, lev_U, lev_Ut;
+};
+
+// Column scaling d_j = 1 / ||A_:,j||_2.  Returns false if a column is empty.
+bool column_scaling(const HostCSR& a, std::vector<double>& d);
+
+// Full set-up.  Throws std::runtime_error with a message on bad input.
+IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm);
+
+// lower = true: row i depends on k < i; otherwise on k > i.
+Levels analyse_levels(const HostCSR& strict, bool lower);
+
+// Dense inverse of S = I + Z^T Z, Z = L1^{-T} L2^T, through its Cholesky
+// factor; row-major (m-n)^2.  Returns false if S is not numerically SPD.
+bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads);
+
+}  // namespace rlsq

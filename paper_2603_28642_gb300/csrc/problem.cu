@@ -1,0 +1,1033 @@
+// Single-problem path of the rlsq C ABI: create / factor / solve / apply.
+//
+// One LSMR iteration is the kernel sequence
+//   k_spmv_lsmr   q = A v^ - alpha u (norm -> beta), r = b - A x (norm)
+//   k_spmvt_lsmr  s = A^T u - beta w, ||A^T r|| -> stopping test on x_k
+//   apply         t = M^{-1} s  (triangular solves, L2 products, S^ solve)
+//   k_finish      alpha = sqrt(<t, s>), LSMR rotations
+//   k_lsmr_update h-bar, x, h
+// captured once in a CUDA graph (check_every iterations per graph) and
+// replayed; the host only reads the `done` word between graphs.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <thread>
+#include <type_traits>
+
+#include "common.h"
+
+namespace rlsq {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void throw_cuda(cudaError_t e, const char* what, int line) {
+    const int code = (e == cudaErrorMemoryAllocation) ? RLSQ_ERR_OOM : RLSQ_ERR_CUDA;
+    throw ApiError(code, std::string("CUDA error ") + cudaGetErrorString(e) + " in " + what +
+                             " (line " + std::to_string(line) + ")");
+}
+
+template <typename T>
+void DevCsr<T>::upload(const HostCSR& h, cudaStream_t s) {
+    rows = static_cast<int32_t>(h.rows);
+    cols = static_cast<int32_t>(h.cols);
+    nnz = h.nnz();
+    if (nnz >= (int64_t(1) << 31)) throw ApiError(RLSQ_ERR_SHAPE, "more than 2^31 - 1 nonzeros");
+    std::vector<int32_t> p32(h.ptr.begin(), h.ptr.end());
+    ptr.upload(p32.data(), p32.size(), s);
+    idx.upload(h.idx.data(), h.idx.size(), s);
+    if constexpr (std::is_same<T, double>::value) {
+        val.upload(reinterpret_cast<const T*>(h.val.data()), h.val.size(), s);
+    } else {
+        std::vector<T> v(h.val.begin(), h.val.end());
+        val.upload(v.data(), v.size(), s);
+    }
+    // host vectors die at return: make the copies complete first
+    RLSQ_CUDA(cudaStreamSynchronize(s));
+}
+
+template <typename T>
+static void upload_vec(DevArray<T>& dst, const std::vector<double>& src, cudaStream_t s) {
+    std::vector<T> v(src.begin(), src.end());
+    dst.upload(v.data(), v.size(), s);
+    RLSQ_CUDA(cudaStreamSynchronize(s));
+}
+
+template <typename T>
+void DevFactor<T>::upload(const IlupResult& F, const std::vector<double>& sinv_h, cudaStream_t s) {
+    const HostCSR* parts[4] = {&F.L1, &F.L1t, &F.U, &F.Ut};
+    const Levels* levs[4] = {&F.lev_L1, &F.lev_L1t, &F.lev_U, &F.lev_Ut};
+    for (int w = 0; w < 4; ++w) {
+        tri[w].upload(*parts[w], s);
+        order[w].upload(levs[w]->order.data(), levs[w]->order.size(), s);
+        level_ptr[w] = levs[w]->level_ptr;
+        if (w >= 2) upload_vec(diag[w], F.Udiag, s);
+    }
+    L2.upload(F.L2, s);
+    L2t.upload(F.L2t, s);
+    upload_vec(d, F.d, s);
+    if (!sinv_h.empty()) upload_vec(sinv, sinv_h, s);
+    else sinv.release();
+    const size_t n = static_cast<size_t>(F.n), m2 = static_cast<size_t>(F.m - F.n);
+    for (auto& v : vn) v.alloc(n);
+    for (auto& v : vm) v.alloc(std::max<size_t>(m2, 1));
+    RLSQ_CUDA(cudaStreamSynchronize(s));
+}
+
+template struct DevCsr<double>;
+template struct DevCsr<float>;
+template struct DevFactor<double>;
+template struct DevFactor<float>;
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+template <class F>
+static void with_G(int G, F&& f) {
+    switch (G) {
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 16: f(std::integral_constant<int, 16>{}); break;
+        default: f(std::integral_constant<int, 32>{}); break;
+    }
+}
+template <class F>
+static void with_rhs(int k, F&& f) {
+    switch (k) {
+        case RHS_SCALED: f(std::integral_constant<int, RHS_SCALED>{}); break;
+        case RHS_SUB: f(std::integral_constant<int, RHS_SUB>{}); break;
+        default: f(std::integral_constant<int, RHS_VEC>{}); break;
+    }
+}
+
+static int max_grid(const rlsq_problem_s* P) { return std::max(1, P->num_sms * 16); }
+
+static int grid_rows(const rlsq_problem_s* P, int64_t rows, int G) {
+    const int64_t g = (rows * G + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, max_grid(P))));
+}
+
+static LsmrState* state_ptr(rlsq_problem_s* P, int which) { return P->S.p + which; }
+static int* error_word(LsmrState* S) {
+    return reinterpret_cast<int*>(reinterpret_cast<char*>(S) + offsetof(LsmrState, error));
+}
+
+// Brackets the launches of its lifetime with an event pair when profiling.
+struct RecScope {
+    rlsq_problem_s* P;
+    cudaStream_t st;
+    size_t slot = 0;
+    RecScope(rlsq_problem_s* p, int cls, double bytes, cudaStream_t s) : P(p), st(s) {
+        if (!P->rec) return;
+        Recorder::Entry e{cls, bytes, nullptr, nullptr};
+        RLSQ_CUDA(cudaEventCreate(&e.a));
+        RLSQ_CUDA(cudaEventCreate(&e.b));
+        RLSQ_CUDA(cudaEventRecord(e.a, st));
+        P->rec->entries.push_back(e);
+        slot = P->rec->entries.size();
+    }
+    ~RecScope() {
+        if (P->rec && slot) cudaEventRecord(P->rec->entries[slot - 1].b, st);
+    }
+};
+
+template <typename T>
+static double trsv_bytes(const rlsq_problem_s* P, const DevFactor<T>& F, int which) {
+    const double n = static_cast<double>(P->n), v = sizeof(T);
+    return (v + 4.0) * static_cast<double>(F.tri[which].nnz) + 8.0 * n + 3.0 * v * n +
+           ((which >= 2) ? v * n : 0.0);
+}
+template <typename T>
+static double mv_bytes(const DevCsr<T>& M, double in_bytes_per_col, double out_bytes_per_row) {
+    return (sizeof(T) + 4.0) * static_cast<double>(M.nnz) + 4.0 * M.rows +
+           in_bytes_per_col * M.cols + out_bytes_per_row * M.rows;
+}
+
+template <typename T>
+static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, Rhs<T> rhs, T* x,
+                        int slot, LsmrState* S, cudaStream_t st) {
+    const Tri<T> tri = F.tview(which);
+    const int n = tri.a.rows;
+    const int G = P->map.G_tri[which];
+    RecScope rs(P, RLSQ_KCLASS_TRSV_L1 + which, trsv_bytes(P, F, which), st);
+    if (P->map.sched[which] == RLSQ_TRSV_LEVEL) {
+        const auto& lp = F.level_ptr[which];
+        for (size_t l = 0; l + 1 < lp.size(); ++l) {
+            const int lo = lp[l], hi = lp[l + 1];
+            const int grid = grid_rows(P, hi - lo, G);
+            with_G(G, [&](auto g) {
+                with_rhs(rk, [&](auto k) {
+                    k_trsv_level<T, decltype(g)::value, decltype(k)::value>
+                        <<<grid, kBlock, 0, st>>>(tri, rhs, x, lo, hi, S);
+                });
+            });
+        }
+    } else {
+        if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
+        with_G(G, [&](auto g) {
+            constexpr int GG = decltype(g)::value;
+            constexpr int ROUNDS = 4;
+            const int chunk_rows = (kBlock / GG) * ROUNDS;
+            const int chunks = (n + chunk_rows - 1) / chunk_rows;
+            with_rhs(rk, [&](auto k) {
+                auto kern = k_trsv_syncfree<T, GG, decltype(k)::value, ROUNDS>;
+                int occ = 0;
+                RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, 0));
+                const int grid = std::max(1, std::min(chunks, std::max(1, occ) * P->num_sms));
+                kern<<<grid, kBlock, 0, st>>>(tri, rhs, x, P->flags.p, slot, P->tickets.p, S,
+                                              error_word(S));
+            });
+        });
+    }
+}
+
+// t = M^{-1} s for the float64 vector s, result in P->t; advances the LSMR
+// scalars (INIT: the first alpha) or only the apply count (standalone).
+template <typename T, bool INIT>
+static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, LsmrState* S,
+                          cudaStream_t st) {
+    const int n = static_cast<int>(P->n);
+    const int m2 = static_cast<int>(P->m - P->n);
+    RLSQ_CUDA(cudaMemsetAsync(P->tickets.p, 0, sizeof(unsigned) * kMaxSlots, st));
+    int slot = 0;
+    T* g1 = F.vn[0].p;
+    T* g2 = F.vn[1].p;
+    launch_trsv<T>(P, F, 3, RHS_SCALED, Rhs<T>{F.d.p, nullptr, s}, g1, slot++, S, st);  // U^{-T} D s
+    launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{g1, nullptr, nullptr}, g2, slot++, S, st);  // L1^{-T}
+    T* g4 = F.vn[0].p;
+    if (P->correction != RLSQ_CORR_NONE) {
+        T* q1 = F.vn[2].p;
+        launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{g2, nullptr, nullptr}, q1, slot++, S, st);  // L1^{-1}
+        const Csr<T> L2 = F.L2.view(), L2t = F.L2t.view();
+        const int gl2 = grid_rows(P, m2, P->map.G_L2), gl2t = grid_rows(P, n, P->map.G_L2t);
+        const int gv = grid_rows(P, m2, 1);
+        T* wv = nullptr;
+        if (P->correction == RLSQ_CORR_CG) {
+            T *rv = F.vm[0].p, *pv = F.vm[1].p, *sp = F.vm[2].p, *w = F.vm[3].p;
+            T *c1 = F.vn[3].p, *c2 = F.vn[4].p, *c3 = F.vn[2].p;
+            {
+                RecScope rs(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
+                with_G(P->map.G_L2, [&](auto g) {
+                    k_l2_start<T, decltype(g)::value><<<gl2, kBlock, 0, st>>>(L2, q1, rv, S, P->part.p,
+                                                                              P->counter.p);
+                });
+            }
+            for (int it = 0; it < P->opts.cg_steps; ++it) {
+                const bool first = (it == 0);
+                {
+                    RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, first ? sizeof(T) : 2 * sizeof(T), sizeof(T)), st);
+                    with_G(P->map.G_L2t, [&](auto g) {
+                        constexpr int GG = decltype(g)::value;
+                        if (first) k_l2t_cg<T, GG, true><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S);
+                        else k_l2t_cg<T, GG, false><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S);
+                    });
+                }
+                launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{c1, nullptr, nullptr}, c2, slot++, S, st);
+                launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{c2, nullptr, nullptr}, c3, slot++, S, st);
+                RecScope rs2(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), first ? 3 * sizeof(T) : 4 * sizeof(T)), st);
+                with_G(P->map.G_L2, [&](auto g) {
+                    constexpr int GG = decltype(g)::value;
+                    if (first)
+                        k_l2_sp<T, GG, true><<<gl2, kBlock, 0, st>>>(L2, c3, rv, pv, sp, S, P->part.p,
+                                                                     P->counter.p);
+                    else
+                        k_l2_sp<T, GG, false><<<gl2, kBlock, 0, st>>>(L2, c3, rv, pv, sp, S, P->part.p,
+                                                                      P->counter.p);
+                });
+                RecScope rs3(P, RLSQ_KCLASS_VEC, (first ? 4.0 : 5.0) * sizeof(T) * m2, st);
+                if (first)
+                    k_cg_update<T, true><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, w, S, P->part.p,
+                                                                P->counter.p);
+                else
+                    k_cg_update<T, false><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, w, S, P->part.p,
+                                                                 P->counter.p);
+            }
+            wv = w;
+        } else {
+            T* e = F.vm[0].p;
+            {
+                RecScope rs(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
+                with_G(P->map.G_L2, [&](auto g) {
+                    k_csr_mv<T, decltype(g)::value><<<gl2, kBlock, 0, st>>>(L2, q1, e, S);
+                });
+            }
+            wv = e;
+            if (P->correction == RLSQ_CORR_DENSE) {
+                T* w = F.vm[3].p;
+                RecScope rs(P, RLSQ_KCLASS_VEC, sizeof(T) * (double)m2 * (m2 + 2), st);
+                k_dense_gemv<T><<<grid_rows(P, m2, 32), kBlock, 0, st>>>(m2, F.sinv.p, e, w, S);
+                wv = w;
+            }
+        }
+        T* f = F.vn[3].p;
+        T* y = F.vn[4].p;
+        {
+            RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, sizeof(T), sizeof(T)), st);
+            with_G(P->map.G_L2t, [&](auto g) {
+                k_csr_mv<T, decltype(g)::value><<<gl2t, kBlock, 0, st>>>(L2t, wv, f, S);
+            });
+        }
+        launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{f, nullptr, nullptr}, y, slot++, S, st);   // L1^{-T} Y^T w
+        launch_trsv<T>(P, F, 0, RHS_SUB, Rhs<T>{g2, y, nullptr}, g4, slot++, S, st);       // L1^{-1}(g2 - .)
+    } else {
+        launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{g2, nullptr, nullptr}, g4, slot++, S, st);
+    }
+    T* g5 = F.vn[2].p;
+    launch_trsv<T>(P, F, 2, RHS_VEC, Rhs<T>{g4, nullptr, nullptr}, g5, slot++, S, st);    // U^{-1}
+    RecScope rs(P, RLSQ_KCLASS_FINISH, (2.0 * sizeof(T) + 16.0) * n, st);
+    k_finish_apply<T, INIT><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, F.d.p, g5, s, P->t.p, S,
+                                                                   P->part.p, P->counter.p);
+}
+
+template <bool INIT>
+static void enqueue_identity_apply(rlsq_problem_s* P, const double* s, LsmrState* S, cudaStream_t st) {
+    // M = I: t = s (the unpreconditioned baseline)
+    const int n = static_cast<int>(P->n);
+    RecScope rs(P, RLSQ_KCLASS_FINISH, 24.0 * n, st);
+    k_finish_apply<double, INIT, true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, nullptr, s, s, P->t.p, S,
+                                                                              P->part.p, P->counter.p);
+}
+
+template <bool INIT>
+static void enqueue_apply_any(rlsq_problem_s* P, const double* s, LsmrState* S, cudaStream_t st,
+                              bool plain) {
+    if (plain) {
+        enqueue_identity_apply<INIT>(P, s, S, st);
+    } else if (P->precision == RLSQ_PREC_FP32) {
+        enqueue_apply<float, INIT>(P, P->f32, s, S, st);
+    } else {
+        enqueue_apply<double, INIT>(P, P->f64, s, S, st);
+    }
+}
+
+static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
+    const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
+    {
+        RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 16.0, 32.0), st);
+        with_G(P->map.G_A, [&](auto g) {
+            k_spmv_lsmr<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
+                P->dA.view(), P->t.p, P->x.p, P->q.p, P->b.p, P->r.p, S, P->part.p, P->counter.p);
+        });
+    }
+    {
+        RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 16.0, 16.0), st);
+        with_G(P->map.G_At, [&](auto g) {
+            k_spmvt_lsmr<decltype(g)::value, false>
+                <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->q.p, P->r.p, P->s.p,
+                                                                        S, P->part.p, P->counter.p);
+        });
+    }
+    enqueue_apply_any<false>(P, P->s.p, S, st, plain);
+    RecScope rs(P, RLSQ_KCLASS_UPDATE, 56.0 * n, st);
+    k_lsmr_update<false><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->t.p, P->h.p, P->hb.p, P->x.p, S);
+}
+
+static void enqueue_start(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
+    const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
+    k_start_b<0><<<grid_rows(P, m, 1), kBlock, 0, st>>>(m, P->b.p, P->q.p, S, P->part.p, P->counter.p);
+    with_G(P->map.G_At, [&](auto g) {
+        k_spmvt_lsmr<decltype(g)::value, true>
+            <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->q.p, P->r.p, P->s.p,
+                                                                    S, P->part.p, P->counter.p);
+    });
+    enqueue_apply_any<true>(P, P->s.p, S, st, plain);
+    k_lsmr_update<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->t.p, P->h.p, P->hb.p, P->x.p, S);
+}
+
+static LsmrState initial_state(const rlsq_problem_s* P, double atol, int maxit) {
+    LsmrState s;
+    std::memset(&s, 0, sizeof(s));
+    s.anorm = P->anorm;
+    s.atol = atol;
+    s.maxit = maxit;
+    s.rho = s.rhobar = s.cbar = 1.0;
+    return s;
+}
+
+static void put_state(rlsq_problem_s* P, LsmrState* S, const LsmrState& h, cudaStream_t st) {
+    *P->pinned_state = h;
+    RLSQ_CUDA(cudaMemcpyAsync(S, P->pinned_state, sizeof(LsmrState), cudaMemcpyHostToDevice, st));
+    RLSQ_CUDA(cudaStreamSynchronize(st));
+}
+
+static void drop_graphs(rlsq_problem_s* P) {
+    for (int i = 0; i < 2; ++i) {
+        if (P->graph[i]) cudaGraphExecDestroy(P->graph[i]);
+        P->graph[i] = nullptr;
+        P->graph_iters[i] = 0;
+    }
+}
+
+static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain) {
+    const int gi = plain ? 1 : 0;
+    if (P->graph[gi] && P->graph_iters[gi] == iters) return P->graph[gi];
+    if (P->graph[gi]) cudaGraphExecDestroy(P->graph[gi]);
+    P->graph[gi] = nullptr;
+    cudaStream_t st = P->stream;
+    LsmrState* S = state_ptr(P, 0);
+    RLSQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int i = 0; i < iters; ++i) enqueue_iteration(P, S, st, plain);
+    } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(st, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    cudaGraph_t g = nullptr;
+    RLSQ_CUDA(cudaStreamEndCapture(st, &g));
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw_cuda(e, "cudaGraphInstantiate", __LINE__);
+    P->graph[gi] = ex;
+    P->graph_iters[gi] = iters;
+    return ex;
+}
+
+static double algorithmic_bytes(const rlsq_problem_s* P, bool plain) {
+    const double m = static_cast<double>(P->m), n = static_cast<double>(P->n);
+    double bytes = 2.0 * 12.0 * static_cast<double>(P->nnz) + 4.0 * (m + n);  // A, A^T: values, indices, pointers
+    bytes += 8.0 * (2 * n + 4 * m);   // SpMV: gathers of v^ and x, q in/out, b in, r out
+    bytes += 8.0 * (2 * m + 2 * n);   // SpMV^T: gathers of u and r, s in/out
+    bytes += 8.0 * 7 * n;             // LSMR update: t, h, h-bar, x in; h, h-bar, x out
+    if (plain || !P->F) return bytes + 8.0 * 3 * n;
+    const IlupResult& F = *P->F;
+    const double wv = (P->precision == RLSQ_PREC_FP32) ? 4.0 : 8.0;
+    const double wf = wv + 4.0;
+    const double m2 = m - n;
+    auto tri = [&](const HostCSR& a) { return wf * a.nnz() + 8.0 * n + 3.0 * wv * n; };
+    auto l2 = [&](const HostCSR& a) { return wf * a.nnz() + 4.0 * a.rows + wv * (a.rows + a.cols); };
+    const int k = P->opts.cg_steps;
+    double ap = tri(F.Ut) + tri(F.L1t) + tri(F.L1) + tri(F.U) + 8.0 * n + wv * n + 2 * 8.0 * n;
+    if (P->correction != RLSQ_CORR_NONE) {
+        ap += tri(F.L1) + tri(F.L1t) + l2(F.L2) + l2(F.L2t);
+        if (P->correction == RLSQ_CORR_CG) {
+            ap += k * (tri(F.L1) + tri(F.L1t) + l2(F.L2) + l2(F.L2t));
+            ap += k * wv * (3 * m2 + 5 * m2);  // p, Sp, r, w traffic of the CG steps
+        } else if (P->correction == RLSQ_CORR_DENSE) {
+            ap += wv * m2 * m2;
+        }
+    }
+    return bytes + ap;
+}
+
+static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
+    info->m = P->m;
+    info->n = P->n;
+    info->nnz_A = P->nnz;
+    info->anorm = P->anorm;
+    info->correction = P->correction;
+    info->precision = P->precision;
+    info->factor_seconds = P->factor_seconds;
+    if (P->F) {
+        const IlupResult& F = *P->F;
+        info->nnz_L1 = F.L1.nnz();
+        info->nnz_L2 = F.L2.nnz();
+        info->nnz_U = F.U.nnz() + F.n;
+        info->nmod = F.nmod;
+        info->levels_L1 = F.lev_L1.nlevels;
+        info->levels_L1t = F.lev_L1t.nlevels;
+        info->levels_U = F.lev_U.nlevels;
+        info->levels_Ut = F.lev_Ut.nlevels;
+    }
+    info->bytes_per_iter = algorithmic_bytes(P, !P->factored);
+}
+
+// Moves b in, runs LSMR, moves x out.
+static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_solve_opts* o,
+                     rlsq_info* info, bool plain) {
+    const auto t0 = std::chrono::steady_clock::now();
+    rlsq_solve_opts opts;
+    rlsq_solve_opts_default(&opts);
+    if (o) opts = *o;
+    if (!b || !x) throw ApiError(RLSQ_ERR_ARG, "null b or x");
+    if (!(opts.atol >= 0.0) || opts.maxit < 0) throw ApiError(RLSQ_ERR_ARG, "bad atol or maxit");
+    if (!plain && !P->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+    const int iters = std::max(1, opts.check_every);
+    cudaStream_t st = P->stream;
+    cudaStream_t user = static_cast<cudaStream_t>(opts.stream);
+    const bool dev = opts.ptr_mode == RLSQ_DEVICE_PTRS;
+    if (dev) {
+        RLSQ_CUDA(cudaEventRecord(P->ev[0], user));
+        RLSQ_CUDA(cudaStreamWaitEvent(st, P->ev[0], 0));
+    }
+    RLSQ_CUDA(cudaMemcpyAsync(P->b.p, b, sizeof(double) * P->m,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    LsmrState* S = state_ptr(P, 0);
+    put_state(P, S, initial_state(P, opts.atol, opts.maxit), st);
+    if (!plain) RLSQ_CUDA(cudaMemsetAsync(P->flags.p, 0, sizeof(int) * P->n, st));
+    enqueue_start(P, S, st, plain);
+    cudaGraphExec_t g = iteration_graph(P, iters, plain);
+    const int64_t max_launches = static_cast<int64_t>(opts.maxit) / iters + 4;
+    int64_t launches = 0;
+    // two graphs in flight; read `done` of the older one
+    int* done = P->pinned_done;
+    done[0] = done[1] = 0;
+    RLSQ_CUDA(cudaGraphLaunch(g, st));
+    RLSQ_CUDA(cudaMemcpyAsync(&done[0], reinterpret_cast<char*>(S) + offsetof(LsmrState, done), sizeof(int),
+                              cudaMemcpyDeviceToHost, st));
+    RLSQ_CUDA(cudaEventRecord(P->ev[0], st));
+    ++launches;
+    int cur = 0;
+    for (;;) {
+        const int nxt = cur ^ 1;
+        RLSQ_CUDA(cudaGraphLaunch(g, st));
+        RLSQ_CUDA(cudaMemcpyAsync(&done[nxt], reinterpret_cast<char*>(S) + offsetof(LsmrState, done),
+                                  sizeof(int), cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaEventRecord(P->ev[nxt], st));
+        ++launches;
+        RLSQ_CUDA(cudaEventSynchronize(P->ev[cur]));
+        if (done[cur]) break;
+        if (launches > max_launches) break;
+        cur = nxt;
+    }
+    RLSQ_CUDA(cudaStreamSynchronize(st));
+    LsmrState hs;
+    RLSQ_CUDA(cudaMemcpy(&hs, S, sizeof(LsmrState), cudaMemcpyDeviceToHost));
+    if (!hs.done) throw ApiError(RLSQ_ERR_CUDA, "solver did not reach a stopping point");
+    RLSQ_CUDA(cudaMemcpyAsync(x, P->x.p, sizeof(double) * P->n,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    RLSQ_CUDA(cudaStreamSynchronize(st));
+    if (dev) {
+        RLSQ_CUDA(cudaEventRecord(P->ev[0], st));
+        RLSQ_CUDA(cudaStreamWaitEvent(user, P->ev[0], 0));
+    }
+    int status = hs.status;
+    if (hs.error != 0) status = RLSQ_ERR_DEVICE_TIMEOUT;
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        fill_factor_info(P, info);
+        if (plain) {
+            info->correction = -1;
+            info->bytes_per_iter = algorithmic_bytes(P, true);
+        }
+        info->status = status;
+        info->iterations = hs.k;
+        info->ratio = hs.ratio;
+        info->rnorm = hs.rnorm;
+        info->arnorm = hs.arnorm;
+        info->solve_seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status == RLSQ_ERR_BREAKDOWN) set_last_error("<s, M^{-1} s> <= 0: preconditioner not positive");
+    else if (status == RLSQ_ERR_MAXIT) set_last_error("iteration limit reached");
+    else if (status == RLSQ_ERR_DEVICE_TIMEOUT) set_last_error("a sync-free triangular solve timed out");
+    return status;
+}
+
+// ||A||_2 by 50 power iterations on A^T A from v = 1/sqrt(n) (Sec. 5.1)
+static double power_norm(rlsq_problem_s* P, int iters) {
+    cudaStream_t st = P->stream;
+    const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
+    DevArray<double> v, y;
+    DevArray<PowerState> ps;
+    v.alloc(n);
+    y.alloc(m);
+    ps.alloc(1);
+    std::vector<double> v0(static_cast<size_t>(n), 1.0 / std::sqrt(static_cast<double>(n)));
+    RLSQ_CUDA(cudaMemcpyAsync(v.p, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    PowerState p0{0.0, 1.0};
+    RLSQ_CUDA(cudaMemcpyAsync(ps.p, &p0, sizeof(p0), cudaMemcpyHostToDevice, st));
+    for (int it = 0; it < iters; ++it) {
+        with_G(P->map.G_A, [&](auto g) {
+            k_power_av<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
+                P->dA.view(), v.p, y.p, ps.p);
+        });
+        with_G(P->map.G_At, [&](auto g) {
+            k_power_atv<decltype(g)::value><<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(
+                P->dAt.view(), y.p, v.p, ps.p, P->part.p, P->counter.p);
+        });
+    }
+    PowerState out;
+    RLSQ_CUDA(cudaMemcpyAsync(&out, ps.p, sizeof(out), cudaMemcpyDeviceToHost, st));
+    RLSQ_CUDA(cudaStreamSynchronize(st));
+    return std::sqrt(out.lambda);
+}
+
+static int pow2_lanes(double avg, int lo, int hi) {
+    int g = lo;
+    while (g < hi && g < avg) g *= 2;
+    return g;
+}
+
+void default_mapping(rlsq_problem_s* P) {
+    const double m = static_cast<double>(P->m), n = static_cast<double>(P->n);
+    P->map.G_A = pow2_lanes(P->nnz / m, 2, 32);
+    P->map.G_At = pow2_lanes(P->nnz / n, 2, 32);
+    if (P->F) {
+        const IlupResult& F = *P->F;
+        const HostCSR* parts[4] = {&F.L1, &F.L1t, &F.U, &F.Ut};
+        for (int w = 0; w < 4; ++w) {
+            P->map.G_tri[w] = pow2_lanes(parts[w]->nnz() / std::max(1.0, n), 2, 32);
+            P->map.sched[w] = RLSQ_TRSV_SYNCFREE;
+        }
+        P->map.G_L2 = pow2_lanes(F.L2.nnz() / std::max(1.0, m - n), 2, 32);
+        P->map.G_L2t = pow2_lanes(F.L2t.nnz() / std::max(1.0, n), 2, 32);
+    }
+}
+
+void autotune(rlsq_problem_s* P);  // autotune.cu
+
+// Times one standalone solve of system `which` with the current mapping
+// (used by the autotuner); inputs in vn[3], output in vn[4].
+int rlsq_trsv_time(rlsq_problem_s* P, int which, float* ms) {
+    cudaStream_t st = P->stream;
+    LsmrState* S = state_ptr(P, 1);
+    put_state(P, S, initial_state(P, 0.0, 0), st);
+    cudaEvent_t a, b;
+    RLSQ_CUDA(cudaEventCreate(&a));
+    RLSQ_CUDA(cudaEventCreate(&b));
+    const int n = static_cast<int>(P->n);
+    auto body = [&]() {
+        RLSQ_CUDA(cudaMemsetAsync(P->flags.p, 0, sizeof(int) * n, st));
+        RLSQ_CUDA(cudaMemsetAsync(P->tickets.p, 0, sizeof(unsigned) * kMaxSlots, st));
+        if (P->precision == RLSQ_PREC_FP32)
+            launch_trsv<float>(P, P->f32, which, RHS_VEC, Rhs<float>{P->f32.vn[3].p, nullptr, nullptr},
+                               P->f32.vn[4].p, 0, S, st);
+        else
+            launch_trsv<double>(P, P->f64, which, RHS_VEC, Rhs<double>{P->f64.vn[3].p, nullptr, nullptr},
+                                P->f64.vn[4].p, 0, S, st);
+        RLSQ_CUDA(cudaGetLastError());
+    };
+    body();
+    std::vector<float> ts;
+    for (int i = 0; i < 5; ++i) {
+        RLSQ_CUDA(cudaEventRecord(a, st));
+        body();
+        RLSQ_CUDA(cudaEventRecord(b, st));
+        RLSQ_CUDA(cudaEventSynchronize(b));
+        float t = 0.f;
+        RLSQ_CUDA(cudaEventElapsedTime(&t, a, b));
+        ts.push_back(t);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    RLSQ_CUDA(cudaMemcpy(P->pinned_state, S, sizeof(LsmrState), cudaMemcpyDeviceToHost));
+    if (P->pinned_state->error) return RLSQ_ERR_DEVICE_TIMEOUT;
+    std::sort(ts.begin(), ts.end());
+    *ms = ts[ts.size() / 2];
+    return RLSQ_OK;
+}
+
+
+}  // namespace rlsq
+
+using namespace rlsq;
+
+rlsq_problem_s::~rlsq_problem_s() {
+    drop_graphs(this);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (pinned_state) cudaFreeHost(pinned_state);
+    if (pinned_done) cudaFreeHost(pinned_done);
+    if (stream) cudaStreamDestroy(stream);
+}
+
+extern "C" {
+
+void rlsq_factor_opts_default(rlsq_factor_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->p = 10;
+    o->tau = 1e-2;
+    o->mu = 0.1;
+    o->small = 1e-10;
+    o->scale_columns = 1;
+    o->correction = RLSQ_CORR_AUTO;
+    o->cg_steps = 2;
+    o->dense_cap = 1024;
+    o->precision = RLSQ_PREC_FP64;
+    o->trsv_schedule = RLSQ_TRSV_AUTO;
+    o->autotune = 0;
+    o->dense_row_min = 0;
+    o->host_threads = 0;
+}
+
+void rlsq_solve_opts_default(rlsq_solve_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->atol = 1e-8;
+    o->maxit = 2000;
+    o->ptr_mode = RLSQ_HOST_PTRS;
+    o->stream = nullptr;
+    o->check_every = 8;
+}
+
+const char* rlsq_last_error(void) { return g_last_error.c_str(); }
+
+int rlsq_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* vals,
+                int32_t ptr_mode, void* stream, rlsq_problem* out) {
+    return guarded([&]() -> int {
+        if (!out || !rowptr || (!colidx && m > 0) || (!vals && m > 0))
+            throw ApiError(RLSQ_ERR_ARG, "null argument");
+        *out = nullptr;
+        if (!(m > n && n > 0)) throw ApiError(RLSQ_ERR_SHAPE, "need m > n > 0");
+        if (m >= (int64_t(1) << 31)) throw ApiError(RLSQ_ERR_SHAPE, "m must be < 2^31");
+        std::unique_ptr<rlsq_problem_s> P(new rlsq_problem_s());
+        P->m = m;
+        P->n = n;
+        HostCSR& A = P->A;
+        A.rows = m;
+        A.cols = n;
+        A.ptr.resize(static_cast<size_t>(m) + 1);
+        const bool dev = ptr_mode == RLSQ_DEVICE_PTRS;
+        cudaStream_t user = static_cast<cudaStream_t>(stream);
+        if (dev) {
+            RLSQ_CUDA(cudaMemcpyAsync(A.ptr.data(), rowptr, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost, user));
+            RLSQ_CUDA(cudaStreamSynchronize(user));
+        } else {
+            std::memcpy(A.ptr.data(), rowptr, sizeof(int64_t) * (m + 1));
+        }
+        if (A.ptr[0] != 0) throw ApiError(RLSQ_ERR_CSR, "rowptr[0] must be 0");
+        for (int64_t i = 0; i < m; ++i)
+            if (A.ptr[i + 1] < A.ptr[i]) throw ApiError(RLSQ_ERR_CSR, "rowptr must be nondecreasing");
+        const int64_t nnz = A.ptr[m];
+        if (nnz >= (int64_t(1) << 31)) throw ApiError(RLSQ_ERR_SHAPE, "nnz must be < 2^31");
+        A.idx.resize(static_cast<size_t>(nnz));
+        A.val.resize(static_cast<size_t>(nnz));
+        if (dev) {
+            RLSQ_CUDA(cudaMemcpyAsync(A.idx.data(), colidx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, user));
+            RLSQ_CUDA(cudaMemcpyAsync(A.val.data(), vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost, user));
+            RLSQ_CUDA(cudaStreamSynchronize(user));
+        } else {
+            std::memcpy(A.idx.data(), colidx, sizeof(int32_t) * nnz);
+            std::memcpy(A.val.data(), vals, sizeof(double) * nnz);
+        }
+        std::vector<char> seen(static_cast<size_t>(n), 0);
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+                const int32_t c = A.idx[e];
+                if (c < 0 || c >= n) throw ApiError(RLSQ_ERR_CSR, "column index out of range");
+                if (e > A.ptr[i] && c <= A.idx[e - 1])
+                    throw ApiError(RLSQ_ERR_CSR, "column indices must be strictly increasing within a row");
+                if (!std::isfinite(A.val[e])) throw ApiError(RLSQ_ERR_CSR, "non-finite value");
+                if (A.val[e] != 0.0) seen[c] = 1;
+            }
+        for (int64_t j = 0; j < n; ++j)
+            if (!seen[j]) throw ApiError(RLSQ_ERR_RANK, "column " + std::to_string(j) + " is empty");
+        P->nnz = nnz;
+        RLSQ_CUDA(cudaGetDevice(&P->device));
+        RLSQ_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+        RLSQ_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+        RLSQ_CUDA(cudaEventCreateWithFlags(&P->ev[0], cudaEventDisableTiming));
+        RLSQ_CUDA(cudaEventCreateWithFlags(&P->ev[1], cudaEventDisableTiming));
+        RLSQ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&P->pinned_state), sizeof(LsmrState)));
+        RLSQ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&P->pinned_done), 2 * sizeof(int)));
+        cudaStream_t st = P->stream;
+        P->dA.upload(A, st);
+        P->dAt.upload(transpose(A), st);
+        for (auto* v : {&P->q, &P->r, &P->b}) v->alloc(static_cast<size_t>(m));
+        for (auto* v : {&P->s, &P->t, &P->h, &P->hb, &P->x}) v->alloc(static_cast<size_t>(n));
+        P->S.alloc(2);
+        P->part.alloc(static_cast<size_t>(max_grid(P.get())) * 2);
+        P->counter.alloc(1);
+        RLSQ_CUDA(cudaMemsetAsync(P->counter.p, 0, sizeof(unsigned), st));
+        P->tickets.alloc(kMaxSlots);
+        P->flags.alloc(static_cast<size_t>(n));
+        default_mapping(P.get());
+        P->anorm = power_norm(P.get(), 50);
+        *out = P.release();
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
+    return guarded([&]() -> int {
+        if (!h) throw ApiError(RLSQ_ERR_ARG, "null handle");
+        rlsq_factor_opts opts;
+        rlsq_factor_opts_default(&opts);
+        if (o) opts = *o;
+        if (!(opts.mu > 0.0 && opts.mu <= 1.0) || !(opts.tau >= 0.0) || !(opts.small > 0.0) ||
+            opts.cg_steps < 1 || opts.correction < 0 || opts.correction > RLSQ_CORR_AUTO ||
+            (opts.precision != RLSQ_PREC_FP64 && opts.precision != RLSQ_PREC_FP32))
+            throw ApiError(RLSQ_ERR_ARG, "bad factor option");
+        if (opts.cg_steps > 16) throw ApiError(RLSQ_ERR_ARG, "cg_steps must be <= 16");
+        const auto t0 = std::chrono::steady_clock::now();
+        h->factored = false;
+        drop_graphs(h);
+        IlupParams prm;
+        prm.p = opts.p;
+        prm.tau = opts.tau;
+        prm.mu = opts.mu;
+        prm.small = opts.small;
+        prm.scale = opts.scale_columns != 0;
+        std::unique_ptr<IlupResult> F;
+        try {
+            F.reset(new IlupResult(ilup_factor(h->A, prm)));
+        } catch (const std::runtime_error& e) {
+            throw ApiError(RLSQ_ERR_RANK, e.what());
+        }
+        int corr = opts.correction;
+        const int64_t m2 = h->m - h->n;
+        if (corr == RLSQ_CORR_AUTO) corr = (m2 <= opts.dense_cap) ? RLSQ_CORR_DENSE : RLSQ_CORR_CG;
+        std::vector<double> sinv;
+        if (corr == RLSQ_CORR_DENSE) {
+            int th = opts.host_threads > 0 ? opts.host_threads
+                                           : static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+            if (!dense_schur_inverse(*F, sinv, th))
+                throw ApiError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
+        }
+        cudaStream_t st = h->stream;
+        h->f64.clear();
+        h->f32.clear();
+        if (opts.precision == RLSQ_PREC_FP32) h->f32.upload(*F, sinv, st);
+        else h->f64.upload(*F, sinv, st);
+        h->F = std::move(F);
+        h->opts = opts;
+        h->correction = corr;
+        h->precision = opts.precision;
+        default_mapping(h);
+        if (opts.trsv_schedule == RLSQ_TRSV_LEVEL || opts.trsv_schedule == RLSQ_TRSV_SYNCFREE)
+            for (int w = 0; w < 4; ++w) h->map.sched[w] = opts.trsv_schedule;
+        h->factored = true;
+        if (opts.autotune) autotune(h);
+        h->factor_seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_solve(rlsq_problem h, const double* b, double* x, const rlsq_solve_opts* opts, rlsq_info* info) {
+    return guarded([&]() -> int {
+        if (!h) throw ApiError(RLSQ_ERR_ARG, "null handle");
+        return run_solve(h, b, x, opts, info, false);
+    });
+}
+
+int rlsq_solve_plain(rlsq_problem h, const double* b, double* x, const rlsq_solve_opts* opts,
+                     rlsq_info* info) {
+    return guarded([&]() -> int {
+        if (!h) throw ApiError(RLSQ_ERR_ARG, "null handle");
+        return run_solve(h, b, x, opts, info, true);
+    });
+}
+
+int rlsq_apply(rlsq_problem h, const double* s, double* t, int32_t ptr_mode, void* stream) {
+    return guarded([&]() -> int {
+        if (!h || !s || !t) throw ApiError(RLSQ_ERR_ARG, "null argument");
+        if (!h->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        cudaStream_t st = h->stream;
+        const bool dev = ptr_mode == RLSQ_DEVICE_PTRS;
+        cudaStream_t user = static_cast<cudaStream_t>(stream);
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], user));
+            RLSQ_CUDA(cudaStreamWaitEvent(st, h->ev[0], 0));
+        }
+        LsmrState* S = state_ptr(h, 1);
+        put_state(h, S, initial_state(h, 0.0, 0), st);
+        RLSQ_CUDA(cudaMemcpyAsync(h->s.p, s, sizeof(double) * h->n,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        RLSQ_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * h->n, st));
+        enqueue_apply_any<true>(h, h->s.p, S, st, false);
+        LsmrState hs;
+        RLSQ_CUDA(cudaMemcpyAsync(h->pinned_state, S, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaMemcpyAsync(t, h->t.p, sizeof(double) * h->n,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaStreamSynchronize(st));
+        hs = *h->pinned_state;
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], st));
+            RLSQ_CUDA(cudaStreamWaitEvent(user, h->ev[0], 0));
+        }
+        if (hs.error) throw ApiError(RLSQ_ERR_DEVICE_TIMEOUT, "a sync-free triangular solve timed out");
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_matvec(rlsq_problem h, int32_t trans, const double* x, double* y, int32_t ptr_mode, void* stream) {
+    return guarded([&]() -> int {
+        if (!h || !x || !y) throw ApiError(RLSQ_ERR_ARG, "null argument");
+        cudaStream_t st = h->stream;
+        const bool dev = ptr_mode == RLSQ_DEVICE_PTRS;
+        cudaStream_t user = static_cast<cudaStream_t>(stream);
+        const int64_t nin = trans ? h->m : h->n, nout = trans ? h->n : h->m;
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], user));
+            RLSQ_CUDA(cudaStreamWaitEvent(st, h->ev[0], 0));
+        }
+        double* in = trans ? h->r.p : h->s.p;
+        double* outv = trans ? h->s.p : h->r.p;
+        RLSQ_CUDA(cudaMemcpyAsync(in, x, sizeof(double) * nin,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        const Csr<double> M = trans ? h->dAt.view() : h->dA.view();
+        const int G = trans ? h->map.G_At : h->map.G_A;
+        with_G(G, [&](auto g) {
+            k_csr_mv<double, decltype(g)::value><<<grid_rows(h, nout, decltype(g)::value), kBlock, 0, st>>>(
+                M, in, outv, nullptr);
+        });
+        RLSQ_CUDA(cudaGetLastError());
+        RLSQ_CUDA(cudaMemcpyAsync(y, outv, sizeof(double) * nout,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaStreamSynchronize(st));
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], st));
+            RLSQ_CUDA(cudaStreamWaitEvent(user, h->ev[0], 0));
+        }
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_trsv(rlsq_problem h, int32_t which, const double* b, double* x, int32_t ptr_mode, void* stream) {
+    return guarded([&]() -> int {
+        if (!h || !b || !x) throw ApiError(RLSQ_ERR_ARG, "null argument");
+        if (which < 0 || which > 3) throw ApiError(RLSQ_ERR_ARG, "bad system id");
+        if (!h->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        cudaStream_t st = h->stream;
+        const bool dev = ptr_mode == RLSQ_DEVICE_PTRS;
+        cudaStream_t user = static_cast<cudaStream_t>(stream);
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], user));
+            RLSQ_CUDA(cudaStreamWaitEvent(st, h->ev[0], 0));
+        }
+        const int n = static_cast<int>(h->n);
+        LsmrState* S = state_ptr(h, 1);
+        put_state(h, S, initial_state(h, 0.0, 0), st);
+        RLSQ_CUDA(cudaMemcpyAsync(h->s.p, b, sizeof(double) * n,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        RLSQ_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * n, st));
+        RLSQ_CUDA(cudaMemsetAsync(h->tickets.p, 0, sizeof(unsigned) * kMaxSlots, st));
+        const int grid = grid_rows(h, n, 1);
+        if (h->precision == RLSQ_PREC_FP32) {
+            DevFactor<float>& F = h->f32;
+            k_convert<float, double><<<grid, kBlock, 0, st>>>(n, h->s.p, F.vn[3].p);
+            launch_trsv<float>(h, F, which, RHS_VEC, Rhs<float>{F.vn[3].p, nullptr, nullptr}, F.vn[4].p, 0,
+                               S, st);
+            k_convert<double, float><<<grid, kBlock, 0, st>>>(n, F.vn[4].p, h->t.p);
+        } else {
+            DevFactor<double>& F = h->f64;
+            launch_trsv<double>(h, F, which, RHS_VEC, Rhs<double>{h->s.p, nullptr, nullptr}, h->t.p, 0, S, st);
+        }
+        RLSQ_CUDA(cudaGetLastError());
+        RLSQ_CUDA(cudaMemcpyAsync(h->pinned_state, S, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaMemcpyAsync(x, h->t.p, sizeof(double) * n,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaStreamSynchronize(st));
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], st));
+            RLSQ_CUDA(cudaStreamWaitEvent(user, h->ev[0], 0));
+        }
+        if (h->pinned_state->error)
+            throw ApiError(RLSQ_ERR_DEVICE_TIMEOUT, "a sync-free triangular solve timed out");
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_profile(rlsq_problem h, const double* b, int32_t warmup, int32_t iters, int32_t plain,
+                 rlsq_profile_out* out) {
+    return guarded([&]() -> int {
+        if (!h || !b || !out || iters < 1 || warmup < 0) throw ApiError(RLSQ_ERR_ARG, "bad argument");
+        if (!plain && !h->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        std::memset(out, 0, sizeof(*out));
+        cudaStream_t st = h->stream;
+        LsmrState* S = state_ptr(h, 0);
+        const int big = 1 << 30;
+        RLSQ_CUDA(cudaMemcpyAsync(h->b.p, b, sizeof(double) * h->m, cudaMemcpyHostToDevice, st));
+        put_state(h, S, initial_state(h, 0.0, big), st);
+        RLSQ_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * h->n, st));
+        enqueue_start(h, S, st, plain != 0);
+        cudaGraphExec_t g1 = iteration_graph(h, 1, plain != 0);
+        for (int i = 0; i < warmup; ++i) RLSQ_CUDA(cudaGraphLaunch(g1, st));
+        cudaEvent_t a, e;
+        RLSQ_CUDA(cudaEventCreate(&a));
+        RLSQ_CUDA(cudaEventCreate(&e));
+        RLSQ_CUDA(cudaStreamSynchronize(st));
+        RLSQ_CUDA(cudaEventRecord(a, st));
+        for (int i = 0; i < iters; ++i) RLSQ_CUDA(cudaGraphLaunch(g1, st));
+        RLSQ_CUDA(cudaEventRecord(e, st));
+        RLSQ_CUDA(cudaEventSynchronize(e));
+        float ms = 0.f;
+        RLSQ_CUDA(cudaEventElapsedTime(&ms, a, e));
+        cudaEventDestroy(a);
+        cudaEventDestroy(e);
+        out->total_ms = ms;
+        out->iters = iters;
+        // one eager iteration with an event pair around every launch
+        std::unique_ptr<Recorder> rec(new Recorder());
+        h->rec = rec.get();
+        try {
+            enqueue_iteration(h, S, st, plain != 0);
+        } catch (...) {
+            h->rec = nullptr;
+            throw;
+        }
+        h->rec = nullptr;
+        RLSQ_CUDA(cudaStreamSynchronize(st));
+        for (auto& en : rec->entries) {
+            float t = 0.f;
+            RLSQ_CUDA(cudaEventElapsedTime(&t, en.a, en.b));
+            out->class_ms[en.cls] += t;
+            out->class_launches[en.cls] += 1;
+            out->class_bytes[en.cls] += en.bytes;
+        }
+        LsmrState hs;
+        RLSQ_CUDA(cudaMemcpy(&hs, S, sizeof(LsmrState), cudaMemcpyDeviceToHost));
+        out->status = hs.done ? (hs.error ? RLSQ_ERR_DEVICE_TIMEOUT : hs.status) : RLSQ_OK;
+        out->bytes_per_iter = algorithmic_bytes(h, plain != 0);
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_get_info(rlsq_problem h, rlsq_info* info) {
+    return guarded([&]() -> int {
+        if (!h || !info) throw ApiError(RLSQ_ERR_ARG, "null argument");
+        std::memset(info, 0, sizeof(*info));
+        fill_factor_info(h, info);
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_get_split(rlsq_problem h, int32_t* prow, int32_t* a2rows, double* d, double* udiag) {
+    return guarded([&]() -> int {
+        if (!h) throw ApiError(RLSQ_ERR_ARG, "null handle");
+        if (!h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        const IlupResult& F = *h->F;
+        if (prow) std::copy(F.prow.begin(), F.prow.end(), prow);
+        if (a2rows) std::copy(F.a2rows.begin(), F.a2rows.end(), a2rows);
+        if (d) std::copy(F.d.begin(), F.d.end(), d);
+        if (udiag) std::copy(F.Udiag.begin(), F.Udiag.end(), udiag);
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_get_factor(rlsq_problem h, int32_t part, int64_t* ptr, int32_t* idx, double* val) {
+    return guarded([&]() -> int {
+        if (!h) throw ApiError(RLSQ_ERR_ARG, "null handle");
+        if (!h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        const IlupResult& F = *h->F;
+        const HostCSR* c = nullptr;
+        if (part == RLSQ_PART_L1) c = &F.L1;
+        else if (part == RLSQ_PART_L2) c = &F.L2;
+        else if (part == RLSQ_PART_U) c = &F.U;
+        else throw ApiError(RLSQ_ERR_ARG, "bad part id");
+        if (ptr) std::copy(c->ptr.begin(), c->ptr.end(), ptr);
+        if (idx) std::copy(c->idx.begin(), c->idx.end(), idx);
+        if (val) std::copy(c->val.begin(), c->val.end(), val);
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_get_levels(rlsq_problem h, int32_t which, int32_t* level) {
+    return guarded([&]() -> int {
+        if (!h || !level) throw ApiError(RLSQ_ERR_ARG, "null argument");
+        if (!h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        const IlupResult& F = *h->F;
+        const Levels* L = nullptr;
+        switch (which) {
+            case RLSQ_SYS_L1: L = &F.lev_L1; break;
+            case RLSQ_SYS_L1T: L = &F.lev_L1t; break;
+            case RLSQ_SYS_U: L = &F.lev_U; break;
+            case RLSQ_SYS_UT: L = &F.lev_Ut; break;
+            default: throw ApiError(RLSQ_ERR_ARG, "bad system id");
+        }
+        std::copy(L->level.begin(), L->level.end(), level);
+        return RLSQ_OK;
+    });
+}
+
+void rlsq_destroy(rlsq_problem h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+"""GPU parity: every kernel of the path, called through the C ABI, against the
+CPU oracle on the same seeded inputs.
+
+Tolerances (float64):
+  * SpMV / SpMV^T: |y - y_ref| <= 1e-13 (|A| |x|)_i  (reordered sums of <= ~20 terms)
+  * each triangular solve and one full preconditioner application: relative
+    2-norm error <= 1e-12
+  * solves: x within 1e-6 relative of the oracle's x, iteration count equal
+    (+-1 when the final ratio sits within 1e-3 of the threshold)
+float32 apply: the error against the float64 oracle is measured and bounded
+by 1e-3 relative (float32 unit roundoff 6e-8 times the conditioning of the
+triangular factors); the test prints it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_28642_gb300 import binding as B
+from paper_2603_28642_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MU = 1.0  # workload pivoting threshold (see the design notes on mu = 0.1)
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make(prob, mode=B.CORR_CG, prec=B.PREC_FP64, sched=B.TRSV_AUTO, mu=MU, **kw):
+    P = B.Problem.from_problem(prob)
+    P.factor(mu=mu, correction=mode, precision=prec, trsv_schedule=sched, **kw)
+    return P
+
+
+def oracle_factor(prob, mode=oracle.CG, mu=MU, steps=2, **kw):
+    f = oracle.Factor(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, mu=mu, **kw)
+    f.set_correction(mode, steps)
+    return f
+
+
+MODES = [(B.CORR_NONE, oracle.NONE), (B.CORR_SI, oracle.SI), (B.CORR_CG, oracle.CG),
+         (B.CORR_DENSE, oracle.DENSE)]
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    return synth.config_problem(0)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    # config-1 recipe at 1/20 scale: many tiles, ragged tail
+    return synth.sparse_problem(100_003, 50_001, 8, seed=1, hidden_diag=True)
+
+
+# ---------------------------------------------------------------------------
+# products with A
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["cfg0", "mid"])
+def test_spmv_and_transpose(which, request):
+    prob = request.getfixturevalue(which)
+    P = B.Problem.from_problem(prob)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(prob.n)
+    y = rng.standard_normal(prob.m)
+    A = prob.to_scipy()
+    absA = abs(A)
+    ax = P.matvec(x)
+    ax_ref = oracle.spmv(prob.m, prob.rowptr, prob.colidx, prob.vals, x)
+    assert np.all(np.abs(ax - ax_ref) <= 1e-13 * (absA @ np.abs(x)) + 1e-300)
+    aty = P.matvec(y, trans=True)
+    aty_ref = oracle.spmv_t(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, y)
+    assert np.all(np.abs(aty - aty_ref) <= 1e-13 * (absA.T @ np.abs(y)) + 1e-300)
+    # deterministic: a second call gives the same bits
+    assert np.array_equal(P.matvec(y, trans=True), aty)
+
+
+def test_anorm_matches_oracle(cfg0):
+    P = B.Problem.from_problem(cfg0)
+    ref = oracle.norm2(cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, 50)
+    assert P.info()["anorm"] == pytest.approx(ref, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# structure through the GPU handle (bit-exact)
+# ---------------------------------------------------------------------------
+def test_structure_bitexact(cfg0):
+    P = make(cfg0, B.CORR_NONE)
+    f = oracle_factor(cfg0, oracle.NONE)
+    prow, a2, d, ud = P.split()
+    oprow, oa2 = f.perm()
+    assert np.array_equal(prow, oprow) and np.array_equal(a2, oa2)
+    assert np.array_equal(d, f.scaling())
+    oU, oud = f.U()
+    assert np.array_equal(ud, oud)
+    for part, ref in ((B.PART_L1, f.L1()), (B.PART_L2, f.L2()), (B.PART_U, oU)):
+        ptr, idx, val = P.factor_csr(part)
+        assert np.array_equal(ptr, ref.ptr) and np.array_equal(idx, ref.idx)
+        assert np.array_equal(val, ref.val)
+    lev, _ = oracle.levels(f.L1(), True)
+    assert np.array_equal(P.levels(B.SYS_L1), lev)
+    levu, _ = oracle.levels(oU, False)
+    assert np.array_equal(P.levels(B.SYS_U), levu)
+
+
+# ---------------------------------------------------------------------------
+# triangular solves, both schedules, every lane count
+# ---------------------------------------------------------------------------
+SOLVES = [(B.SYS_L1, "solve_L1"), (B.SYS_L1T, "solve_L1t"), (B.SYS_U, "solve_U"),
+          (B.SYS_UT, "solve_Ut")]
+
+
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL])
+@pytest.mark.parametrize("which", ["cfg0", "mid"])
+def test_triangular_solves(sched, which, request):
+    prob = request.getfixturevalue(which)
+    P = make(prob, B.CORR_NONE, sched=sched)
+    f = oracle_factor(prob, oracle.NONE)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(prob.n)
+    for sys_id, name in SOLVES:
+        x = P.trsv(sys_id, b)
+        ref = getattr(f, name)(b)
+        assert rel(x, ref) <= 1e-12, (sys_id, rel(x, ref))
+
+
+def test_triangular_solves_all_lane_counts(cfg0):
+    """Force every lane count through the autotuner's candidate set by
+    autotuning, then check again (the tuned mapping must stay exact)."""
+    P = make(cfg0, B.CORR_NONE, autotune=1)
+    f = oracle_factor(cfg0, oracle.NONE)
+    b = np.random.default_rng(4).standard_normal(cfg0.n)
+    for sys_id, name in SOLVES:
+        assert rel(P.trsv(sys_id, b), getattr(f, name)(b)) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# one preconditioner application, every correction mode
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("modes", MODES, ids=["NONE", "SI", "CG", "DENSE"])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL])
+def test_apply_fp64(cfg0, modes, sched):
+    bm, om = modes
+    P = make(cfg0, bm, sched=sched)
+    f = oracle_factor(cfg0, om)
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        s = rng.standard_normal(cfg0.n)
+        t = P.apply(s)
+        assert rel(t, f.apply(s)) <= 1e-12
+
+
+@pytest.mark.parametrize("modes", [MODES[0], MODES[2]], ids=["NONE", "CG"])
+def test_apply_fp64_mid(mid, modes):
+    bm, om = modes
+    P = make(mid, bm)
+    f = oracle_factor(mid, om)
+    s = np.random.default_rng(6).standard_normal(mid.n)
+    assert rel(P.apply(s), f.apply(s)) <= 1e-12
+
+
+@pytest.mark.parametrize("modes", MODES, ids=["NONE", "SI", "CG", "DENSE"])
+def test_apply_fp32_error(cfg0, modes):
+    bm, om = modes
+    P = make(cfg0, bm, prec=B.PREC_FP32)
+    f = oracle_factor(cfg0, om)
+    s = np.random.default_rng(7).standard_normal(cfg0.n)
+    err = rel(P.apply(s), f.apply(s))
+    print(f"fp32 apply relative error ({bm}): {err:.3e}")
+    assert err <= 1e-3
+
+
+# ---------------------------------------------------------------------------
+# full solves
+# ---------------------------------------------------------------------------
+def _check_solve(prob, res, ref):
+    info = res.info
+    assert res.status == 0, (B.ERR.get(res.status), info)
+    assert ref.status == 0
+    close = abs(ref.ratio_hist[-1] / 1e-8 - 1) < 1e-3 or abs(info["ratio"] / 1e-8 - 1) < 1e-3
+    if close:
+        assert abs(info["iterations"] - ref.its) <= 1
+    else:
+        assert info["iterations"] == ref.its
+    assert rel(res.x, ref.x) <= 1e-6
+    # stopping quantity recomputed from scratch
+    A = prob.to_scipy()
+    r = prob.b - A @ res.x
+    anorm = info["anorm"]
+    assert np.linalg.norm(A.T @ r) / (anorm * np.linalg.norm(r)) < 1.001e-8
+
+
+@pytest.mark.parametrize("modes", [MODES[0], MODES[2], MODES[3]], ids=["NONE", "CG", "DENSE"])
+def test_solve_cfg0(cfg0, modes):
+    bm, om = modes
+    P = make(cfg0, bm)
+    f = oracle_factor(cfg0, om)
+    ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
+    res = P.solve(cfg0.b)
+    _check_solve(cfg0, res, ref)
+
+
+def test_solve_plain_cfg0(cfg0):
+    P = B.Problem.from_problem(cfg0)
+    ref = oracle.lsmr(None, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
+    res = P.solve(cfg0.b, plain=True)
+    _check_solve(cfg0, res, ref)
+
+
+def test_solve_mid_cg(mid):
+    P = make(mid, B.CORR_CG)
+    f = oracle_factor(mid, oracle.CG)
+    ref = oracle.lsmr(f, mid.m, mid.n, mid.rowptr, mid.colidx, mid.vals, mid.b)
+    res = P.solve(mid.b)
+    _check_solve(mid, res, ref)
+
+
+def test_solve_fp32_apply_iterations(cfg0):
+    """float32 apply with float64 recurrences: converges to the same x; the
+    iteration-count change is reported."""
+    f = oracle_factor(cfg0, oracle.CG)
+    ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
+    res = make(cfg0, B.CORR_CG, prec=B.PREC_FP32).solve(cfg0.b)
+    assert res.status == 0
+    print(f"fp32 apply: {res.info['iterations']} its vs fp64 oracle {ref.its}")
+    assert rel(res.x, ref.x) <= 1e-6
+    assert abs(res.info["iterations"] - ref.its) <= max(3, ref.its // 5)
+
+
+def test_solve_deterministic_and_device_pointers(cfg0):
+    import torch
+
+    P = make(cfg0, B.CORR_CG)
+    r1 = P.solve(cfg0.b)
+    r2 = P.solve(cfg0.b)
+    assert np.array_equal(r1.x, r2.x)
+    bd = torch.from_numpy(cfg0.b).cuda()
+    r3 = P.solve(bd)
+    torch.cuda.synchronize()
+    assert np.array_equal(r3.x.cpu().numpy(), r1.x)
+
+
+def test_zero_rhs(cfg0):
+    P = make(cfg0, B.CORR_NONE)
+    res = P.solve(np.zeros(cfg0.m))
+    assert res.status == 0 and res.info["iterations"] == 0 and not res.x.any()
+
+
+def test_maxit_reports_last_iterate(cfg0):
+    P = make(cfg0, B.CORR_NONE)
+    res = P.solve(cfg0.b, maxit=3, check_every=2)
+    assert res.status == B.ERR_MAXIT and res.info["iterations"] == 3
+    f = oracle_factor(cfg0, oracle.NONE)
+    ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b, maxit=3)
+    assert ref.status == 1 and rel(res.x, ref.x) <= 1e-10
+
+
+def test_si_breakdown_is_reported():
+    """mu = 0.1 on these matrices gives ||Y|| >> 1: S^ = I is indefinite and
+    the solve must stop with BREAKDOWN, like the oracle."""
+    prob = synth.config_problem(0)
+    f = oracle_factor(prob, oracle.SI, mu=0.1)
+    ref = oracle.lsmr(f, prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, prob.b)
+    assert ref.status == -2
+    res = make(prob, B.CORR_SI, mu=0.1).solve(prob.b, allow_fail=True)
+    assert res.status == B.ERR_BREAKDOWN
+
+
+def test_bad_input_errors():
+    prob = synth.config_problem(0)
+    with pytest.raises(B.RlsqError) as e:
+        B.Problem(prob.n, prob.m, prob.rowptr[: prob.n + 1], prob.colidx, prob.vals)
+    assert e.value.code in (-2, -3)
+    P = B.Problem.from_problem(prob)
+    with pytest.raises(B.RlsqError) as e:
+        P.solve(prob.b)
+    assert e.value.code == -5
