@@ -210,7 +210,9 @@ def run_ours(args):
 
     barrier()
     clk = Clocks(local)
+    torch.cuda.nvtx.range_push("timed")
     prof = P.profile(prob.b, warmup=max(3, args.warmup), iters=args.steps)
+    torch.cuda.nvtx.range_pop()
     clocks = clk.stop()
     barrier()
     total_ms = prof["total_ms"]
@@ -228,15 +230,15 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = world * e2e_res.info["iterations"] / e2e_s
 
-    # time to tolerance, float64 and float32 apply
+    # time to tolerance: float64, unpreconditioned, then float32 apply (the
+    # host factor is reused; only the device copy changes precision)
     tol64 = P.solve(prob.b)
-    P32 = B.Problem.from_problem(prob)
-    P32.factor(**FACTOR, precision=B.PREC_FP32, autotune=1)
-    tol32 = P32.solve(prob.b)
-    prof32 = P32.profile(prob.b, warmup=3, iters=args.steps)
+    plain = P.solve(prob.b, plain=True)
+    P.factor(**FACTOR, precision=B.PREC_FP32, autotune=1)
+    tol32 = P.solve(prob.b)
+    prof32 = P.profile(prob.b, warmup=3, iters=args.steps)
     x64 = tol64.x
     err32 = float(np.linalg.norm(tol32.x - x64) / np.linalg.norm(x64))
-    plain = P.solve(prob.b, plain=True)
 
     # roofline of the dominant kernel class
     hbm, src = peaks()

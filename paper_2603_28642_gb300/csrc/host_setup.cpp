@@ -136,10 +136,18 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) ac.val[e] = ac.val[e] * R.d[j];
     }
 
-    std::vector<int64_t> rc(static_cast<size_t>(m));
-    for (int64_t i = 0; i < m; ++i) rc[i] = a.ptr[i + 1] - a.ptr[i];
+    std::vector<int32_t> rc(static_cast<size_t>(m));
+    for (int64_t i = 0; i < m; ++i) rc[i] = static_cast<int32_t>(a.ptr[i + 1] - a.ptr[i]);
 
-    std::vector<int32_t> pivpos(static_cast<size_t>(m), -1);
+    // Per-row state touched together by the solve: working value, "touched in
+    // column j" mark and pivot position, one 16-byte record per row so a
+    // random row access costs one cache line.
+    struct RowState {
+        double x;
+        int32_t mark;
+        int32_t piv;
+    };
+    std::vector<RowState> rows(static_cast<size_t>(m), RowState{0.0, -1, -1});
     R.prow.assign(static_cast<size_t>(n), -1);
     R.Udiag.assign(static_cast<size_t>(n), 0.0);
 
@@ -153,8 +161,6 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     Ui.reserve(guess);
     Uv.reserve(guess);
 
-    std::vector<double> x(static_cast<size_t>(m));
-    std::vector<int32_t> xmark(static_cast<size_t>(m), -1);
     std::vector<int32_t> vmark(static_cast<size_t>(n), -1);
     std::vector<int32_t> touched, reach, stack;
     std::vector<Entry> cand;
@@ -168,11 +174,12 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         // scatter the scaled column and seed the graph search
         for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) {
             const int32_t i = ac.idx[e];
-            x[i] = ac.val[e];
-            xmark[i] = j;
+            RowState& ri = rows[i];
+            ri.x = ac.val[e];
+            ri.mark = j;
             touched.push_back(i);
             colinf = std::max(colinf, std::fabs(ac.val[e]));
-            const int32_t k = pivpos[i];
+            const int32_t k = ri.piv;
             if (k >= 0 && vmark[k] != j) {
                 vmark[k] = j;
                 stack.push_back(k);
@@ -184,7 +191,7 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
             stack.pop_back();
             reach.push_back(k);
             for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
-                const int32_t q = pivpos[Li[e]];
+                const int32_t q = rows[Li[e]].piv;
                 if (q >= 0 && vmark[q] != j) {
                     vmark[q] = j;
                     stack.push_back(q);
@@ -194,19 +201,39 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         std::sort(reach.begin(), reach.end());
         // numeric: unit lower solve in ascending pivot position
         cand.clear();
-        for (const int32_t k : reach) {
-            const int32_t pr = R.prow[k];
-            const double ukj = (xmark[pr] == j) ? x[pr] : 0.0;
+        // two-stage prefetch: the L column arrays kFar positions ahead, the
+        // rows they name kNear positions ahead
+        constexpr size_t kNear = 4, kFar = 8;
+        for (size_t t = 0; t < std::min(kFar, reach.size()); ++t) {
+            __builtin_prefetch(&Li[Lp[reach[t]]]);
+            __builtin_prefetch(&Lv[Lp[reach[t]]]);
+        }
+        for (size_t t = 0; t < std::min(kNear, reach.size()); ++t)
+            for (int64_t e = Lp[reach[t]]; e < Lp[reach[t] + 1]; ++e) __builtin_prefetch(&rows[Li[e]], 1);
+        for (size_t t = 0; t < reach.size(); ++t) {
+            if (t + kFar < reach.size()) {
+                const int32_t kf = reach[t + kFar];
+                __builtin_prefetch(&Li[Lp[kf]]);
+                __builtin_prefetch(&Lv[Lp[kf]]);
+                __builtin_prefetch(&rows[R.prow[kf]]);
+            }
+            if (t + kNear < reach.size()) {
+                const int32_t kp = reach[t + kNear];
+                for (int64_t e = Lp[kp]; e < Lp[kp + 1]; ++e) __builtin_prefetch(&rows[Li[e]], 1);
+            }
+            const int32_t k = reach[t];
+            const RowState& rp = rows[R.prow[k]];
+            const double ukj = (rp.mark == j) ? rp.x : 0.0;
             if (ukj == 0.0) continue;
             cand.push_back({std::fabs(ukj), k, ukj});
             for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
-                const int32_t i = Li[e];
-                if (xmark[i] != j) {
-                    xmark[i] = j;
-                    x[i] = 0.0;
-                    touched.push_back(i);
+                RowState& ri = rows[Li[e]];
+                if (ri.mark != j) {
+                    ri.mark = j;
+                    ri.x = 0.0;
+                    touched.push_back(Li[e]);
                 }
-                x[i] = x[i] - Lv[e] * ukj;
+                ri.x = ri.x - Lv[e] * ukj;
             }
         }
         dual_drop(cand, prm.p, prm.tau);
@@ -223,23 +250,23 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         double maxabs = 0.0;
         bool any = false;
         for (const int32_t i : touched)
-            if (pivpos[i] < 0 && x[i] != 0.0) {
+            if (rows[i].piv < 0 && rows[i].x != 0.0) {
                 any = true;
-                maxabs = std::max(maxabs, std::fabs(x[i]));
+                maxabs = std::max(maxabs, std::fabs(rows[i].x));
             }
         int32_t r = -1;
         double piv;
         if (!any) {
             for (int64_t i = 0; i < m; ++i)
-                if (pivpos[i] < 0 && (r < 0 || rc[i] < rc[r])) r = static_cast<int32_t>(i);
+                if (rows[i].piv < 0 && (r < 0 || rc[i] < rc[r])) r = static_cast<int32_t>(i);
             piv = modval;
             R.nmod++;
         } else {
             const double thr = prm.mu * maxabs;
             double rmag = 0.0;
             for (const int32_t i : touched) {
-                if (pivpos[i] >= 0 || x[i] == 0.0) continue;
-                const double mag = std::fabs(x[i]);
+                if (rows[i].piv >= 0 || rows[i].x == 0.0) continue;
+                const double mag = std::fabs(rows[i].x);
                 if (!(mag >= thr)) continue;
                 bool take = r < 0;
                 if (!take) {
@@ -252,21 +279,21 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
                     rmag = mag;
                 }
             }
-            piv = x[r];
+            piv = rows[r].x;
             if (std::fabs(piv) < prm.small) {
                 piv = (piv < 0.0) ? -modval : modval;
                 R.nmod++;
             }
         }
         R.Udiag[j] = piv;
-        pivpos[r] = j;
+        rows[r].piv = j;
         R.prow[j] = r;
 
         // L part: scale by the pivot, then drop
         cand.clear();
         for (const int32_t i : touched) {
-            if (pivpos[i] >= 0 || x[i] == 0.0) continue;
-            const double l = x[i] / piv;
+            if (rows[i].piv >= 0 || rows[i].x == 0.0) continue;
+            const double l = rows[i].x / piv;
             cand.push_back({std::fabs(l), i, l});
         }
         dual_drop(cand, prm.p, prm.tau);
@@ -281,6 +308,10 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
 
     // split: pivot rows in pivot order form L1, the rest (ascending id) L2
     const int64_t m2 = m - n;
+    std::vector<int32_t> pivpos(static_cast<size_t>(m));
+    for (int64_t i = 0; i < m; ++i) pivpos[i] = rows[i].piv;
+    rows.clear();
+    rows.shrink_to_fit();
     std::vector<int32_t> a2idx(static_cast<size_t>(m), -1);
     R.a2rows.reserve(static_cast<size_t>(m2));
     for (int64_t i = 0; i < m; ++i)

@@ -755,11 +755,21 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         prm.mu = opts.mu;
         prm.small = opts.small;
         prm.scale = opts.scale_columns != 0;
+        // The host factor depends only on (p, tau, mu, small, scaling): a call
+        // that changes the correction, precision or schedule re-uses it.
         std::unique_ptr<IlupResult> F;
-        try {
-            F.reset(new IlupResult(ilup_factor(h->A, prm)));
-        } catch (const std::runtime_error& e) {
-            throw ApiError(RLSQ_ERR_RANK, e.what());
+        const bool same = h->F && h->opts.p == opts.p && h->opts.tau == opts.tau &&
+                          h->opts.mu == opts.mu && h->opts.small == opts.small &&
+                          h->opts.scale_columns == opts.scale_columns;
+        if (same) {
+            F = std::move(h->F);
+        } else {
+            h->F.reset();
+            try {
+                F.reset(new IlupResult(ilup_factor(h->A, prm)));
+            } catch (const std::runtime_error& e) {
+                throw ApiError(RLSQ_ERR_RANK, e.what());
+            }
         }
         int corr = opts.correction;
         const int64_t m2 = h->m - h->n;
