@@ -273,6 +273,33 @@ typedef struct {
 int rlsq_profile(rlsq_problem h, const double *b, int32_t warmup, int32_t iters, int32_t plain,
                  rlsq_profile_out *out);
 
+/* ---- allocation-free triangular solve ---------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that must
+ * not allocate device memory while they run -- a latency-critical serving
+ * loop, where a cudaMalloc can stall the whole device, or a process whose
+ * free device memory is already held by another allocator.
+ *
+ * rlsq_trsv_noalloc solves the triangular system `which` (RLSQ_SYS_*) of a
+ * problem factored with RLSQ_PREC_FP64, like rlsq_trsv, with the sync-free
+ * kernel.  b (input) and x (output) are caller-owned DEVICE arrays of length n
+ * on the problem's device; the work is ordered on `stream` and the call
+ * returns after it finished.  It calls no cudaMalloc / cudaFree: the solve's
+ * working memory (ready flags, ticket counter, error word) lives in one
+ * statically sized device array of RLSQ_NOALLOC_MAX_ROWS + 128 32-bit words
+ * (8 MiB + 512 B) that every GPU which loads the library keeps until the
+ * process exits.
+ *  - n > RLSQ_NOALLOC_MAX_ROWS is rejected with RLSQ_ERR_SHAPE (nothing runs).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call reuses the same array and clears what must start at zero;
+ *    calls that overlap on the GPU (other streams, other threads, other
+ *    problems) race on it and must be serialised by the caller.
+ *  - Errors: ARG (null pointer, bad id, float32 factor, other device),
+ *    NOT_FACTORED, SHAPE, DEVICE_TIMEOUT, CUDA. */
+#define RLSQ_NOALLOC_MAX_ROWS 2097152
+int rlsq_trsv_noalloc(rlsq_problem h, int32_t which, const double *b, double *x, void *stream);
+
 /* ---- host-only set-up (no GPU needed) -------------------------------------
  * The row-selecting rectangular ILU set-up that rlsq_factor runs, callable on
  * its own: column scaling (Sec. 5.1), ILUP(p, tau) with threshold pivoting

@@ -95,7 +95,7 @@ EXPORTS = [
     "rlsq_destroy", "rlsq_server_create", "rlsq_server_register", "rlsq_server_submit",
     "rlsq_server_poll", "rlsq_server_get_stats", "rlsq_server_destroy", "rlsq_last_error",
     "rlsq_setup_create", "rlsq_setup_sizes", "rlsq_setup_split", "rlsq_setup_factor",
-    "rlsq_setup_levels", "rlsq_setup_destroy", "rlsq_profile",
+    "rlsq_setup_levels", "rlsq_setup_destroy", "rlsq_profile", "rlsq_trsv_noalloc",
 ]
 
 KCLASS = ["spmv", "spmvt", "trsv_L1", "trsv_L1t", "trsv_U", "trsv_Ut", "l2", "l2t", "vec",
@@ -150,6 +150,7 @@ def load(build_if_missing: bool = True):
             "rlsq_setup_levels": (C.c_int, [P, i32, P]),
             "rlsq_setup_destroy": (None, [P]),
             "rlsq_profile": (C.c_int, [P, P, i32, i32, i32, P]),
+            "rlsq_trsv_noalloc": (C.c_int, [P, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -343,6 +344,18 @@ class Problem:
         return dict(status=o.status, iters=o.iters, total_ms=o.total_ms,
                     ms_per_iter=o.total_ms / o.iters, bytes_per_iter=o.bytes_per_iter,
                     classes=classes)
+
+
+def trsv_noalloc(problem, which: int, b, x):
+    """rlsq_trsv_noalloc: triangular solve whose working memory is a static
+    device array, for callers that cannot allocate device memory.  b and x
+    are CUDA float64 tensors of length n; x is written in place."""
+    pb, mb = _ptr(b)
+    px, mx = _ptr(x)
+    if mb != DEVICE_PTRS or mx != DEVICE_PTRS:
+        raise TypeError("rlsq_trsv_noalloc takes device arrays")
+    _check(load().rlsq_trsv_noalloc(problem.handle, int(which), pb, px, _stream_of(b)))
+    return x
 
 
 def batch_solve(problems, bs, **kw):

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "librlsq.so")
 
-SOURCES = ["host_setup.cpp", "host_api.cpp", "problem.cu", "autotune.cu", "batch.cu"]
+SOURCES = ["host_setup.cpp", "host_api.cpp", "problem.cu", "autotune.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
