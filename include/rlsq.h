@@ -74,7 +74,8 @@ extern "C" {
 
 #define RLSQ_TRSV_AUTO 0     /* choose per system (autotuned when autotune != 0) */
 #define RLSQ_TRSV_LEVEL 1    /* one launch per level set */
-#define RLSQ_TRSV_SYNCFREE 2 /* one launch, rows wait on per-row ready flags (bounded waits) */
+#define RLSQ_TRSV_SYNCFREE 2 /* one launch, rows wait on the values they need (bounded waits) */
+#define RLSQ_TRSV_COOP 3     /* one persistent launch, grid barrier between levels (bounded waits) */
 
 /* triangular systems for rlsq_trsv */
 #define RLSQ_SYS_L1 0   /* L1 x = b   (unit lower)      */

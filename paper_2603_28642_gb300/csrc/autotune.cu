@@ -5,6 +5,7 @@
 // (median of a few runs after a warm-up) on the problem's own matrices; the
 // fastest wins.  Results are cached on the handle until the next factor.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "common.h"
@@ -16,6 +17,7 @@ namespace {
 template <class F>
 void with_lanes(int G, F&& f) {
     switch (G) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
         case 2: f(std::integral_constant<int, 2>{}); break;
         case 4: f(std::integral_constant<int, 4>{}); break;
         case 8: f(std::integral_constant<int, 8>{}); break;
@@ -48,12 +50,12 @@ float time_median(cudaStream_t st, Body&& body, int reps = 5) {
 
 int grid_for(const rlsq_problem_s* P, int64_t rows, int G) {
     const int64_t g = (rows * G + kBlock - 1) / kBlock;
-    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * 16))));
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * 32))));
 }
 
 template <typename T>
 int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y) {
-    static const int cands[] = {2, 4, 8, 16, 32};
+    static const int cands[] = {1, 2, 4, 8, 16, 32};
     int best = 8;
     float tbest = 1e30f;
     for (int G : cands) {
@@ -88,36 +90,82 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
         P->map.G_L2 = best_mv_lanes<T>(P, F.L2.view(), F.vn[3].p, F.vm[1].p);
         P->map.G_L2t = best_mv_lanes<T>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p);
     }
-    static const int cands[] = {2, 4, 8, 16, 32};
+    static const int cands[] = {1, 2, 4, 8, 16, 32};
     for (int w = 0; w < 4; ++w) {
         int bestG = P->map.G_tri[w], bestS = P->map.sched[w];
         float tbest = 1e30f;
-        for (int sched : {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_LEVEL}) {
+        int bestB = P->map.sf_blocks[w];
+        for (int sched : {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_LEVEL, RLSQ_TRSV_COOP}) {
             for (int G : cands) {
-                P->map.sched[w] = sched;
-                P->map.G_tri[w] = G;
-                float ms = 0.f;
-                if (rlsq_trsv_time(P, w, &ms) != RLSQ_OK) continue;
-                if (ms < tbest) {
-                    tbest = ms;
-                    bestG = G;
-                    bestS = sched;
+                if (sched == RLSQ_TRSV_COOP && G != 1) continue;  // one thread per row
+                for (int nb : {1, 2, 3, 6}) {
+                    if (sched != RLSQ_TRSV_SYNCFREE && nb != 1) continue;
+                    P->map.sched[w] = sched;
+                    P->map.G_tri[w] = G;
+                    P->map.sf_blocks[w] = nb;
+                    float ms = 0.f;
+                    if (rlsq_trsv_time(P, w, &ms) != RLSQ_OK) continue;
+                    if (ms < tbest) {
+                        tbest = ms;
+                        bestG = G;
+                        bestS = sched;
+                        bestB = nb;
+                    }
                 }
             }
         }
         P->map.G_tri[w] = bestG;
         P->map.sched[w] = bestS;
+        P->map.sf_blocks[w] = bestB;
+    }
+}
+
+// Lanes per row of the fused LSMR products, timed on a scratch state (the
+// kernels write only the work vectors, which a solve re-initialises).
+static void tune_products(rlsq_problem_s* P) {
+    static const int cands[] = {1, 2, 4, 8, 16, 32};
+    LsmrState* S = P->S.p + 1;
+    LsmrState h;
+    std::memset(&h, 0, sizeof(h));
+    h.alpha = h.inv_alpha = h.beta = h.inv_beta = 1.0;
+    h.anorm = 1.0;
+    h.atol = -1.0;             // the stopping test never fires while timing
+    h.maxit = 0x7fffffff;
+    RLSQ_CUDA(cudaMemcpy(S, &h, sizeof(h), cudaMemcpyHostToDevice));
+    RLSQ_CUDA(cudaMemsetAsync(P->tx.p, 0, sizeof(double2) * P->n, P->stream));
+    RLSQ_CUDA(cudaMemsetAsync(P->qr.p, 0, sizeof(double2) * P->m, P->stream));
+    RLSQ_CUDA(cudaMemsetAsync(P->b.p, 0, sizeof(double) * P->m, P->stream));
+    float best_a = 1e30f, best_t = 1e30f;
+    for (int G : cands) {
+        const float ta = time_median(P->stream, [&]() {
+            with_lanes(G, [&](auto g) {
+                constexpr int GG = decltype(g)::value;
+                k_spmv_lsmr<GG><<<grid_for(P, P->m, GG), kBlock, 0, P->stream>>>(
+                    P->dA.view(), P->tx.p, P->qr.p, P->b.p, S, P->part.p, P->counter.p);
+            });
+            RLSQ_CUDA(cudaGetLastError());
+        });
+        if (ta < best_a) {
+            best_a = ta;
+            P->map.G_A = G;
+        }
+        const float tt = time_median(P->stream, [&]() {
+            with_lanes(G, [&](auto g) {
+                constexpr int GG = decltype(g)::value;
+                k_spmvt_lsmr<GG, false><<<grid_for(P, P->n, GG), kBlock, 0, P->stream>>>(
+                    P->dAt.view(), P->qr.p, P->s.p, S, P->part.p, P->counter.p);
+            });
+            RLSQ_CUDA(cudaGetLastError());
+        });
+        if (tt < best_t) {
+            best_t = tt;
+            P->map.G_At = G;
+        }
     }
 }
 
 void autotune(rlsq_problem_s* P) {
-    const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
-    std::vector<double> ones(static_cast<size_t>(m), 1.0);
-    RLSQ_CUDA(cudaMemcpyAsync(P->q.p, ones.data(), sizeof(double) * m, cudaMemcpyHostToDevice, P->stream));
-    RLSQ_CUDA(cudaMemcpyAsync(P->s.p, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, P->stream));
-    RLSQ_CUDA(cudaStreamSynchronize(P->stream));
-    P->map.G_A = best_mv_lanes<double>(P, P->dA.view(), P->s.p, P->r.p);
-    P->map.G_At = best_mv_lanes<double>(P, P->dAt.view(), P->q.p, P->t.p);
+    tune_products(P);
     if (!P->factored) return;
     if (P->precision == RLSQ_PREC_FP32) tune_factor<float>(P, P->f32);
     else tune_factor<double>(P, P->f64);

@@ -91,6 +91,7 @@ struct Mapping {
     int G_tri[4] = {4, 4, 4, 4};        // lanes per row: L1, L1^T, U, U^T
     int sched[4] = {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE};
     int G_L2 = 4, G_L2t = 4;
+    int sf_blocks[4] = {2, 2, 2, 2};    // sync-free solve: resident blocks per SM (bounds the polling rows)
 };
 
 template <typename T>
@@ -99,6 +100,7 @@ struct DevFactor {
     DevArray<T> diag[4];       // U diagonal for U and U^T (unit for L1, L1^T)
     DevArray<int32_t> order[4];
     std::vector<int32_t> level_ptr[4];
+    DevArray<int32_t> level_ptr_d[4];  // device copies for the persistent solve
     DevCsr<T> L2, L2t;
     DevArray<T> d;
     DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
@@ -107,15 +109,17 @@ struct DevFactor {
     void clear() {
         for (int w = 0; w < 4; ++w) {
             tri[w].ptr.release(); tri[w].idx.release(); tri[w].val.release();
-            diag[w].release(); order[w].release(); level_ptr[w].clear();
+            diag[w].release(); order[w].release(); level_ptr[w].clear(); level_ptr_d[w].release();
         }
         for (auto* c : {&L2, &L2t}) { c->ptr.release(); c->idx.release(); c->val.release(); }
         d.release(); sinv.release();
         for (auto& v : vn) v.release();
         for (auto& v : vm) v.release();
     }
+    // tri[w], diag[w] are stored by solve position (rows in level order)
     Tri<T> tview(int which) const {
-        return Tri<T>{tri[which].view(), (which >= 2) ? diag[which].p : nullptr, order[which].p};
+        return Tri<T>{tri[which].rows, tri[which].ptr.p, tri[which].idx.p, tri[which].val.p,
+                      (which >= 2) ? diag[which].p : nullptr, order[which].p};
     }
 };
 
@@ -125,6 +129,7 @@ struct Recorder {
         int cls;
         double bytes;
         cudaEvent_t a, b;
+        int launches;
     };
     std::vector<Entry> entries;
     ~Recorder() {
@@ -156,12 +161,13 @@ struct rlsq_problem_s {
     rlsq::DevFactor<float> f32;
     rlsq::Mapping map;
 
-    // LSMR work vectors (float64)
-    rlsq::DevArray<double> q, r, b, s, t, h, hb, x;
+    // LSMR work vectors (float64); qr[i] = (q_i, r_i), tx[j] = (t_j, x_j)
+    rlsq::DevArray<double2> qr, tx;
+    rlsq::DevArray<double> b, s, h, hb;
     rlsq::DevArray<rlsq::LsmrState> S;   // [0] solve, [1] standalone calls
     rlsq::DevArray<double> part;
-    rlsq::DevArray<unsigned> counter, tickets;
-    rlsq::DevArray<int> flags;
+    rlsq::DevArray<unsigned> counter, tickets, barriers;  // barriers: one per triangular-solve slot
+    int coop_blocks = 0;                                    // co-resident blocks of the persistent solve
     rlsq::LsmrState* pinned_state = nullptr;   // host-pinned mirror
     int* pinned_done = nullptr;                // [2]
     cudaEvent_t ev[2] = {nullptr, nullptr};

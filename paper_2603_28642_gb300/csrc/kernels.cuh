@@ -18,6 +18,7 @@
 namespace rlsq {
 
 constexpr int kBlock = 256;          // threads per block for every kernel here
+constexpr int kMinBlocks = 6;        // resident blocks per SM asked of the register allocator
 constexpr int kMaxSlots = 64;        // triangular-solve launches per apply
 constexpr long long kWaitNs = 1000000000LL;  // bounded wait of a sync-free solve: 1 s
 
@@ -77,7 +78,9 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask) {
 }
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
-    if constexpr (G == 32) {
+    if constexpr (G == 1) {
+        return 1u << (threadIdx.x & 31u);
+    } else if constexpr (G == 32) {
         return 0xffffffffu;
     } else {
         const unsigned lane = threadIdx.x & 31u;
@@ -178,14 +181,37 @@ __device__ __forceinline__ void row_dot(const Csr<TV>& a, int row, int lane, con
 // LSMR products with A (float64)
 // ---------------------------------------------------------------------------
 
-// q <- A (t * inv_alpha) - alpha * (q * inv_beta)   [u_{k+1} beta_{k+2}]
-// r <- b - A x                                        [r_k]
+// Dot products of one row with the two halves of an interleaved vector pair
+// (p[j].x, p[j].y): one 16-byte gather per entry, four entries in flight per
+// lane.
+template <int G, typename TV>
+__device__ __forceinline__ void row_dot_pair(const Csr<TV>& a, int row, int lane, const double2* __restrict__ p,
+                                             double& s1, double& s2) {
+    const int e1 = a.ptr[row + 1];
+    int e = a.ptr[row] + lane;
+    for (; e + 3 * G < e1; e += 4 * G) {
+        const int j0 = a.idx[e], j1 = a.idx[e + G], j2 = a.idx[e + 2 * G], j3 = a.idx[e + 3 * G];
+        const double a0 = a.val[e], a1 = a.val[e + G], a2 = a.val[e + 2 * G], a3 = a.val[e + 3 * G];
+        const double2 p0 = p[j0], p1 = p[j1], p2 = p[j2], p3 = p[j3];
+        s1 += a0 * p0.x + a1 * p1.x + a2 * p2.x + a3 * p3.x;
+        s2 += a0 * p0.y + a1 * p1.y + a2 * p2.y + a3 * p3.y;
+    }
+    for (; e < e1; e += G) {
+        const double2 pj = p[a.idx[e]];
+        const double av = a.val[e];
+        s1 += av * pj.x;
+        s2 += av * pj.y;
+    }
+}
+
+// tx[j] = (t_j, x_j): v^ = t * inv_alpha and the current iterate x_k.
+// qr[i] = (q_i, r_i) with u = q * inv_beta.
+// q <- A v^ - alpha u  (= beta_{k+2} u_{k+2}),  r <- b - A x_k
 // totals: beta = ||q||, rnorm = ||r||
 template <int G>
-__global__ void __launch_bounds__(kBlock)
-k_spmv_lsmr(Csr<double> A, const double* __restrict__ t, const double* __restrict__ x,
-            double* __restrict__ q, const double* __restrict__ b, double* __restrict__ r,
-            LsmrState* S, double* part, unsigned* counter) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks)
+k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__ qr,
+            const double* __restrict__ b, LsmrState* S, double* part, unsigned* counter) {
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, alpha = S->alpha, inv_beta = S->inv_beta;
     const unsigned mask = group_mask<G>();
@@ -194,14 +220,16 @@ k_spmv_lsmr(Csr<double> A, const double* __restrict__ t, const double* __restric
     double acc[2] = {0.0, 0.0};
     for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < A.rows; row += groups) {
         double s1 = 0.0, s2 = 0.0;
-        row_dot2<G>(A, row, lane, t, x, s1, s2);
-        s1 = group_sum<G>(s1, mask);
-        s2 = group_sum<G>(s2, mask);
+        row_dot_pair<G>(A, row, lane, tx, s1, s2);
+        if (G > 1) {
+            s1 = group_sum<G>(s1, mask);
+            s2 = group_sum<G>(s2, mask);
+        }
         if (lane == 0) {
-            const double qn = s1 * inv_alpha - alpha * (q[row] * inv_beta);
+            const double2 old = qr[row];
+            const double qn = s1 * inv_alpha - alpha * (old.x * inv_beta);
             const double rr = b[row] - s2;
-            q[row] = qn;
-            r[row] = rr;
+            qr[row] = make_double2(qn, rr);
             acc[0] += qn * qn;
             acc[1] += rr * rr;
         }
@@ -219,9 +247,9 @@ k_spmv_lsmr(Csr<double> A, const double* __restrict__ t, const double* __restric
 // z  = A^T r                                            [only its norm]
 // totals: arnorm = ||z||; ratio check on x_k; FIRST: s = A^T q * inv_beta.
 template <int G, bool FIRST>
-__global__ void __launch_bounds__(kBlock)
-k_spmvt_lsmr(Csr<double> At, const double* __restrict__ q, const double* __restrict__ r,
-             double* __restrict__ s, LsmrState* S, double* part, unsigned* counter) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks)
+k_spmvt_lsmr(Csr<double> At, const double2* __restrict__ qr, double* __restrict__ s, LsmrState* S,
+             double* part, unsigned* counter) {
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, beta = S->beta, inv_beta = S->inv_beta;
     const unsigned mask = group_mask<G>();
@@ -230,13 +258,11 @@ k_spmvt_lsmr(Csr<double> At, const double* __restrict__ q, const double* __restr
     double acc[1] = {0.0};
     for (int col = (blockIdx.x * kBlock + threadIdx.x) / G; col < At.rows; col += groups) {
         double s1 = 0.0, s2 = 0.0;
-        if (FIRST) {
-            row_dot<G>(At, col, lane, q, s1);
-        } else {
-            row_dot2<G>(At, col, lane, q, r, s1, s2);
+        row_dot_pair<G>(At, col, lane, qr, s1, s2);
+        if (G > 1) {
+            s1 = group_sum<G>(s1, mask);
+            s2 = group_sum<G>(s2, mask);
         }
-        s1 = group_sum<G>(s1, mask);
-        if (!FIRST) s2 = group_sum<G>(s2, mask);
         if (lane == 0) {
             s[col] = FIRST ? s1 * inv_beta : s1 * inv_beta - beta * (s[col] * inv_alpha);
             acc[0] += s2 * s2;
@@ -278,11 +304,18 @@ __device__ __forceinline__ T rhs_at(const Rhs<T>& h, int i) {
     return h.a[i] * (T)h.s[i];
 }
 
+// A triangular system stored by solve position: position t solves unknown
+// order[t] (rows sorted by level, then id), and the row's entries (the
+// strictly triangular part; column ids are unknown ids) and its diagonal are
+// stored at position t, so every level is one contiguous range.
 template <typename T>
 struct Tri {
-    Csr<T> a;             // strictly triangular part (rows = unknowns)
-    const T* diag;        // nullptr: unit diagonal
-    const int32_t* order; // rows sorted by (level, id)
+    int32_t n;
+    const int32_t* ptr;    // n + 1, by position
+    const int32_t* idx;    // unknown ids of the entries
+    const T* val;
+    const T* diag;         // by position; nullptr: unit diagonal
+    const int32_t* order;  // order[t]: unknown solved at position t
 };
 
 // Waits until flag == epoch.  Gives up after kWaitNs or when another thread
@@ -302,10 +335,11 @@ __device__ __forceinline__ bool wait_flag(const int* flag, int epoch, int* err) 
     }
 }
 
-// Sync-free solve.  Blocks take chunks of the level order from a ticket
-// counter; every group of G lanes solves one row at a time, waiting on the
-// ready flags of the unknowns it reads.  A dependency always sits earlier
-// in the level order, hence in a chunk taken earlier by a running block (or
+// Sync-free solve with per-row ready flags (used by the allocation-free entry
+// point, whose scratch holds the flags).  Blocks take chunks of positions
+// from a ticket counter; every group of G lanes solves one row at a time,
+// waiting on the flags of the unknowns it reads.  A dependency always sits at
+// an earlier position, hence in a chunk taken earlier by a running block (or
 // earlier in the same chunk), so every wait ends; the 1 s bound only guards
 // against faults.  epoch = 1 + 64 * apply_count + slot.
 template <typename T, int G, int K, int ROUNDS>
@@ -314,7 +348,7 @@ k_trsv_syncfree(Tri<T> tri, Rhs<T> rhs, T* x, int* flags, int slot, unsigned* ti
                 const LsmrState* S, int* err) {
     if (S->done) return;
     const int epoch = 1 + kMaxSlots * S->apply_count + slot;
-    const int n = tri.a.rows;
+    const int n = tri.n;
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
     constexpr int per_round = kBlock / G;
@@ -337,20 +371,20 @@ k_trsv_syncfree(Tri<T> tri, Rhs<T> rhs, T* x, int* flags, int slot, unsigned* ti
             const int row = tri.order[tpos];
             T sum = (T)0;
             bool ok = true;
-            const int e1 = tri.a.ptr[row + 1];
-            for (int e = tri.a.ptr[row] + lane; e < e1; e += G) {
-                const int j = tri.a.idx[e];
+            const int e1 = tri.ptr[tpos + 1];
+            for (int e = tri.ptr[tpos] + lane; e < e1; e += G) {
+                const int j = tri.idx[e];
                 if (!wait_flag(&flags[j], epoch, err)) {
                     ok = false;
                     break;
                 }
-                sum += tri.a.val[e] * ld_l2(&x[j]);
+                sum += tri.val[e] * ld_l2(&x[j]);
             }
             sum = group_sum<G>(sum, mask);
             ok = __all_sync(mask, ok);
             if (lane == 0) {
                 T v = rhs_at<T, K>(rhs, row) - sum;
-                if (tri.diag) v = v / tri.diag[row];
+                if (tri.diag) v = v / tri.diag[tpos];
                 if (!ok) v = (T)NAN;
                 x[row] = v;
                 st_release(&flags[row], epoch);
@@ -359,7 +393,214 @@ k_trsv_syncfree(Tri<T> tri, Rhs<T> rhs, T* x, int* flags, int slot, unsigned* ti
     }
 }
 
-// Level-scheduled solve: one launch per level, rows order[lo..hi).
+// ---- sentinel-based sync-free solve ---------------------------------------
+// Before the solve the output vector is filled with all-one bytes (a NaN
+// whose bit pattern arithmetic never produces: the GPU's computed NaNs have a
+// clear sign bit).  An unknown is ready once its value is no longer that
+// pattern, so one relaxed load both tests readiness and delivers the value.
+// The polled word is the datum itself, so no ordering with other accesses is
+// needed: no "memory" clobber, which lets the compiler issue the row's other
+// loads (position -> unknown, right-hand side, diagonal) before the wait.
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+    return __longlong_as_double((long long)v);
+}
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return __uint_as_float(v);
+}
+__device__ __forceinline__ void st_relaxed(double* p, double x) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"((unsigned long long)__double_as_longlong(x)));
+}
+__device__ __forceinline__ void st_relaxed(float* p, float x) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(__float_as_uint(x)));
+}
+__device__ __forceinline__ bool is_pending(double v) { return __double_as_longlong(v) == -1LL; }
+__device__ __forceinline__ bool is_pending(float v) { return __float_as_uint(v) == 0xffffffffu; }
+
+// Spins until x[j] is written; NaN and ok = false after kWaitNs or once
+// another thread has given up.
+// Polls back off exponentially (64 ns .. 1 us): hundreds of thousands of
+// waiting rows polling flat out would otherwise take the issue slots and L2
+// bandwidth that the rows being solved need.
+template <typename T>
+__device__ __noinline__ T wait_value(const T* p, int* err, bool& ok) {
+    const unsigned long long t0 = globaltimer();
+    unsigned ns = 64;
+    for (;;) {
+        __nanosleep(ns);
+        const T v = ld_relaxed(p);
+        if (!is_pending(v)) return v;
+        if (ns < 1024) ns <<= 1;
+        if (*(volatile int*)err != 0 || (long long)(globaltimer() - t0) > kWaitNs) {
+            atomicCAS(err, 0, 1);
+            ok = false;
+            return (T)NAN;
+        }
+    }
+}
+
+// One row per group of G lanes (G = 1: one thread per row); entries are read
+// four at a time per lane so that several gathers are in flight.  Chunks of
+// positions are handed out by a ticket counter as in k_trsv_syncfree.
+template <typename T, int G, int K, int ROUNDS>
+__global__ void __launch_bounds__(kBlock, kMinBlocks)
+k_trsv_sentinel(Tri<T> tri, Rhs<T> rhs, T* x, int slot, unsigned* tickets, const LsmrState* S,
+                int* err) {
+    if (S->done) return;
+    const int n = tri.n;
+    const unsigned mask = group_mask<G>();
+    const int lane = threadIdx.x & (G - 1);
+    constexpr int per_round = kBlock / G;
+    constexpr int chunk_rows = per_round * ROUNDS;
+    __shared__ int chunk;
+    for (;;) {
+        __syncwarp();
+        if (threadIdx.x == 0) chunk = (int)atomicAdd(&tickets[slot], 1u);
+        __syncthreads();
+        const long long c0 = (long long)chunk * chunk_rows;
+        __syncthreads();
+        if (c0 >= n) break;
+#pragma unroll 1
+        for (int rd = 0; rd < ROUNDS; ++rd) {
+            const long long tpos = c0 + rd * per_round + threadIdx.x / G;
+            if (tpos >= n) break;
+            const int e1 = tri.ptr[tpos + 1];
+            int e = tri.ptr[tpos] + lane;
+            // everything that does not depend on other rows, loaded up front
+            const int row = tri.order[tpos];
+            const T rv = rhs_at<T, K>(rhs, row);
+            const T dg = tri.diag ? tri.diag[tpos] : (T)1;
+            T sum = (T)0;
+            bool ok = true;
+            for (; e + 3 * G < e1; e += 4 * G) {
+                const int j0 = tri.idx[e], j1 = tri.idx[e + G], j2 = tri.idx[e + 2 * G], j3 = tri.idx[e + 3 * G];
+                const T a0 = tri.val[e], a1 = tri.val[e + G], a2 = tri.val[e + 2 * G], a3 = tri.val[e + 3 * G];
+                T v0 = ld_relaxed(&x[j0]), v1 = ld_relaxed(&x[j1]), v2 = ld_relaxed(&x[j2]), v3 = ld_relaxed(&x[j3]);
+                if (is_pending(v0)) v0 = wait_value(&x[j0], err, ok);
+                if (is_pending(v1)) v1 = wait_value(&x[j1], err, ok);
+                if (is_pending(v2)) v2 = wait_value(&x[j2], err, ok);
+                if (is_pending(v3)) v3 = wait_value(&x[j3], err, ok);
+                sum += a0 * v0 + a1 * v1 + a2 * v2 + a3 * v3;
+            }
+            for (; e < e1; e += G) {
+                const int j = tri.idx[e];
+                T v = ld_relaxed(&x[j]);
+                if (is_pending(v)) v = wait_value(&x[j], err, ok);
+                sum += tri.val[e] * v;
+            }
+            if (G > 1) {
+                sum = group_sum<G>(sum, mask);
+                ok = __all_sync(mask, ok);
+            }
+            if (lane == 0) {
+                T v = rv - sum;
+                if (tri.diag) v = v / dg;
+                if (!ok) v = (T)NAN;
+                st_relaxed(&x[row], v);
+            }
+        }
+    }
+}
+
+// Persistent level-synchronous solve: one co-resident block of kCoopBlock
+// threads per SM walks the levels in order; inside a level the rows are dealt
+// out block-cyclically, and a grid-wide barrier separates levels.  The barrier
+// counter only grows (arrivals = level * blocks), so it needs no reset within
+// a launch; waits are bounded like every other wait here.  x is read through
+// L2 (__ldcg) because other SMs wrote it.
+constexpr int kCoopBlock = 1024;
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned long long t0 = globaltimer();
+        while ((unsigned)ld_acquire(reinterpret_cast<const int*>(bar)) < target) {
+            if (*(volatile int*)err != 0) break;
+            if ((long long)(globaltimer() - t0) > kWaitNs) {
+                atomicCAS(err, 0, 1);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// The first row a thread owns in a level, read before the barrier that
+// opens the level: nothing here depends on the unknowns being solved.
+template <typename T, int KP>
+struct RowAhead {
+    int row, e0, e1;
+    T rv, dg;
+    int j[KP];
+    T a[KP];
+};
+
+template <typename T, int K, int KP>
+__device__ __forceinline__ void read_ahead(const Tri<T>& tri, const Rhs<T>& rhs, int t, RowAhead<T, KP>& r) {
+    r.row = tri.order[t];
+    r.e0 = tri.ptr[t];
+    r.e1 = tri.ptr[t + 1];
+    r.rv = rhs_at<T, K>(rhs, r.row);
+    r.dg = tri.diag ? tri.diag[t] : (T)1;
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+        const bool in = r.e0 + q < r.e1;
+        r.j[q] = in ? tri.idx[r.e0 + q] : 0;
+        r.a[q] = in ? tri.val[r.e0 + q] : (T)0;
+    }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kCoopBlock, 1)
+k_trsv_coop(Tri<T> tri, Rhs<T> rhs, T* x, const int32_t* __restrict__ level_ptr, int nlevels, unsigned* bar,
+            const LsmrState* S, int* err) {
+    constexpr int KP = 8;
+    if (S->done) return;
+    const int nthreads = gridDim.x * kCoopBlock;
+    // block-cyclic: consecutive rows of a level go to different SMs, so every
+    // SM's load/store unit carries 1/gridDim of the level's gathers
+    const int tid = threadIdx.x * gridDim.x + blockIdx.x;
+    RowAhead<T, KP> ra;
+    int lo = level_ptr[0], hi = level_ptr[1];
+    if (lo + tid < hi) read_ahead<T, K, KP>(tri, rhs, lo + tid, ra);
+    for (int l = 0; l < nlevels; ++l) {
+        int t = lo + tid;
+        if (t < hi) {
+            // first row: its structure is already in registers, so all its
+            // gathers of solved unknowns go out at once
+            T sum = (T)0;
+#pragma unroll
+            for (int q = 0; q < KP; ++q) sum += ra.a[q] * __ldcg(&x[ra.j[q]]);
+            for (int e = ra.e0 + KP; e < ra.e1; ++e) sum += tri.val[e] * __ldcg(&x[tri.idx[e]]);
+            T v = ra.rv - sum;
+            if (tri.diag) v = v / ra.dg;
+            x[ra.row] = v;
+            // further rows of a wide level
+            for (t += nthreads; t < hi; t += nthreads) {
+                const int row = tri.order[t];
+                T s2 = (T)0;
+                for (int e = tri.ptr[t]; e < tri.ptr[t + 1]; ++e) s2 += tri.val[e] * __ldcg(&x[tri.idx[e]]);
+                T w = rhs_at<T, K>(rhs, row) - s2;
+                if (tri.diag) w = w / tri.diag[t];
+                x[row] = w;
+            }
+        }
+        if (l + 1 < nlevels) {
+            lo = hi;
+            hi = level_ptr[l + 2];
+            if (lo + tid < hi) read_ahead<T, K, KP>(tri, rhs, lo + tid, ra);
+            grid_barrier(bar, (unsigned)(l + 1) * gridDim.x, err);
+        }
+    }
+}
+
+// Level-scheduled solve: one launch per level, positions [lo, hi).
 template <typename T, int G, int K>
 __global__ void __launch_bounds__(kBlock)
 k_trsv_level(Tri<T> tri, Rhs<T> rhs, T* x, int lo, int hi, const LsmrState* S) {
@@ -369,12 +610,15 @@ k_trsv_level(Tri<T> tri, Rhs<T> rhs, T* x, int lo, int hi, const LsmrState* S) {
     const int groups = (gridDim.x * kBlock) / G;
     for (int tpos = lo + (blockIdx.x * kBlock + threadIdx.x) / G; tpos < hi; tpos += groups) {
         const int row = tri.order[tpos];
+        const T rv = rhs_at<T, K>(rhs, row);
+        const T dg = tri.diag ? tri.diag[tpos] : (T)1;
         T sum = (T)0;
-        row_dot<G>(tri.a, row, lane, x, sum);
-        sum = group_sum<G>(sum, mask);
+        const int e1 = tri.ptr[tpos + 1];
+        for (int e = tri.ptr[tpos] + lane; e < e1; e += G) sum += tri.val[e] * x[tri.idx[e]];
+        if (G > 1) sum = group_sum<G>(sum, mask);
         if (lane == 0) {
-            T v = rhs_at<T, K>(rhs, row) - sum;
-            if (tri.diag) v = v / tri.diag[row];
+            T v = rv - sum;
+            if (tri.diag) v = v / dg;
             x[row] = v;
         }
     }
@@ -528,12 +772,13 @@ k_dense_gemv(int m2, const T* __restrict__ Sinv, const T* __restrict__ e, T* __r
 template <typename T, bool INIT, bool IDENT = false>
 __global__ void __launch_bounds__(kBlock)
 k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const double* __restrict__ s,
-               double* __restrict__ t, LsmrState* S, double* part, unsigned* counter) {
+               double2* __restrict__ tx, LsmrState* S, double* part, unsigned* counter) {
     if (S->done) return;
+    double* t = reinterpret_cast<double*>(tx);  // t_i lives at tx[i].x
     double acc[1] = {0.0};
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
         const double ti = IDENT ? s[i] : (double)(d[i] * g5[i]);
-        t[i] = ti;
+        t[2 * i] = ti;
         acc[0] += ti * s[i];
     }
     double tot[1];
@@ -591,36 +836,37 @@ k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const d
 // INIT: h = v^_1, h-bar = 0, x = 0.  Else: h-bar, x, h updates, k += 1.
 template <bool INIT>
 __global__ void __launch_bounds__(kBlock)
-k_lsmr_update(int n, const double* __restrict__ t, double* __restrict__ h, double* __restrict__ hb,
-              double* __restrict__ x, LsmrState* S) {
+k_lsmr_update(int n, double2* __restrict__ tx, double* __restrict__ h, double* __restrict__ hb,
+              LsmrState* S) {
     if (S->done) return;
     const double ia = S->inv_alpha;
     const double chb = S->c_hbar, cx = S->c_x, ch = S->c_h;
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
-        const double vh = t[i] * ia;
+        const double2 p = tx[i];
+        const double vh = p.x * ia;
         if (INIT) {
             h[i] = vh;
             hb[i] = 0.0;
-            x[i] = 0.0;
+            tx[i] = make_double2(p.x, 0.0);
         } else {
             const double hbi = h[i] - chb * hb[i];
             hb[i] = hbi;
-            x[i] = x[i] + cx * hbi;
+            tx[i] = make_double2(p.x, p.y + cx * hbi);
             h[i] = vh - ch * h[i];
         }
     }
     if (!INIT && blockIdx.x == 0 && threadIdx.x == 0) S->k += 1;
 }
 
-// q = b, totals: beta = ||b||
+// (q, r) = (b, b), totals: beta = ||b||
 template <int UNUSED = 0>
 __global__ void __launch_bounds__(kBlock)
-k_start_b(int m, const double* __restrict__ b, double* __restrict__ q, LsmrState* S, double* part,
+k_start_b(int m, const double* __restrict__ b, double2* __restrict__ qr, LsmrState* S, double* part,
           unsigned* counter) {
     double acc[1] = {0.0};
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < m; i += gridDim.x * kBlock) {
         const double v = b[i];
-        q[i] = v;
+        qr[i] = make_double2(v, v);  // q = beta_1 u_1 = b, r_0 = b
         acc[0] += v * v;
     }
     double tot[1];

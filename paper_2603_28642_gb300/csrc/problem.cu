@@ -60,10 +60,32 @@ void DevFactor<T>::upload(const IlupResult& F, const std::vector<double>& sinv_h
     const HostCSR* parts[4] = {&F.L1, &F.L1t, &F.U, &F.Ut};
     const Levels* levs[4] = {&F.lev_L1, &F.lev_L1t, &F.lev_U, &F.lev_Ut};
     for (int w = 0; w < 4; ++w) {
-        tri[w].upload(*parts[w], s);
-        order[w].upload(levs[w]->order.data(), levs[w]->order.size(), s);
+        // rows permuted into solve order so each level is contiguous
+        const HostCSR& a = *parts[w];
+        const std::vector<int32_t>& ord = levs[w]->order;
+        HostCSR lo;
+        lo.rows = a.rows;
+        lo.cols = a.cols;
+        lo.ptr.assign(static_cast<size_t>(a.rows) + 1, 0);
+        lo.idx.reserve(a.idx.size());
+        lo.val.reserve(a.val.size());
+        for (int64_t t = 0; t < a.rows; ++t) {
+            const int32_t r = ord[t];
+            for (int64_t e = a.ptr[r]; e < a.ptr[r + 1]; ++e) {
+                lo.idx.push_back(a.idx[e]);
+                lo.val.push_back(a.val[e]);
+            }
+            lo.ptr[t + 1] = static_cast<int64_t>(lo.idx.size());
+        }
+        tri[w].upload(lo, s);
+        order[w].upload(ord.data(), ord.size(), s);
         level_ptr[w] = levs[w]->level_ptr;
-        if (w >= 2) upload_vec(diag[w], F.Udiag, s);
+        level_ptr_d[w].upload(level_ptr[w].data(), level_ptr[w].size(), s);
+        if (w >= 2) {
+            std::vector<double> dl(ord.size());
+            for (size_t t = 0; t < ord.size(); ++t) dl[t] = F.Udiag[ord[t]];
+            upload_vec(diag[w], dl, s);
+        }
     }
     L2.upload(F.L2, s);
     L2t.upload(F.L2t, s);
@@ -87,6 +109,7 @@ template struct DevFactor<float>;
 template <class F>
 static void with_G(int G, F&& f) {
     switch (G) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
         case 2: f(std::integral_constant<int, 2>{}); break;
         case 4: f(std::integral_constant<int, 4>{}); break;
         case 8: f(std::integral_constant<int, 8>{}); break;
@@ -103,7 +126,7 @@ static void with_rhs(int k, F&& f) {
     }
 }
 
-static int max_grid(const rlsq_problem_s* P) { return std::max(1, P->num_sms * 16); }
+static int max_grid(const rlsq_problem_s* P) { return std::max(1, P->num_sms * 32); }
 
 static int grid_rows(const rlsq_problem_s* P, int64_t rows, int G) {
     const int64_t g = (rows * G + kBlock - 1) / kBlock;
@@ -122,15 +145,16 @@ struct RecScope {
     size_t slot = 0;
     RecScope(rlsq_problem_s* p, int cls, double bytes, cudaStream_t s) : P(p), st(s) {
         if (!P->rec) return;
-        Recorder::Entry e{cls, bytes, nullptr, nullptr};
+        Recorder::Entry e{cls, bytes, nullptr, nullptr, 1};
         RLSQ_CUDA(cudaEventCreate(&e.a));
         RLSQ_CUDA(cudaEventCreate(&e.b));
-        RLSQ_CUDA(cudaEventRecord(e.a, st));
+        // external record: becomes an event-record node when captured
+        RLSQ_CUDA(cudaEventRecordWithFlags(e.a, st, cudaEventRecordExternal));
         P->rec->entries.push_back(e);
         slot = P->rec->entries.size();
     }
     ~RecScope() {
-        if (P->rec && slot) cudaEventRecord(P->rec->entries[slot - 1].b, st);
+        if (P->rec && slot) cudaEventRecordWithFlags(P->rec->entries[slot - 1].b, st, cudaEventRecordExternal);
     }
 };
 
@@ -150,7 +174,7 @@ template <typename T>
 static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, Rhs<T> rhs, T* x,
                         int slot, LsmrState* S, cudaStream_t st) {
     const Tri<T> tri = F.tview(which);
-    const int n = tri.a.rows;
+    const int n = tri.n;
     const int G = P->map.G_tri[which];
     RecScope rs(P, RLSQ_KCLASS_TRSV_L1 + which, trsv_bytes(P, F, which), st);
     if (P->map.sched[which] == RLSQ_TRSV_LEVEL) {
@@ -165,20 +189,43 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
                 });
             });
         }
+        if (P->rec && !P->rec->entries.empty()) P->rec->entries.back().launches = static_cast<int>(lp.size()) - 1;
+    } else if (P->map.sched[which] == RLSQ_TRSV_COOP) {
+        if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
+        const int nlev = static_cast<int>(F.level_ptr[which].size()) - 1;
+        with_rhs(rk, [&](auto k) {
+            auto kern = k_trsv_coop<T, decltype(k)::value>;
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(static_cast<unsigned>(P->coop_blocks));
+            cfg.blockDim = dim3(kCoopBlock);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, F.level_ptr_d[which].p, nlev,
+                                         P->barriers.p + slot, static_cast<const LsmrState*>(S), error_word(S)));
+        });
     } else {
         if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
+        // all-one bytes mark "not yet solved" (see k_trsv_sentinel)
+        RLSQ_CUDA(cudaMemsetAsync(x, 0xff, sizeof(T) * static_cast<size_t>(n), st));
         with_G(G, [&](auto g) {
             constexpr int GG = decltype(g)::value;
-            constexpr int ROUNDS = 4;
+            constexpr int ROUNDS = 1;
             const int chunk_rows = (kBlock / GG) * ROUNDS;
             const int chunks = (n + chunk_rows - 1) / chunk_rows;
             with_rhs(rk, [&](auto k) {
-                auto kern = k_trsv_syncfree<T, GG, decltype(k)::value, ROUNDS>;
+                auto kern = k_trsv_sentinel<T, GG, decltype(k)::value, ROUNDS>;
                 int occ = 0;
                 RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, 0));
-                const int grid = std::max(1, std::min(chunks, std::max(1, occ) * P->num_sms));
-                kern<<<grid, kBlock, 0, st>>>(tri, rhs, x, P->flags.p, slot, P->tickets.p, S,
-                                              error_word(S));
+                // rows in flight = grid * kBlock / G; every one of them polls, so
+                // the window is kept to a few levels rather than the whole GPU
+                occ = std::max(1, std::min(occ, P->map.sf_blocks[which]));
+                const int grid = std::max(1, std::min(chunks, occ * P->num_sms));
+                kern<<<grid, kBlock, 0, st>>>(tri, rhs, x, slot, P->tickets.p, S, error_word(S));
             });
         });
     }
@@ -192,6 +239,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
     const int n = static_cast<int>(P->n);
     const int m2 = static_cast<int>(P->m - P->n);
     RLSQ_CUDA(cudaMemsetAsync(P->tickets.p, 0, sizeof(unsigned) * kMaxSlots, st));
+    RLSQ_CUDA(cudaMemsetAsync(P->barriers.p, 0, sizeof(unsigned) * kMaxSlots, st));
     int slot = 0;
     T* g1 = F.vn[0].p;
     T* g2 = F.vn[1].p;
@@ -278,7 +326,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
     T* g5 = F.vn[2].p;
     launch_trsv<T>(P, F, 2, RHS_VEC, Rhs<T>{g4, nullptr, nullptr}, g5, slot++, S, st);    // U^{-1}
     RecScope rs(P, RLSQ_KCLASS_FINISH, (2.0 * sizeof(T) + 16.0) * n, st);
-    k_finish_apply<T, INIT><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, F.d.p, g5, s, P->t.p, S,
+    k_finish_apply<T, INIT><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, F.d.p, g5, s, P->tx.p, S,
                                                                    P->part.p, P->counter.p);
 }
 
@@ -287,7 +335,7 @@ static void enqueue_identity_apply(rlsq_problem_s* P, const double* s, LsmrState
     // M = I: t = s (the unpreconditioned baseline)
     const int n = static_cast<int>(P->n);
     RecScope rs(P, RLSQ_KCLASS_FINISH, 24.0 * n, st);
-    k_finish_apply<double, INIT, true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, nullptr, s, s, P->t.p, S,
+    k_finish_apply<double, INIT, true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, nullptr, s, s, P->tx.p, S,
                                                                               P->part.p, P->counter.p);
 }
 
@@ -309,32 +357,32 @@ static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, 
         RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 16.0, 32.0), st);
         with_G(P->map.G_A, [&](auto g) {
             k_spmv_lsmr<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
-                P->dA.view(), P->t.p, P->x.p, P->q.p, P->b.p, P->r.p, S, P->part.p, P->counter.p);
+                P->dA.view(), P->tx.p, P->qr.p, P->b.p, S, P->part.p, P->counter.p);
         });
     }
     {
         RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 16.0, 16.0), st);
         with_G(P->map.G_At, [&](auto g) {
             k_spmvt_lsmr<decltype(g)::value, false>
-                <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->q.p, P->r.p, P->s.p,
-                                                                        S, P->part.p, P->counter.p);
+                <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
+                                                                        P->part.p, P->counter.p);
         });
     }
     enqueue_apply_any<false>(P, P->s.p, S, st, plain);
     RecScope rs(P, RLSQ_KCLASS_UPDATE, 56.0 * n, st);
-    k_lsmr_update<false><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->t.p, P->h.p, P->hb.p, P->x.p, S);
+    k_lsmr_update<false><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, P->hb.p, S);
 }
 
 static void enqueue_start(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
     const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
-    k_start_b<0><<<grid_rows(P, m, 1), kBlock, 0, st>>>(m, P->b.p, P->q.p, S, P->part.p, P->counter.p);
+    k_start_b<0><<<grid_rows(P, m, 1), kBlock, 0, st>>>(m, P->b.p, P->qr.p, S, P->part.p, P->counter.p);
     with_G(P->map.G_At, [&](auto g) {
         k_spmvt_lsmr<decltype(g)::value, true>
-            <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->q.p, P->r.p, P->s.p,
-                                                                    S, P->part.p, P->counter.p);
+            <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
+                                                                    P->part.p, P->counter.p);
     });
     enqueue_apply_any<true>(P, P->s.p, S, st, plain);
-    k_lsmr_update<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->t.p, P->h.p, P->hb.p, P->x.p, S);
+    k_lsmr_update<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, P->hb.p, S);
 }
 
 static LsmrState initial_state(const rlsq_problem_s* P, double atol, int maxit) {
@@ -459,7 +507,6 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     LsmrState* S = state_ptr(P, 0);
     put_state(P, S, initial_state(P, opts.atol, opts.maxit), st);
-    if (!plain) RLSQ_CUDA(cudaMemsetAsync(P->flags.p, 0, sizeof(int) * P->n, st));
     enqueue_start(P, S, st, plain);
     cudaGraphExec_t g = iteration_graph(P, iters, plain);
     const int64_t max_launches = static_cast<int64_t>(opts.maxit) / iters + 4;
@@ -489,8 +536,10 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
     LsmrState hs;
     RLSQ_CUDA(cudaMemcpy(&hs, S, sizeof(LsmrState), cudaMemcpyDeviceToHost));
     if (!hs.done) throw ApiError(RLSQ_ERR_CUDA, "solver did not reach a stopping point");
-    RLSQ_CUDA(cudaMemcpyAsync(x, P->x.p, sizeof(double) * P->n,
-                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    // x_j lives at tx[j].y
+    RLSQ_CUDA(cudaMemcpy2DAsync(x, sizeof(double), reinterpret_cast<const double*>(P->tx.p) + 1,
+                                sizeof(double2), sizeof(double), static_cast<size_t>(P->n),
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     RLSQ_CUDA(cudaStreamSynchronize(st));
     if (dev) {
         RLSQ_CUDA(cudaEventRecord(P->ev[0], st));
@@ -556,17 +605,20 @@ static int pow2_lanes(double avg, int lo, int hi) {
 
 void default_mapping(rlsq_problem_s* P) {
     const double m = static_cast<double>(P->m), n = static_cast<double>(P->n);
-    P->map.G_A = pow2_lanes(P->nnz / m, 2, 32);
-    P->map.G_At = pow2_lanes(P->nnz / n, 2, 32);
+    // about four entries per lane; the autotuner refines this
+    P->map.G_A = pow2_lanes(P->nnz / m / 4.0, 1, 32);
+    P->map.G_At = pow2_lanes(P->nnz / n / 4.0, 1, 32);
     if (P->F) {
         const IlupResult& F = *P->F;
         const HostCSR* parts[4] = {&F.L1, &F.L1t, &F.U, &F.Ut};
         for (int w = 0; w < 4; ++w) {
-            P->map.G_tri[w] = pow2_lanes(parts[w]->nnz() / std::max(1.0, n), 2, 32);
+            // one thread per row unless rows are long
+            const double avg = parts[w]->nnz() / std::max(1.0, n);
+            P->map.G_tri[w] = avg <= 12.0 ? 1 : pow2_lanes(avg / 4.0, 1, 32);
             P->map.sched[w] = RLSQ_TRSV_SYNCFREE;
         }
-        P->map.G_L2 = pow2_lanes(F.L2.nnz() / std::max(1.0, m - n), 2, 32);
-        P->map.G_L2t = pow2_lanes(F.L2t.nnz() / std::max(1.0, n), 2, 32);
+        P->map.G_L2 = pow2_lanes(F.L2.nnz() / std::max(1.0, m - n) / 4.0, 1, 32);
+        P->map.G_L2t = pow2_lanes(F.L2t.nnz() / std::max(1.0, n) / 4.0, 1, 32);
     }
 }
 
@@ -581,10 +633,9 @@ int rlsq_trsv_time(rlsq_problem_s* P, int which, float* ms) {
     cudaEvent_t a, b;
     RLSQ_CUDA(cudaEventCreate(&a));
     RLSQ_CUDA(cudaEventCreate(&b));
-    const int n = static_cast<int>(P->n);
     auto body = [&]() {
-        RLSQ_CUDA(cudaMemsetAsync(P->flags.p, 0, sizeof(int) * n, st));
         RLSQ_CUDA(cudaMemsetAsync(P->tickets.p, 0, sizeof(unsigned) * kMaxSlots, st));
+        RLSQ_CUDA(cudaMemsetAsync(P->barriers.p, 0, sizeof(unsigned) * kMaxSlots, st));
         if (P->precision == RLSQ_PREC_FP32)
             launch_trsv<float>(P, P->f32, which, RHS_VEC, Rhs<float>{P->f32.vn[3].p, nullptr, nullptr},
                                P->f32.vn[4].p, 0, S, st);
@@ -720,14 +771,23 @@ int rlsq_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* coli
         cudaStream_t st = P->stream;
         P->dA.upload(A, st);
         P->dAt.upload(transpose(A), st);
-        for (auto* v : {&P->q, &P->r, &P->b}) v->alloc(static_cast<size_t>(m));
-        for (auto* v : {&P->s, &P->t, &P->h, &P->hb, &P->x}) v->alloc(static_cast<size_t>(n));
+        P->qr.alloc(static_cast<size_t>(m));
+        P->tx.alloc(static_cast<size_t>(n));
+        P->b.alloc(static_cast<size_t>(m));
+        for (auto* v : {&P->s, &P->h, &P->hb}) v->alloc(static_cast<size_t>(n));
         P->S.alloc(2);
         P->part.alloc(static_cast<size_t>(max_grid(P.get())) * 2);
         P->counter.alloc(1);
         RLSQ_CUDA(cudaMemsetAsync(P->counter.p, 0, sizeof(unsigned), st));
         P->tickets.alloc(kMaxSlots);
-        P->flags.alloc(static_cast<size_t>(n));
+        P->barriers.alloc(kMaxSlots);
+        {
+            int occ = 0;
+            RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trsv_coop<double, RHS_VEC>, kCoopBlock, 0));
+            int occ32 = 0;
+            RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_trsv_coop<float, RHS_VEC>, kCoopBlock, 0));
+            P->coop_blocks = std::max(1, std::min(occ, occ32)) * P->num_sms;
+        }
         default_mapping(P.get());
         P->anorm = power_norm(P.get(), 50);
         *out = P.release();
@@ -791,7 +851,8 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         h->correction = corr;
         h->precision = opts.precision;
         default_mapping(h);
-        if (opts.trsv_schedule == RLSQ_TRSV_LEVEL || opts.trsv_schedule == RLSQ_TRSV_SYNCFREE)
+        if (opts.trsv_schedule == RLSQ_TRSV_LEVEL || opts.trsv_schedule == RLSQ_TRSV_SYNCFREE ||
+            opts.trsv_schedule == RLSQ_TRSV_COOP)
             for (int w = 0; w < 4; ++w) h->map.sched[w] = opts.trsv_schedule;
         h->factored = true;
         if (opts.autotune) autotune(h);
@@ -831,12 +892,12 @@ int rlsq_apply(rlsq_problem h, const double* s, double* t, int32_t ptr_mode, voi
         put_state(h, S, initial_state(h, 0.0, 0), st);
         RLSQ_CUDA(cudaMemcpyAsync(h->s.p, s, sizeof(double) * h->n,
                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        RLSQ_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * h->n, st));
         enqueue_apply_any<true>(h, h->s.p, S, st, false);
         LsmrState hs;
         RLSQ_CUDA(cudaMemcpyAsync(h->pinned_state, S, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
-        RLSQ_CUDA(cudaMemcpyAsync(t, h->t.p, sizeof(double) * h->n,
-                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaMemcpy2DAsync(t, sizeof(double), reinterpret_cast<const double*>(h->tx.p),
+                                    sizeof(double2), sizeof(double), static_cast<size_t>(h->n),
+                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
         RLSQ_CUDA(cudaStreamSynchronize(st));
         hs = *h->pinned_state;
         if (dev) {
@@ -859,8 +920,8 @@ int rlsq_matvec(rlsq_problem h, int32_t trans, const double* x, double* y, int32
             RLSQ_CUDA(cudaEventRecord(h->ev[0], user));
             RLSQ_CUDA(cudaStreamWaitEvent(st, h->ev[0], 0));
         }
-        double* in = trans ? h->r.p : h->s.p;
-        double* outv = trans ? h->s.p : h->r.p;
+        double* in = trans ? h->b.p : h->s.p;
+        double* outv = trans ? h->s.p : h->b.p;
         RLSQ_CUDA(cudaMemcpyAsync(in, x, sizeof(double) * nin,
                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         const Csr<double> M = trans ? h->dAt.view() : h->dA.view();
@@ -898,22 +959,22 @@ int rlsq_trsv(rlsq_problem h, int32_t which, const double* b, double* x, int32_t
         put_state(h, S, initial_state(h, 0.0, 0), st);
         RLSQ_CUDA(cudaMemcpyAsync(h->s.p, b, sizeof(double) * n,
                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        RLSQ_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * n, st));
         RLSQ_CUDA(cudaMemsetAsync(h->tickets.p, 0, sizeof(unsigned) * kMaxSlots, st));
+        RLSQ_CUDA(cudaMemsetAsync(h->barriers.p, 0, sizeof(unsigned) * kMaxSlots, st));
         const int grid = grid_rows(h, n, 1);
         if (h->precision == RLSQ_PREC_FP32) {
             DevFactor<float>& F = h->f32;
             k_convert<float, double><<<grid, kBlock, 0, st>>>(n, h->s.p, F.vn[3].p);
             launch_trsv<float>(h, F, which, RHS_VEC, Rhs<float>{F.vn[3].p, nullptr, nullptr}, F.vn[4].p, 0,
                                S, st);
-            k_convert<double, float><<<grid, kBlock, 0, st>>>(n, F.vn[4].p, h->t.p);
+            k_convert<double, float><<<grid, kBlock, 0, st>>>(n, F.vn[4].p, h->h.p);
         } else {
             DevFactor<double>& F = h->f64;
-            launch_trsv<double>(h, F, which, RHS_VEC, Rhs<double>{h->s.p, nullptr, nullptr}, h->t.p, 0, S, st);
+            launch_trsv<double>(h, F, which, RHS_VEC, Rhs<double>{h->s.p, nullptr, nullptr}, h->h.p, 0, S, st);
         }
         RLSQ_CUDA(cudaGetLastError());
         RLSQ_CUDA(cudaMemcpyAsync(h->pinned_state, S, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
-        RLSQ_CUDA(cudaMemcpyAsync(x, h->t.p, sizeof(double) * n,
+        RLSQ_CUDA(cudaMemcpyAsync(x, h->h.p, sizeof(double) * n,
                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
         RLSQ_CUDA(cudaStreamSynchronize(st));
         if (dev) {
@@ -937,7 +998,6 @@ int rlsq_profile(rlsq_problem h, const double* b, int32_t warmup, int32_t iters,
         const int big = 1 << 30;
         RLSQ_CUDA(cudaMemcpyAsync(h->b.p, b, sizeof(double) * h->m, cudaMemcpyHostToDevice, st));
         put_state(h, S, initial_state(h, 0.0, big), st);
-        RLSQ_CUDA(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * h->n, st));
         enqueue_start(h, S, st, plain != 0);
         cudaGraphExec_t g1 = iteration_graph(h, 1, plain != 0);
         for (int i = 0; i < warmup; ++i) RLSQ_CUDA(cudaGraphLaunch(g1, st));
@@ -955,22 +1015,42 @@ int rlsq_profile(rlsq_problem h, const double* b, int32_t warmup, int32_t iters,
         cudaEventDestroy(e);
         out->total_ms = ms;
         out->iters = iters;
-        // one eager iteration with an event pair around every launch
+        // Per-kernel times: one iteration captured with an event-record node
+        // before and after every launch, replayed `iters` times; the graph runs
+        // exactly like the timed one, so no host gap enters the times.
         std::unique_ptr<Recorder> rec(new Recorder());
         h->rec = rec.get();
+        cudaGraph_t pg = nullptr;
+        RLSQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
             enqueue_iteration(h, S, st, plain != 0);
         } catch (...) {
             h->rec = nullptr;
+            cudaStreamEndCapture(st, &pg);
+            if (pg) cudaGraphDestroy(pg);
             throw;
         }
         h->rec = nullptr;
-        RLSQ_CUDA(cudaStreamSynchronize(st));
-        for (auto& en : rec->entries) {
-            float t = 0.f;
-            RLSQ_CUDA(cudaEventElapsedTime(&t, en.a, en.b));
-            out->class_ms[en.cls] += t;
-            out->class_launches[en.cls] += 1;
+        RLSQ_CUDA(cudaStreamEndCapture(st, &pg));
+        cudaGraphExec_t pex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&pex, pg, 0);
+        cudaGraphDestroy(pg);
+        if (ie != cudaSuccess) throw_cuda(ie, "cudaGraphInstantiate", __LINE__);
+        std::vector<double> acc(rec->entries.size(), 0.0);
+        for (int i = 0; i < iters; ++i) {
+            RLSQ_CUDA(cudaGraphLaunch(pex, st));
+            RLSQ_CUDA(cudaStreamSynchronize(st));
+            for (size_t q = 0; q < rec->entries.size(); ++q) {
+                float t = 0.f;
+                RLSQ_CUDA(cudaEventElapsedTime(&t, rec->entries[q].a, rec->entries[q].b));
+                acc[q] += t;
+            }
+        }
+        cudaGraphExecDestroy(pex);
+        for (size_t q = 0; q < rec->entries.size(); ++q) {
+            const auto& en = rec->entries[q];
+            out->class_ms[en.cls] += acc[q] / iters;
+            out->class_launches[en.cls] += en.launches;
             out->class_bytes[en.cls] += en.bytes;
         }
         LsmrState hs;

@@ -112,7 +112,7 @@ SOLVES = [(B.SYS_L1, "solve_L1"), (B.SYS_L1T, "solve_L1t"), (B.SYS_U, "solve_U")
           (B.SYS_UT, "solve_Ut")]
 
 
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP])
 @pytest.mark.parametrize("which", ["cfg0", "mid"])
 def test_triangular_solves(sched, which, request):
     prob = request.getfixturevalue(which)
@@ -140,7 +140,7 @@ def test_triangular_solves_all_lane_counts(cfg0):
 # one preconditioner application, every correction mode
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("modes", MODES, ids=["NONE", "SI", "CG", "DENSE"])
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP])
 def test_apply_fp64(cfg0, modes, sched):
     bm, om = modes
     P = make(cfg0, bm, sched=sched)
