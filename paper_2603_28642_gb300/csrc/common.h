@@ -145,7 +145,15 @@ struct Recorder {
 struct rlsq_problem_s {
     int64_t m = 0, n = 0, nnz = 0;
     rlsq::HostCSR A;                 // host copy (the set-up runs on the host)
-    rlsq::DevCsr<double> dA, dAt;    // CSR and CSC (= CSR of A^T) of A
+    rlsq::DevCsr<double> dA, dAt;    // CSR and CSC (= CSR of A^T) of the sparse rows, internal row order
+    // Dense rows (sparse-dense problems): rows with many nonzeros sit at the end
+    // of the internal row order (empty in dA) and are kept row-major in Ad.
+    int64_t ms = 0, md = 0;          // sparse and dense row counts (ms + md = m)
+    std::vector<int32_t> row_perm;   // internal row i holds user row row_perm[i] (empty: identity)
+    rlsq::DevArray<int32_t> row_perm_d;
+    rlsq::DevArray<double> Ad;       // md x n
+    rlsq::DevArray<double2> dense_part, dense_av, dense_atv;
+    int dense_chunks = 0;
     double anorm = 0.0;
     cudaStream_t stream = nullptr;   // internal stream
     int device = 0;

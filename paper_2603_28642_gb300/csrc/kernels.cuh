@@ -208,10 +208,13 @@ __device__ __forceinline__ void row_dot_pair(const Csr<TV>& a, int row, int lane
 // qr[i] = (q_i, r_i) with u = q * inv_beta.
 // q <- A v^ - alpha u  (= beta_{k+2} u_{k+2}),  r <- b - A x_k
 // totals: beta = ||q||, rnorm = ||r||
+// Dense rows (ms <= row < m, empty in the CSR) take their two products from
+// dense_av (the dense-row GEMV ran just before); dense_av = nullptr if none.
 template <int G>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__ qr,
-            const double* __restrict__ b, LsmrState* S, double* part, unsigned* counter) {
+            const double* __restrict__ b, LsmrState* S, double* part, unsigned* counter,
+            int ms = 0, const double2* __restrict__ dense_av = nullptr) {
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, alpha = S->alpha, inv_beta = S->inv_beta;
     const unsigned mask = group_mask<G>();
@@ -226,6 +229,11 @@ k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__
             s2 = group_sum<G>(s2, mask);
         }
         if (lane == 0) {
+            if (dense_av && row >= ms) {
+                const double2 dv = dense_av[row - ms];
+                s1 += dv.x;
+                s2 += dv.y;
+            }
             const double2 old = qr[row];
             const double qn = s1 * inv_alpha - alpha * (old.x * inv_beta);
             const double rr = b[row] - s2;
@@ -246,10 +254,12 @@ k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__
 // s <- A^T q * inv_beta - beta * (s * inv_alpha)      [s of the next apply]
 // z  = A^T r                                            [only its norm]
 // totals: arnorm = ||z||; ratio check on x_k; FIRST: s = A^T q * inv_beta.
+// dense_atv[col] (nullptr if no dense rows): the dense rows' contribution
+// to A^T u and A^T r, computed just before.
 template <int G, bool FIRST>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 k_spmvt_lsmr(Csr<double> At, const double2* __restrict__ qr, double* __restrict__ s, LsmrState* S,
-             double* part, unsigned* counter) {
+             double* part, unsigned* counter, const double2* __restrict__ dense_atv = nullptr) {
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, beta = S->beta, inv_beta = S->inv_beta;
     const unsigned mask = group_mask<G>();
@@ -264,6 +274,11 @@ k_spmvt_lsmr(Csr<double> At, const double2* __restrict__ qr, double* __restrict_
             s2 = group_sum<G>(s2, mask);
         }
         if (lane == 0) {
+            if (dense_atv) {
+                const double2 dv = dense_atv[col];
+                s1 += dv.x;
+                s2 += dv.y;
+            }
             s[col] = FIRST ? s1 * inv_beta : s1 * inv_beta - beta * (s[col] * inv_alpha);
             acc[0] += s2 * s2;
         }
@@ -282,6 +297,109 @@ k_spmvt_lsmr(Csr<double> At, const double2* __restrict__ qr, double* __restrict_
             S->status = kErrMaxit;
         }
     }
+}
+
+struct PowerState {
+    double lambda, inv_lambda;
+};
+
+// ---------------------------------------------------------------------------
+// dense-row block (sparse-dense problems, Sec. 3.3): Ad is m_d x n row-major
+// ---------------------------------------------------------------------------
+constexpr int kDenseChunk = 1024;  // columns per block of the A_d products
+constexpr int kDenseRowsPerBlock = kBlock / 32;
+
+// Partial dot products of every dense row with (v1, v2) over one chunk of
+// columns: PAIR reads (v1, v2) = p[j], otherwise (v, 0).  One warp per dense
+// row; the chunk of the vector is staged in shared memory once per block.
+template <bool PAIR>
+__global__ void __launch_bounds__(kBlock)
+k_dense_av(const double* __restrict__ Ad, int md, int n, const void* __restrict__ vin,
+           double2* __restrict__ part, const LsmrState* S) {
+    if (S && S->done) return;
+    __shared__ double2 vs[kDenseChunk];
+    const int c0 = blockIdx.x * kDenseChunk;
+    const int cn = min(kDenseChunk, n - c0);
+    for (int i = threadIdx.x; i < cn; i += kBlock) {
+        if (PAIR) vs[i] = reinterpret_cast<const double2*>(vin)[c0 + i];
+        else vs[i] = make_double2(reinterpret_cast<const double*>(vin)[c0 + i], 0.0);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.y * kDenseRowsPerBlock + warp;
+    if (r >= md) return;
+    const double* a = Ad + (size_t)r * n + c0;
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = lane; i < cn; i += 32) {
+        const double av = a[i];
+        s1 += av * vs[i].x;
+        s2 += av * vs[i].y;
+    }
+    s1 = group_sum<32>(s1, 0xffffffffu);
+    s2 = group_sum<32>(s2, 0xffffffffu);
+    if (lane == 0) part[(size_t)r * gridDim.x + blockIdx.x] = make_double2(s1, s2);
+}
+
+// Sums the chunk partials of each dense row in chunk order.
+static __global__ void __launch_bounds__(kBlock)
+k_dense_av_finish(int md, int nchunks, const double2* __restrict__ part, double2* __restrict__ out,
+                  const LsmrState* S) {
+    if (S && S->done) return;
+    const int r = blockIdx.x * kBlock + threadIdx.x;
+    if (r >= md) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+        const double2 p = part[(size_t)r * nchunks + c];
+        s1 += p.x;
+        s2 += p.y;
+    }
+    out[r] = make_double2(s1, s2);
+}
+
+// out[j] = (sum_r Ad[r, j] u1[r], sum_r Ad[r, j] u2[r]) with (u1, u2) = u[r]
+// (PAIR) or (u[r], 0); one thread per column, dense rows in order, the u
+// values staged in shared memory (dynamic, 16 * md bytes).
+template <bool PAIR>
+__global__ void __launch_bounds__(kBlock)
+k_dense_atv(const double* __restrict__ Ad, int md, int n, const void* __restrict__ uin,
+            double2* __restrict__ out, const LsmrState* S) {
+    if (S && S->done) return;
+    extern __shared__ double2 us[];
+    for (int i = threadIdx.x; i < md; i += kBlock) {
+        if (PAIR) us[i] = reinterpret_cast<const double2*>(uin)[i];
+        else us[i] = make_double2(reinterpret_cast<const double*>(uin)[i], 0.0);
+    }
+    __syncthreads();
+    for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int r = 0; r < md; ++r) {
+            const double av = Ad[(size_t)r * n + j];
+            s1 += av * us[r].x;
+            s2 += av * us[r].y;
+        }
+        out[j] = make_double2(s1, s2);
+    }
+}
+
+// y[j] += add[j].x (plain products with the dense block)
+static __global__ void k_add_x(int n, const double2* __restrict__ add, double* __restrict__ y) {
+    for (int j = blockIdx.x * kBlock + threadIdx.x; j < n; j += gridDim.x * kBlock) y[j] += add[j].x;
+}
+// y[ms + r] = d[r].x * scale (scale = P->inv_lambda when P is given)
+static __global__ void k_put_dense(int md, int ms, const double2* __restrict__ d, double* __restrict__ y,
+                            const PowerState* P) {
+    const int r = blockIdx.x * kBlock + threadIdx.x;
+    if (r < md) y[ms + r] = d[r].x * (P ? P->inv_lambda : 1.0);
+}
+// out[i] = in[perm[i]]
+static __global__ void k_gather(int m, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                         double* __restrict__ out) {
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < m; i += gridDim.x * kBlock) out[i] = in[perm[i]];
+}
+// out[perm[i]] = in[i]
+static __global__ void k_scatter(int m, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                          double* __restrict__ out) {
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < m; i += gridDim.x * kBlock) out[perm[i]] = in[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -890,9 +1008,6 @@ __global__ void k_convert(int n, const TI* __restrict__ a, TO* __restrict__ b) {
 // ---------------------------------------------------------------------------
 // plain products and the power method for ||A||_2
 // ---------------------------------------------------------------------------
-struct PowerState {
-    double lambda, inv_lambda;
-};
 
 // y = A (v * scale) with scale = inv_lambda (1/sqrt(n) at start via v)
 template <int G>
@@ -913,7 +1028,7 @@ k_power_av(Csr<double> A, const double* __restrict__ v, double* __restrict__ y, 
 template <int G>
 __global__ void __launch_bounds__(kBlock)
 k_power_atv(Csr<double> At, const double* __restrict__ y, double* __restrict__ w, PowerState* P,
-            double* part, unsigned* counter) {
+            double* part, unsigned* counter, const double2* __restrict__ dense_atv = nullptr) {
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
     const int groups = (gridDim.x * kBlock) / G;
@@ -923,6 +1038,7 @@ k_power_atv(Csr<double> At, const double* __restrict__ y, double* __restrict__ w
         row_dot<G>(At, row, lane, y, s);
         s = group_sum<G>(s, mask);
         if (lane == 0) {
+            if (dense_atv) s += dense_atv[row].x;
             w[row] = s;
             acc[0] += s * s;
         }

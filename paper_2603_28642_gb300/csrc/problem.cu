@@ -134,6 +134,12 @@ static int grid_rows(const rlsq_problem_s* P, int64_t rows, int G) {
 }
 
 static LsmrState* state_ptr(rlsq_problem_s* P, int which) { return P->S.p + which; }
+
+// dense-row block products (defined with the A layout below)
+template <bool PAIR>
+static void enqueue_dense_av(rlsq_problem_s* P, const void* v, const LsmrState* S, cudaStream_t st);
+template <bool PAIR>
+static void enqueue_dense_atv(rlsq_problem_s* P, const void* u, const LsmrState* S, cudaStream_t st);
 static int* error_word(LsmrState* S) {
     return reinterpret_cast<int*>(reinterpret_cast<char*>(S) + offsetof(LsmrState, error));
 }
@@ -353,19 +359,31 @@ static void enqueue_apply_any(rlsq_problem_s* P, const double* s, LsmrState* S, 
 
 static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
     const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
+    const bool dense = P->md > 0;
+    const double dense_bytes = 8.0 * static_cast<double>(P->md) * static_cast<double>(P->n) + 16.0 * P->n;
+    if (dense) {
+        RecScope rs(P, RLSQ_KCLASS_DENSE, dense_bytes, st);
+        enqueue_dense_av<true>(P, P->tx.p, S, st);
+    }
     {
         RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 16.0, 32.0), st);
         with_G(P->map.G_A, [&](auto g) {
             k_spmv_lsmr<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
-                P->dA.view(), P->tx.p, P->qr.p, P->b.p, S, P->part.p, P->counter.p);
+                P->dA.view(), P->tx.p, P->qr.p, P->b.p, S, P->part.p, P->counter.p, static_cast<int>(P->ms),
+                dense ? P->dense_av.p : nullptr);
         });
+    }
+    if (dense) {
+        RecScope rs(P, RLSQ_KCLASS_DENSE, dense_bytes, st);
+        enqueue_dense_atv<true>(P, P->qr.p + P->ms, S, st);
     }
     {
         RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 16.0, 16.0), st);
         with_G(P->map.G_At, [&](auto g) {
             k_spmvt_lsmr<decltype(g)::value, false>
                 <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
-                                                                        P->part.p, P->counter.p);
+                                                                        P->part.p, P->counter.p,
+                                                                        dense ? P->dense_atv.p : nullptr);
         });
     }
     enqueue_apply_any<false>(P, P->s.p, S, st, plain);
@@ -376,10 +394,13 @@ static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, 
 static void enqueue_start(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
     const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
     k_start_b<0><<<grid_rows(P, m, 1), kBlock, 0, st>>>(m, P->b.p, P->qr.p, S, P->part.p, P->counter.p);
+    const bool dense = P->md > 0;
+    if (dense) enqueue_dense_atv<true>(P, P->qr.p + P->ms, S, st);
     with_G(P->map.G_At, [&](auto g) {
         k_spmvt_lsmr<decltype(g)::value, true>
             <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
-                                                                    P->part.p, P->counter.p);
+                                                                    P->part.p, P->counter.p,
+                                                                    dense ? P->dense_atv.p : nullptr);
     });
     enqueue_apply_any<true>(P, P->s.p, S, st, plain);
     k_lsmr_update<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, P->hb.p, S);
@@ -438,7 +459,9 @@ static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain)
 
 static double algorithmic_bytes(const rlsq_problem_s* P, bool plain) {
     const double m = static_cast<double>(P->m), n = static_cast<double>(P->n);
-    double bytes = 2.0 * 12.0 * static_cast<double>(P->nnz) + 4.0 * (m + n);  // A, A^T: values, indices, pointers
+    const double dnnz = static_cast<double>(P->md) * n;
+    double bytes = 2.0 * 12.0 * (static_cast<double>(P->nnz) - dnnz) + 4.0 * (m + n);  // sparse A, A^T
+    bytes += 2.0 * 8.0 * dnnz;  // dense-row block, once for A and once for A^T
     bytes += 8.0 * (2 * n + 4 * m);   // SpMV: gathers of v^ and x, q in/out, b in, r out
     bytes += 8.0 * (2 * m + 2 * n);   // SpMV^T: gathers of u and r, s in/out
     bytes += 8.0 * 7 * n;             // LSMR update: t, h, h-bar, x in; h, h-bar, x out
@@ -467,6 +490,7 @@ static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
     info->m = P->m;
     info->n = P->n;
     info->nnz_A = P->nnz;
+    info->n_dense_rows = P->md;
     info->anorm = P->anorm;
     info->correction = P->correction;
     info->precision = P->precision;
@@ -483,6 +507,18 @@ static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
         info->levels_Ut = F.lev_Ut.nlevels;
     }
     info->bytes_per_iter = algorithmic_bytes(P, !P->factored);
+}
+
+// b (user row order) -> P->b (internal row order: dense rows last)
+static void upload_b(rlsq_problem_s* P, const double* b, bool dev, cudaStream_t st) {
+    const auto kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (P->md == 0) {
+        RLSQ_CUDA(cudaMemcpyAsync(P->b.p, b, sizeof(double) * P->m, kind, st));
+        return;
+    }
+    double* tmp = reinterpret_cast<double*>(P->qr.p);  // 2m doubles, free before the solve starts
+    RLSQ_CUDA(cudaMemcpyAsync(tmp, b, sizeof(double) * P->m, kind, st));
+    k_gather<<<grid_rows(P, P->m, 1), kBlock, 0, st>>>(static_cast<int>(P->m), P->row_perm_d.p, tmp, P->b.p);
 }
 
 // Moves b in, runs LSMR, moves x out.
@@ -503,8 +539,7 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
         RLSQ_CUDA(cudaEventRecord(P->ev[0], user));
         RLSQ_CUDA(cudaStreamWaitEvent(st, P->ev[0], 0));
     }
-    RLSQ_CUDA(cudaMemcpyAsync(P->b.p, b, sizeof(double) * P->m,
-                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    upload_b(P, b, dev, st);
     LsmrState* S = state_ptr(P, 0);
     put_state(P, S, initial_state(P, opts.atol, opts.maxit), st);
     enqueue_start(P, S, st, plain);
@@ -568,6 +603,97 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
     return status;
 }
 
+// Splits A into sparse rows (CSR + CSC, internal order: sparse rows first in
+// user order, dense rows last and empty) and a dense row-major block.  A row
+// is dense when it has at least `threshold` nonzeros (threshold <= 0: no
+// dense rows); at most kMaxDenseRows rows are taken, densest first.
+constexpr int64_t kMaxDenseRows = 3000;  // the A^T kernel keeps them in 48 KB of shared memory
+
+static int64_t auto_dense_threshold(const HostCSR& A) {
+    std::vector<int64_t> len(static_cast<size_t>(A.rows));
+    for (int64_t i = 0; i < A.rows; ++i) len[i] = A.ptr[i + 1] - A.ptr[i];
+    std::nth_element(len.begin(), len.begin() + len.size() / 2, len.end());
+    const int64_t med = len[len.size() / 2];
+    return std::max<int64_t>(64, 16 * std::max<int64_t>(med, 1));
+}
+
+static void layout_A(rlsq_problem_s* P, int64_t threshold) {
+    const HostCSR& A = P->A;
+    const int64_t m = A.rows, n = A.cols;
+    std::vector<int32_t> dense;
+    if (threshold > 0)
+        for (int64_t i = 0; i < m; ++i)
+            if (A.ptr[i + 1] - A.ptr[i] >= threshold) dense.push_back(static_cast<int32_t>(i));
+    if (static_cast<int64_t>(dense.size()) > kMaxDenseRows) {
+        std::stable_sort(dense.begin(), dense.end(), [&](int32_t a, int32_t b) {
+            return A.ptr[a + 1] - A.ptr[a] > A.ptr[b + 1] - A.ptr[b];
+        });
+        dense.resize(kMaxDenseRows);
+        std::sort(dense.begin(), dense.end());
+    }
+    cudaStream_t st = P->stream;
+    P->md = static_cast<int64_t>(dense.size());
+    P->ms = m - P->md;
+    if (P->md == 0) {
+        P->row_perm.clear();
+        P->row_perm_d.release();
+        P->Ad.release();
+        P->dA.upload(A, st);
+        P->dAt.upload(transpose(A), st);
+        return;
+    }
+    std::vector<char> is_dense(static_cast<size_t>(m), 0);
+    for (int32_t r : dense) is_dense[r] = 1;
+    P->row_perm.clear();
+    for (int64_t i = 0; i < m; ++i)
+        if (!is_dense[i]) P->row_perm.push_back(static_cast<int32_t>(i));
+    for (int32_t r : dense) P->row_perm.push_back(r);
+    HostCSR S;
+    S.rows = m;
+    S.cols = n;
+    S.ptr.assign(static_cast<size_t>(m) + 1, 0);
+    for (int64_t i = 0; i < P->ms; ++i) {
+        const int32_t r = P->row_perm[i];
+        for (int64_t e = A.ptr[r]; e < A.ptr[r + 1]; ++e) {
+            S.idx.push_back(A.idx[e]);
+            S.val.push_back(A.val[e]);
+        }
+        S.ptr[i + 1] = static_cast<int64_t>(S.idx.size());
+    }
+    for (int64_t i = P->ms; i < m; ++i) S.ptr[i + 1] = S.ptr[i];
+    P->dA.upload(S, st);
+    P->dAt.upload(transpose(S), st);
+    std::vector<double> ad(static_cast<size_t>(P->md * n), 0.0);
+    for (int64_t q = 0; q < P->md; ++q) {
+        const int32_t r = dense[q];
+        for (int64_t e = A.ptr[r]; e < A.ptr[r + 1]; ++e) ad[q * n + A.idx[e]] = A.val[e];
+    }
+    P->Ad.upload(ad.data(), ad.size(), st);
+    P->row_perm_d.upload(P->row_perm.data(), P->row_perm.size(), st);
+    P->dense_chunks = static_cast<int>((n + kDenseChunk - 1) / kDenseChunk);
+    P->dense_part.alloc(static_cast<size_t>(P->md * P->dense_chunks));
+    P->dense_av.alloc(static_cast<size_t>(P->md));
+    P->dense_atv.alloc(static_cast<size_t>(n));
+    RLSQ_CUDA(cudaStreamSynchronize(st));
+}
+
+// A_d (v1, v2) -> dense_av; PAIR reads interleaved pairs, else (v, 0).
+template <bool PAIR>
+static void enqueue_dense_av(rlsq_problem_s* P, const void* v, const LsmrState* S, cudaStream_t st) {
+    const int md = static_cast<int>(P->md), n = static_cast<int>(P->n);
+    dim3 grid(static_cast<unsigned>(P->dense_chunks), static_cast<unsigned>((md + kDenseRowsPerBlock - 1) / kDenseRowsPerBlock));
+    k_dense_av<PAIR><<<grid, kBlock, 0, st>>>(P->Ad.p, md, n, v, P->dense_part.p, S);
+    k_dense_av_finish<<<(md + kBlock - 1) / kBlock, kBlock, 0, st>>>(md, P->dense_chunks, P->dense_part.p,
+                                                                    P->dense_av.p, S);
+}
+// A_d^T (u1, u2) -> dense_atv; u points at the dense rows' entries
+template <bool PAIR>
+static void enqueue_dense_atv(rlsq_problem_s* P, const void* u, const LsmrState* S, cudaStream_t st) {
+    const int md = static_cast<int>(P->md), n = static_cast<int>(P->n);
+    const int grid = static_cast<int>(std::min<int64_t>((n + kBlock - 1) / kBlock, max_grid(P)));
+    k_dense_atv<PAIR><<<grid, kBlock, sizeof(double2) * md, st>>>(P->Ad.p, md, n, u, P->dense_atv.p, S);
+}
+
 // ||A||_2 by 50 power iterations on A^T A from v = 1/sqrt(n) (Sec. 5.1)
 static double power_norm(rlsq_problem_s* P, int iters) {
     cudaStream_t st = P->stream;
@@ -581,14 +707,21 @@ static double power_norm(rlsq_problem_s* P, int iters) {
     RLSQ_CUDA(cudaMemcpyAsync(v.p, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     PowerState p0{0.0, 1.0};
     RLSQ_CUDA(cudaMemcpyAsync(ps.p, &p0, sizeof(p0), cudaMemcpyHostToDevice, st));
+    const bool dense = P->md > 0;
     for (int it = 0; it < iters; ++it) {
         with_G(P->map.G_A, [&](auto g) {
             k_power_av<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
                 P->dA.view(), v.p, y.p, ps.p);
         });
+        if (dense) {
+            enqueue_dense_av<false>(P, v.p, nullptr, st);
+            k_put_dense<<<static_cast<int>((P->md + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+                static_cast<int>(P->md), static_cast<int>(P->ms), P->dense_av.p, y.p, ps.p);
+            enqueue_dense_atv<false>(P, y.p + P->ms, nullptr, st);
+        }
         with_G(P->map.G_At, [&](auto g) {
             k_power_atv<decltype(g)::value><<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(
-                P->dAt.view(), y.p, v.p, ps.p, P->part.p, P->counter.p);
+                P->dAt.view(), y.p, v.p, ps.p, P->part.p, P->counter.p, dense ? P->dense_atv.p : nullptr);
         });
     }
     PowerState out;
@@ -769,8 +902,7 @@ int rlsq_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* coli
         RLSQ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&P->pinned_state), sizeof(LsmrState)));
         RLSQ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&P->pinned_done), 2 * sizeof(int)));
         cudaStream_t st = P->stream;
-        P->dA.upload(A, st);
-        P->dAt.upload(transpose(A), st);
+        layout_A(P.get(), auto_dense_threshold(A));
         P->qr.alloc(static_cast<size_t>(m));
         P->tx.alloc(static_cast<size_t>(n));
         P->b.alloc(static_cast<size_t>(m));
@@ -846,6 +978,11 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         h->f32.clear();
         if (opts.precision == RLSQ_PREC_FP32) h->f32.upload(*F, sinv, st);
         else h->f64.upload(*F, sinv, st);
+        if (opts.dense_row_min != 0) {
+            // an explicit dense-row threshold (< 0: none) replaces the automatic one
+            layout_A(h, opts.dense_row_min);
+            h->anorm = power_norm(h, 50);
+        }
         h->F = std::move(F);
         h->opts = opts;
         h->correction = corr;
@@ -922,14 +1059,33 @@ int rlsq_matvec(rlsq_problem h, int32_t trans, const double* x, double* y, int32
         }
         double* in = trans ? h->b.p : h->s.p;
         double* outv = trans ? h->s.p : h->b.p;
-        RLSQ_CUDA(cudaMemcpyAsync(in, x, sizeof(double) * nin,
-                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        double* tmp = reinterpret_cast<double*>(h->qr.p);  // 2m doubles
+        const bool dense = h->md > 0;
+        const auto kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (trans && dense) {
+            // user row order -> internal order
+            RLSQ_CUDA(cudaMemcpyAsync(tmp, x, sizeof(double) * nin, kind, st));
+            k_gather<<<grid_rows(h, h->m, 1), kBlock, 0, st>>>(static_cast<int>(h->m), h->row_perm_d.p, tmp, in);
+        } else {
+            RLSQ_CUDA(cudaMemcpyAsync(in, x, sizeof(double) * nin, kind, st));
+        }
         const Csr<double> M = trans ? h->dAt.view() : h->dA.view();
         const int G = trans ? h->map.G_At : h->map.G_A;
         with_G(G, [&](auto g) {
             k_csr_mv<double, decltype(g)::value><<<grid_rows(h, nout, decltype(g)::value), kBlock, 0, st>>>(
                 M, in, outv, nullptr);
         });
+        if (dense && !trans) {
+            enqueue_dense_av<false>(h, in, nullptr, st);
+            k_put_dense<<<static_cast<int>((h->md + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+                static_cast<int>(h->md), static_cast<int>(h->ms), h->dense_av.p, outv, nullptr);
+            // internal order -> user row order
+            k_scatter<<<grid_rows(h, h->m, 1), kBlock, 0, st>>>(static_cast<int>(h->m), h->row_perm_d.p, outv, tmp);
+            outv = tmp;
+        } else if (dense && trans) {
+            enqueue_dense_atv<false>(h, in + h->ms, nullptr, st);
+            k_add_x<<<grid_rows(h, h->n, 1), kBlock, 0, st>>>(static_cast<int>(h->n), h->dense_atv.p, outv);
+        }
         RLSQ_CUDA(cudaGetLastError());
         RLSQ_CUDA(cudaMemcpyAsync(y, outv, sizeof(double) * nout,
                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
@@ -996,7 +1152,7 @@ int rlsq_profile(rlsq_problem h, const double* b, int32_t warmup, int32_t iters,
         cudaStream_t st = h->stream;
         LsmrState* S = state_ptr(h, 0);
         const int big = 1 << 30;
-        RLSQ_CUDA(cudaMemcpyAsync(h->b.p, b, sizeof(double) * h->m, cudaMemcpyHostToDevice, st));
+        upload_b(h, b, false, st);
         put_state(h, S, initial_state(h, 0.0, big), st);
         enqueue_start(h, S, st, plain != 0);
         cudaGraphExec_t g1 = iteration_graph(h, 1, plain != 0);

@@ -277,3 +277,55 @@ def test_bad_input_errors():
     with pytest.raises(B.RlsqError) as e:
         P.solve(prob.b)
     assert e.value.code == -5
+
+
+# ---------------------------------------------------------------------------
+# sparse-dense problems: dense rows go through the dense-row GEMV block
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def sparse_dense():
+    # 20,000 sparse rows (6 per row + hidden +-4) and 50 full rows over n = 10,000
+    return synth.sparse_dense_problem(20_000, 10_000, 6, 50, seed=2)
+
+
+def test_dense_rows_detected_and_products(sparse_dense):
+    prob = sparse_dense
+    P = B.Problem.from_problem(prob)
+    assert P.info()["n_dense_rows"] == 50
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(prob.n)
+    y = rng.standard_normal(prob.m)
+    absA = abs(prob.to_scipy())
+    ax = P.matvec(x)
+    ref = oracle.spmv(prob.m, prob.rowptr, prob.colidx, prob.vals, x)
+    assert np.all(np.abs(ax - ref) <= 1e-13 * (absA @ np.abs(x)) + 1e-300)
+    aty = P.matvec(y, trans=True)
+    ref_t = oracle.spmv_t(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, y)
+    assert np.all(np.abs(aty - ref_t) <= 1e-13 * (absA.T @ np.abs(y)) + 1e-300)
+    assert P.info()["anorm"] == pytest.approx(
+        oracle.norm2(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, 50), rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", [B.PREC_FP64, B.PREC_FP32])
+def test_sparse_dense_solve(sparse_dense, prec):
+    prob = sparse_dense
+    P = make(prob, B.CORR_CG, prec=prec)
+    prow, a2, _, _ = P.split()
+    assert set(prob.dense_rows.tolist()) <= set(a2.tolist())  # Sec. 3.3: dense rows land in A2
+    f = oracle_factor(prob, oracle.CG)
+    ref = oracle.lsmr(f, prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, prob.b)
+    res = P.solve(prob.b)
+    if prec == B.PREC_FP64:
+        _check_solve(prob, res, ref)
+    else:
+        assert res.status == 0 and rel(res.x, ref.x) <= 1e-6
+
+
+def test_dense_block_off_gives_same_solution(sparse_dense):
+    prob = sparse_dense
+    on = make(prob, B.CORR_NONE).solve(prob.b)
+    off = make(prob, B.CORR_NONE, dense_row_min=-1)
+    assert off.info()["n_dense_rows"] == 0
+    res = off.solve(prob.b)
+    assert res.info["iterations"] == on.info["iterations"]
+    assert rel(res.x, on.x) <= 1e-10
