@@ -118,17 +118,19 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 // Every block contributes NV partial sums; the last block to finish adds the
 // partials in block order (deterministic) and returns true with the totals
 // in `tot` (thread 0 only; the whole last block returns true).
+// (bid, nblocks) name this block among the blocks that reduce together: the
+// whole grid for a single problem, one slot's blocks in a batch.
 template <int NV>
-__device__ bool last_block_total(double (&v)[NV], double* part, unsigned* counter,
-                                 double (&tot)[NV]) {
+__device__ bool last_block_total_ctx(double (&v)[NV], double* part, unsigned* counter,
+                                     double (&tot)[NV], unsigned bid, unsigned nblocks) {
     block_sum<NV>(v);
     __shared__ bool is_last;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) part[(size_t)blockIdx.x * NV + i] = v[i];
+        for (int i = 0; i < NV; ++i) part[(size_t)bid * NV + i] = v[i];
         __threadfence();
         const unsigned prev = atomicAdd(counter, 1u);
-        is_last = (prev == gridDim.x - 1);
+        is_last = (prev == nblocks - 1);
     }
     __syncthreads();
     if (!is_last) return false;
@@ -136,7 +138,7 @@ __device__ bool last_block_total(double (&v)[NV], double* part, unsigned* counte
     double acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x)
 #pragma unroll
         for (int i = 0; i < NV; ++i) acc[i] += ld_l2(&part[(size_t)b * NV + i]);
     block_sum<NV>(acc);
@@ -146,6 +148,12 @@ __device__ bool last_block_total(double (&v)[NV], double* part, unsigned* counte
         *counter = 0u;
     }
     return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool last_block_total(double (&v)[NV], double* part, unsigned* counter,
+                                                 double (&tot)[NV]) {
+    return last_block_total_ctx<NV>(v, part, counter, tot, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -885,29 +893,17 @@ k_dense_gemv(int m2, const T* __restrict__ Sinv, const T* __restrict__ e, T* __r
 // end of the apply and the LSMR vector updates (float64)
 // ---------------------------------------------------------------------------
 
-// t = d * g5 (IDENT: t = s, the unpreconditioned case), <t, s>; INIT: start the recurrences, else one LSMR
-// rotation step; either way the apply counter advances.
-template <typename T, bool INIT, bool IDENT = false>
-__global__ void __launch_bounds__(kBlock)
-k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const double* __restrict__ s,
-               double2* __restrict__ tx, LsmrState* S, double* part, unsigned* counter) {
-    if (S->done) return;
-    double* t = reinterpret_cast<double*>(tx);  // t_i lives at tx[i].x
-    double acc[1] = {0.0};
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
-        const double ti = IDENT ? s[i] : (double)(d[i] * g5[i]);
-        t[2 * i] = ti;
-        acc[0] += ti * s[i];
-    }
-    double tot[1];
-    if (!(last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0)) return;
+// Advances the LSMR scalars after <t, s> is known (INIT: the first alpha, else
+// one pair of rotations P_k, Pbar_k and the update coefficients); also counts
+// the application and maps a device wait timeout to the solve's status.
+template <bool INIT>
+__device__ void lsmr_scalar_step(LsmrState* S, double ts) {
     S->apply_count += 1;
     if (S->error != 0) {
         S->done = 1;
         S->status = kErrTimeout;
         return;
     }
-    const double ts = tot[0];
     S->ts = ts;
     if (!(ts >= 0.0) || !isfinite(ts)) {
         S->done = 1;
@@ -949,6 +945,25 @@ k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const d
     }
     S->alpha = alpha;
     S->inv_alpha = alpha > 0.0 ? 1.0 / alpha : 0.0;
+}
+
+// t = d * g5 (IDENT: t = s, the unpreconditioned case), <t, s>; INIT: start the recurrences, else one LSMR
+// rotation step; either way the apply counter advances.
+template <typename T, bool INIT, bool IDENT = false>
+__global__ void __launch_bounds__(kBlock)
+k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const double* __restrict__ s,
+               double2* __restrict__ tx, LsmrState* S, double* part, unsigned* counter) {
+    if (S->done) return;
+    double* t = reinterpret_cast<double*>(tx);  // t_i lives at tx[i].x
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+        const double ti = IDENT ? s[i] : (double)(d[i] * g5[i]);
+        t[2 * i] = ti;
+        acc[0] += ti * s[i];
+    }
+    double tot[1];
+    if (!(last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0)) return;
+    lsmr_scalar_step<INIT>(S, tot[0]);
 }
 
 // INIT: h = v^_1, h-bar = 0, x = 0.  Else: h-bar, x, h updates, k += 1.
