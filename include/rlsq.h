@@ -108,6 +108,9 @@ typedef struct {
                               rows and multiplied by a dense-row GEMV block; 0 = automatic,
                               < 0 = never */
     int32_t host_threads;  /* threads for the dense S set-up (0 = hardware concurrency) */
+    int32_t level_merge;   /* levels fused per group in the triangular solves: 1 = none,
+                              k > 1 = groups of k levels (same-group dependencies are
+                              substituted on the host), 0 = chosen per system */
 } rlsq_factor_opts;
 
 /* Options of a solve. */
@@ -134,6 +137,8 @@ typedef struct {
     int32_t correction;    /* the resolved mode */
     int32_t precision;
     double bytes_per_iter; /* algorithmic HBM bytes of one LSMR iteration */
+    int32_t solve_levels[4]; /* levels the GPU walks per system after fusing (RLSQ_SYS_* order) */
+    int32_t level_merge[4];  /* fused levels per group, per system */
 } rlsq_info;
 
 /* Server options and statistics (continuous batching of right-hand sides). */
@@ -155,7 +160,8 @@ typedef struct {
 /* ---- defaults -------------------------------------------------------------- */
 /* p = 10, tau = 1e-2, mu = 0.1, small = 1e-10 (the paper's values, Sec. 5.2),
    scale_columns = 1, correction = AUTO, cg_steps = 2, dense_cap = 1024,
-   precision = FP64, trsv_schedule = AUTO, autotune = 0, dense_row_min = 0. */
+   precision = FP64, trsv_schedule = AUTO, autotune = 0, dense_row_min = 0,
+   level_merge = 0. */
 void rlsq_factor_opts_default(rlsq_factor_opts *opts);
 /* atol = 1e-8, maxit = 2000, host pointers, default stream, check_every = 8 */
 void rlsq_solve_opts_default(rlsq_solve_opts *opts);

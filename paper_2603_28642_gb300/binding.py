@@ -43,6 +43,7 @@ class FactorOpts(C.Structure):
         ("scale_columns", C.c_int32), ("correction", C.c_int32), ("cg_steps", C.c_int32),
         ("dense_cap", C.c_int64), ("precision", C.c_int32), ("trsv_schedule", C.c_int32),
         ("autotune", C.c_int32), ("dense_row_min", C.c_int64), ("host_threads", C.c_int32),
+        ("level_merge", C.c_int32),
     ]
 
 
@@ -63,11 +64,15 @@ class Info(C.Structure):
         ("n_dense_rows", C.c_int64),
         ("levels_L1", C.c_int32), ("levels_L1t", C.c_int32), ("levels_U", C.c_int32),
         ("levels_Ut", C.c_int32), ("correction", C.c_int32), ("precision", C.c_int32),
-        ("bytes_per_iter", C.c_double),
+        ("bytes_per_iter", C.c_double), ("solve_levels", C.c_int32 * 4), ("level_merge", C.c_int32 * 4),
     ]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") and not isinstance(v, (bytes, str)) else v
+        return out
 
 
 class ServerOpts(C.Structure):

@@ -222,7 +222,7 @@ kb_trsv_level(const BSlot<T>* slots, const int32_t* phase, int want, int cond, i
     T* x = D->vn[io];
     for (int t = lo + blockIdx.x * kBlock + threadIdx.x; t < hi; t += gridDim.x * kBlock) {
         const int row = tri.order[t];
-        const T rv = rhs_at<T, K>(rhs, row);
+        const T rv = rhs_full<T, K>(tri, rhs, t, row);
         const T dg = tri.diag ? tri.diag[t] : (T)1;
         T sum = (T)0;
         const int e1 = tri.ptr[t + 1];

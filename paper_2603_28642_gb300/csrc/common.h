@@ -96,7 +96,8 @@ struct Mapping {
 
 template <typename T>
 struct DevFactor {
-    DevCsr<T> tri[4];          // strictly triangular parts: L1, L1^T, U, U^T
+    DevCsr<T> tri[4];          // strictly triangular parts: L1, L1^T, U, U^T (after level fusing)
+    DevCsr<T> rtri[4];         // right-hand-side terms of fused rows (empty when not fused)
     DevArray<T> diag[4];       // U diagonal for U and U^T (unit for L1, L1^T)
     DevArray<int32_t> order[4];
     std::vector<int32_t> level_ptr[4];
@@ -105,10 +106,11 @@ struct DevFactor {
     DevArray<T> d;
     DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
     DevArray<T> vn[5], vm[4];  // work vectors
-    void upload(const IlupResult& F, const std::vector<double>& sinv_h, cudaStream_t s);
+    void upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h, cudaStream_t s);
     void clear() {
         for (int w = 0; w < 4; ++w) {
             tri[w].ptr.release(); tri[w].idx.release(); tri[w].val.release();
+            rtri[w].ptr.release(); rtri[w].idx.release(); rtri[w].val.release(); rtri[w].nnz = 0;
             diag[w].release(); order[w].release(); level_ptr[w].clear(); level_ptr_d[w].release();
         }
         for (auto* c : {&L2, &L2t}) { c->ptr.release(); c->idx.release(); c->val.release(); }
@@ -118,8 +120,11 @@ struct DevFactor {
     }
     // tri[w], diag[w] are stored by solve position (rows in level order)
     Tri<T> tview(int which) const {
+        const bool fused = rtri[which].nnz > 0;
         return Tri<T>{tri[which].rows, tri[which].ptr.p, tri[which].idx.p, tri[which].val.p,
-                      (which >= 2) ? diag[which].p : nullptr, order[which].p};
+                      (which >= 2) ? diag[which].p : nullptr, order[which].p,
+                      fused ? rtri[which].ptr.p : nullptr, fused ? rtri[which].idx.p : nullptr,
+                      fused ? rtri[which].val.p : nullptr};
     }
 };
 
@@ -165,6 +170,7 @@ struct rlsq_problem_s {
     int precision = RLSQ_PREC_FP64;
     double factor_seconds = 0.0;
     std::unique_ptr<rlsq::IlupResult> F;
+    std::vector<rlsq::MergedTri> merged;  // the four systems as the GPU solves them
     rlsq::DevFactor<double> f64;
     rlsq::DevFactor<float> f32;
     rlsq::Mapping map;

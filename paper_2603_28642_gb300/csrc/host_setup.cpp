@@ -376,6 +376,88 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     return R;
 }
 
+MergedTri merge_levels(const HostCSR& strict, const double* diag, const Levels& lev, int k, int64_t max_nnz) {
+    MergedTri M;
+    M.k = std::max(1, k);
+    const int64_t n = strict.rows;
+    if (M.k == 1) {
+        M.T = strict;
+        M.R.rows = n;
+        M.R.cols = n;
+        M.R.ptr.assign(static_cast<size_t>(n) + 1, 0);
+        M.lev = lev;
+        return M;
+    }
+    auto group = [&](int64_t i) { return lev.level[i] / M.k; };
+    // merged rows, built in level order (a row's same-group dependencies come first)
+    std::vector<std::vector<std::pair<int32_t, double>>> Trow(static_cast<size_t>(n)), Rrow(static_cast<size_t>(n));
+    std::vector<double> accT(static_cast<size_t>(n), 0.0), accR(static_cast<size_t>(n), 0.0);
+    std::vector<int32_t> markT(static_cast<size_t>(n), -1), markR(static_cast<size_t>(n), -1);
+    std::vector<int32_t> listT, listR;
+    int64_t total = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        const int32_t i = lev.order[t];
+        listT.clear();
+        listR.clear();
+        auto addT = [&](int32_t c, double v) {
+            if (markT[c] != i) { markT[c] = i; accT[c] = 0.0; listT.push_back(c); }
+            accT[c] += v;
+        };
+        auto addR = [&](int32_t c, double v) {
+            if (markR[c] != i) { markR[c] = i; accR[c] = 0.0; listR.push_back(c); }
+            accR[c] += v;
+        };
+        for (int64_t e = strict.ptr[i]; e < strict.ptr[i + 1]; ++e) {
+            const int32_t j = strict.idx[e];
+            const double a = strict.val[e];
+            if (group(j) != group(i)) {
+                addT(j, a);
+                continue;
+            }
+            // x_j = (rhs_j + sum_Rj c rhs - sum_Tj c x) / d_j, substituted into - a x_j
+            const double f = diag ? a / diag[j] : a;
+            addR(j, -f);
+            for (const auto& rc : Rrow[j]) addR(rc.first, -f * rc.second);
+            for (const auto& tc : Trow[j]) addT(tc.first, -f * tc.second);
+        }
+        std::sort(listT.begin(), listT.end());
+        std::sort(listR.begin(), listR.end());
+        for (int32_t c : listT) Trow[i].push_back({c, accT[c]});
+        for (int32_t c : listR) Rrow[i].push_back({c, accR[c]});
+        total += static_cast<int64_t>(listT.size() + listR.size());
+        if (max_nnz > 0 && total > max_nnz) {
+            M.k = 0;  // too much fill: rejected
+            return M;
+        }
+    }
+    auto to_csr = [&](const std::vector<std::vector<std::pair<int32_t, double>>>& rows, HostCSR& out) {
+        out.rows = n;
+        out.cols = n;
+        out.ptr.assign(static_cast<size_t>(n) + 1, 0);
+        for (int64_t i = 0; i < n; ++i) out.ptr[i + 1] = out.ptr[i] + static_cast<int64_t>(rows[i].size());
+        out.idx.resize(static_cast<size_t>(out.ptr[n]));
+        out.val.resize(static_cast<size_t>(out.ptr[n]));
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t w = out.ptr[i];
+            for (const auto& p : rows[i]) {
+                out.idx[w] = p.first;
+                out.val[w] = p.second;
+                ++w;
+            }
+        }
+    };
+    to_csr(Trow, M.T);
+    to_csr(Rrow, M.R);
+    // lower systems depend on smaller ids, upper ones on larger ids; the
+    // merged dependencies keep that direction
+    bool lower = true;
+    for (int64_t i = 0; i < n && lower; ++i)
+        for (int64_t e = strict.ptr[i]; e < strict.ptr[i + 1]; ++e)
+            if (strict.idx[e] > i) { lower = false; break; }
+    M.lev = analyse_levels(M.T, lower);
+    return M;
+}
+
 bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads) {
     const int64_t n = f.n, m2 = f.m - f.n;
     if (m2 <= 0) {

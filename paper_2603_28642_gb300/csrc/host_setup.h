@@ -67,6 +67,21 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm);
 // lower = true: row i depends on k < i; otherwise on k > i.
 Levels analyse_levels(const HostCSR& strict, bool lower);
 
+// A triangular system with groups of `k` consecutive levels fused: inside a
+// group, a row's dependencies on rows of the same group are substituted, so
+// every remaining dependency lies in an earlier group.  Row i then reads
+//   x_i = (rhs_i + sum_R c rhs_j - sum_T c x_j) / diag_i
+// with R the right-hand-side terms brought in by the substitution.  The
+// result is the same solution (up to rounding) with about levels / k levels.
+struct MergedTri {
+    HostCSR T;       // remaining dependencies (unknown ids), strictly earlier groups
+    HostCSR R;       // extra right-hand-side terms (unknown ids, coefficients)
+    Levels lev;      // levels of T
+    int k = 1;
+};
+// max_nnz > 0: give up (k = 0 in the result) once T and R hold more entries.
+MergedTri merge_levels(const HostCSR& strict, const double* diag, const Levels& lev, int k, int64_t max_nnz = 0);
+
 // Dense inverse of S = I + Z^T Z, Z = L1^{-T} L2^T, through its Cholesky
 // factor; row-major (m-n)^2.  Returns false if S is not numerically SPD.
 bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads);

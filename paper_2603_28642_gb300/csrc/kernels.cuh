@@ -179,10 +179,17 @@ __device__ __forceinline__ void row_dot2(const Csr<TV>& a, int row, int lane, co
         s2 += v * (TA)x2[j];
     }
 }
+// one row's dot product, four entries in flight per lane
 template <int G, typename TV, typename TX, typename TA>
 __device__ __forceinline__ void row_dot(const Csr<TV>& a, int row, int lane, const TX* x, TA& s) {
     const int e1 = a.ptr[row + 1];
-    for (int e = a.ptr[row] + lane; e < e1; e += G) s += (TA)a.val[e] * (TA)x[a.idx[e]];
+    int e = a.ptr[row] + lane;
+    for (; e + 3 * G < e1; e += 4 * G) {
+        const int j0 = a.idx[e], j1 = a.idx[e + G], j2 = a.idx[e + 2 * G], j3 = a.idx[e + 3 * G];
+        s += (TA)a.val[e] * (TA)x[j0] + (TA)a.val[e + G] * (TA)x[j1] + (TA)a.val[e + 2 * G] * (TA)x[j2] +
+             (TA)a.val[e + 3 * G] * (TA)x[j3];
+    }
+    for (; e < e1; e += G) s += (TA)a.val[e] * (TA)x[a.idx[e]];
 }
 
 // ---------------------------------------------------------------------------
@@ -442,7 +449,23 @@ struct Tri {
     const T* val;
     const T* diag;         // by position; nullptr: unit diagonal
     const int32_t* order;  // order[t]: unknown solved at position t
+    // right-hand-side terms of rows whose same-group dependencies were
+    // substituted (fused levels): x_i uses rhs_i + sum rval * rhs(ridx);
+    // rptr == nullptr when no levels are fused
+    const int32_t* rptr;
+    const int32_t* ridx;
+    const T* rval;
 };
+
+template <typename T, int K>
+__device__ __forceinline__ T rhs_full(const Tri<T>& tri, const Rhs<T>& rhs, int t, int row) {
+    T rv = rhs_at<T, K>(rhs, row);
+    if (tri.rptr) {
+        const int q1 = tri.rptr[t + 1];
+        for (int q = tri.rptr[t]; q < q1; ++q) rv += tri.rval[q] * rhs_at<T, K>(rhs, tri.ridx[q]);
+    }
+    return rv;
+}
 
 // Waits until flag == epoch.  Gives up after kWaitNs or when another thread
 // has already given up; returns false then.
@@ -509,7 +532,7 @@ k_trsv_syncfree(Tri<T> tri, Rhs<T> rhs, T* x, int* flags, int slot, unsigned* ti
             sum = group_sum<G>(sum, mask);
             ok = __all_sync(mask, ok);
             if (lane == 0) {
-                T v = rhs_at<T, K>(rhs, row) - sum;
+                T v = rhs_full<T, K>(tri, rhs, (int)tpos, row) - sum;
                 if (tri.diag) v = v / tri.diag[tpos];
                 if (!ok) v = (T)NAN;
                 x[row] = v;
@@ -597,7 +620,7 @@ k_trsv_sentinel(Tri<T> tri, Rhs<T> rhs, T* x, int slot, unsigned* tickets, const
             int e = tri.ptr[tpos] + lane;
             // everything that does not depend on other rows, loaded up front
             const int row = tri.order[tpos];
-            const T rv = rhs_at<T, K>(rhs, row);
+            const T rv = rhs_full<T, K>(tri, rhs, (int)tpos, row);
             const T dg = tri.diag ? tri.diag[tpos] : (T)1;
             T sum = (T)0;
             bool ok = true;
@@ -672,7 +695,7 @@ __device__ __forceinline__ void read_ahead(const Tri<T>& tri, const Rhs<T>& rhs,
     r.row = tri.order[t];
     r.e0 = tri.ptr[t];
     r.e1 = tri.ptr[t + 1];
-    r.rv = rhs_at<T, K>(rhs, r.row);
+    r.rv = rhs_full<T, K>(tri, rhs, t, r.row);
     r.dg = tri.diag ? tri.diag[t] : (T)1;
 #pragma unroll
     for (int q = 0; q < KP; ++q) {
@@ -712,7 +735,7 @@ k_trsv_coop(Tri<T> tri, Rhs<T> rhs, T* x, const int32_t* __restrict__ level_ptr,
                 const int row = tri.order[t];
                 T s2 = (T)0;
                 for (int e = tri.ptr[t]; e < tri.ptr[t + 1]; ++e) s2 += tri.val[e] * __ldcg(&x[tri.idx[e]]);
-                T w = rhs_at<T, K>(rhs, row) - s2;
+                T w = rhs_full<T, K>(tri, rhs, t, row) - s2;
                 if (tri.diag) w = w / tri.diag[t];
                 x[row] = w;
             }
@@ -736,7 +759,7 @@ k_trsv_level(Tri<T> tri, Rhs<T> rhs, T* x, int lo, int hi, const LsmrState* S) {
     const int groups = (gridDim.x * kBlock) / G;
     for (int tpos = lo + (blockIdx.x * kBlock + threadIdx.x) / G; tpos < hi; tpos += groups) {
         const int row = tri.order[tpos];
-        const T rv = rhs_at<T, K>(rhs, row);
+        const T rv = rhs_full<T, K>(tri, rhs, tpos, row);
         const T dg = tri.diag ? tri.diag[tpos] : (T)1;
         T sum = (T)0;
         const int e1 = tri.ptr[tpos + 1];
@@ -809,7 +832,14 @@ k_l2t_cg(Csr<T> L2t, const T* __restrict__ r, const T* __restrict__ p, T* __rest
     for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2t.rows; row += groups) {
         T s = (T)0;
         const int e1 = L2t.ptr[row + 1];
-        for (int e = L2t.ptr[row] + lane; e < e1; e += G) {
+        int e = L2t.ptr[row] + lane;
+        for (; e + G < e1; e += 2 * G) {
+            const int j0 = L2t.idx[e], j1 = L2t.idx[e + G];
+            const T p0 = FIRST ? r[j0] : r[j0] + beta * p[j0];
+            const T p1 = FIRST ? r[j1] : r[j1] + beta * p[j1];
+            s += L2t.val[e] * p0 + L2t.val[e + G] * p1;
+        }
+        for (; e < e1; e += G) {
             const int j = L2t.idx[e];
             const T pj = FIRST ? r[j] : r[j] + beta * p[j];
             s += L2t.val[e] * pj;

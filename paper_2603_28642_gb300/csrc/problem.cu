@@ -56,30 +56,34 @@ static void upload_vec(DevArray<T>& dst, const std::vector<double>& src, cudaStr
 }
 
 template <typename T>
-void DevFactor<T>::upload(const IlupResult& F, const std::vector<double>& sinv_h, cudaStream_t s) {
-    const HostCSR* parts[4] = {&F.L1, &F.L1t, &F.U, &F.Ut};
-    const Levels* levs[4] = {&F.lev_L1, &F.lev_L1t, &F.lev_U, &F.lev_Ut};
+void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h,
+                          cudaStream_t s) {
     for (int w = 0; w < 4; ++w) {
         // rows permuted into solve order so each level is contiguous
-        const HostCSR& a = *parts[w];
-        const std::vector<int32_t>& ord = levs[w]->order;
-        HostCSR lo;
-        lo.rows = a.rows;
-        lo.cols = a.cols;
-        lo.ptr.assign(static_cast<size_t>(a.rows) + 1, 0);
-        lo.idx.reserve(a.idx.size());
-        lo.val.reserve(a.val.size());
-        for (int64_t t = 0; t < a.rows; ++t) {
-            const int32_t r = ord[t];
-            for (int64_t e = a.ptr[r]; e < a.ptr[r + 1]; ++e) {
-                lo.idx.push_back(a.idx[e]);
-                lo.val.push_back(a.val[e]);
+        const MergedTri& M = merged[w];
+        const std::vector<int32_t>& ord = M.lev.order;
+        auto permute = [&](const HostCSR& a) {
+            HostCSR lo;
+            lo.rows = a.rows;
+            lo.cols = a.cols;
+            lo.ptr.assign(static_cast<size_t>(a.rows) + 1, 0);
+            lo.idx.reserve(a.idx.size());
+            lo.val.reserve(a.val.size());
+            for (int64_t t = 0; t < a.rows; ++t) {
+                const int32_t r = ord[t];
+                for (int64_t e = a.ptr[r]; e < a.ptr[r + 1]; ++e) {
+                    lo.idx.push_back(a.idx[e]);
+                    lo.val.push_back(a.val[e]);
+                }
+                lo.ptr[t + 1] = static_cast<int64_t>(lo.idx.size());
             }
-            lo.ptr[t + 1] = static_cast<int64_t>(lo.idx.size());
-        }
-        tri[w].upload(lo, s);
+            return lo;
+        };
+        tri[w].upload(permute(M.T), s);
+        if (M.R.nnz() > 0) rtri[w].upload(permute(M.R), s);
+        else { rtri[w].ptr.release(); rtri[w].idx.release(); rtri[w].val.release(); rtri[w].nnz = 0; }
         order[w].upload(ord.data(), ord.size(), s);
-        level_ptr[w] = levs[w]->level_ptr;
+        level_ptr[w] = M.lev.level_ptr;
         level_ptr_d[w].upload(level_ptr[w].data(), level_ptr[w].size(), s);
         if (w >= 2) {
             std::vector<double> dl(ord.size());
@@ -167,7 +171,7 @@ struct RecScope {
 template <typename T>
 static double trsv_bytes(const rlsq_problem_s* P, const DevFactor<T>& F, int which) {
     const double n = static_cast<double>(P->n), v = sizeof(T);
-    return (v + 4.0) * static_cast<double>(F.tri[which].nnz) + 8.0 * n + 3.0 * v * n +
+    return (v + 4.0) * static_cast<double>(F.tri[which].nnz + F.rtri[which].nnz) + 8.0 * n + 3.0 * v * n +
            ((which >= 2) ? v * n : 0.0);
 }
 template <typename T>
@@ -506,6 +510,10 @@ static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
         info->levels_U = F.lev_U.nlevels;
         info->levels_Ut = F.lev_Ut.nlevels;
     }
+    for (size_t w = 0; w < P->merged.size() && w < 4; ++w) {
+        info->solve_levels[w] = P->merged[w].lev.nlevels;
+        info->level_merge[w] = P->merged[w].k;
+    }
     info->bytes_per_iter = algorithmic_bytes(P, !P->factored);
 }
 
@@ -746,7 +754,9 @@ void default_mapping(rlsq_problem_s* P) {
         const HostCSR* parts[4] = {&F.L1, &F.L1t, &F.U, &F.Ut};
         for (int w = 0; w < 4; ++w) {
             // one thread per row unless rows are long
-            const double avg = parts[w]->nnz() / std::max(1.0, n);
+            const double nz = P->merged.size() == 4 ? static_cast<double>(P->merged[w].T.nnz())
+                                                    : static_cast<double>(parts[w]->nnz());
+            const double avg = nz / std::max(1.0, n);
             P->map.G_tri[w] = avg <= 12.0 ? 1 : pow2_lanes(avg / 4.0, 1, 32);
             P->map.sched[w] = RLSQ_TRSV_SYNCFREE;
         }
@@ -829,6 +839,7 @@ void rlsq_factor_opts_default(rlsq_factor_opts* o) {
     o->autotune = 0;
     o->dense_row_min = 0;
     o->host_threads = 0;
+    o->level_merge = 0;
 }
 
 void rlsq_solve_opts_default(rlsq_solve_opts* o) {
@@ -974,10 +985,41 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
                 throw ApiError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
         }
         cudaStream_t st = h->stream;
+        // fused levels per system (0: the k of least modelled time, about
+        // 5 us per level plus the bytes at 4 TB/s)
+        h->merged.clear();
+        {
+            const HostCSR* parts[4] = {&F->L1, &F->L1t, &F->U, &F->Ut};
+            const Levels* levs[4] = {&F->lev_L1, &F->lev_L1t, &F->lev_U, &F->lev_Ut};
+            const double wv = opts.precision == RLSQ_PREC_FP32 ? 4.0 : 8.0;
+            for (int w = 0; w < 4; ++w) {
+                const double* dg = w >= 2 ? F->Udiag.data() : nullptr;
+                if (opts.level_merge >= 1) {
+                    h->merged.push_back(merge_levels(*parts[w], dg, *levs[w], opts.level_merge));
+                    continue;
+                }
+                MergedTri best = merge_levels(*parts[w], dg, *levs[w], 1);
+                auto cost = [&](const MergedTri& M) {
+                    return M.lev.nlevels * 5.0e-6 +
+                           ((wv + 4.0) * static_cast<double>(M.T.nnz() + M.R.nnz()) + 8.0 * h->n) / 4.0e12;
+                };
+                double cbest = cost(best);
+                for (int kk = 2; kk <= 4; ++kk) {
+                    MergedTri M = merge_levels(*parts[w], dg, *levs[w], kk, 4 * std::max<int64_t>(parts[w]->nnz(), h->n));
+                    if (M.k == 0) break;
+                    const double c = cost(M);
+                    if (c < cbest) {
+                        cbest = c;
+                        best = std::move(M);
+                    }
+                }
+                h->merged.push_back(std::move(best));
+            }
+        }
         h->f64.clear();
         h->f32.clear();
-        if (opts.precision == RLSQ_PREC_FP32) h->f32.upload(*F, sinv, st);
-        else h->f64.upload(*F, sinv, st);
+        if (opts.precision == RLSQ_PREC_FP32) h->f32.upload(*F, h->merged.data(), sinv, st);
+        else h->f64.upload(*F, h->merged.data(), sinv, st);
         if (opts.dense_row_min != 0) {
             // an explicit dense-row threshold (< 0: none) replaces the automatic one
             layout_A(h, opts.dense_row_min);

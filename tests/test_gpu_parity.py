@@ -329,3 +329,39 @@ def test_dense_block_off_gives_same_solution(sparse_dense):
     res = off.solve(prob.b)
     assert res.info["iterations"] == on.info["iterations"]
     assert rel(res.x, on.x) <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# fused levels: same solutions, fewer levels
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP])
+def test_fused_levels_solves(mid, k, sched):
+    P = make(mid, B.CORR_CG, sched=sched, level_merge=k)
+    info = P.info()
+    assert info["level_merge"] == [k] * 4
+    if k > 1:
+        assert all(s < l for s, l in zip(info["solve_levels"],
+                                         [info["levels_L1"], info["levels_L1t"], info["levels_U"],
+                                          info["levels_Ut"]]))
+    f = oracle_factor(mid, oracle.CG)
+    b = np.random.default_rng(9).standard_normal(mid.n)
+    for sys_id, name in SOLVES:
+        assert rel(P.trsv(sys_id, b), getattr(f, name)(b)) <= 1e-12
+    assert rel(P.apply(b), f.apply(b)) <= 1e-12
+
+
+def test_fused_levels_batch_and_noalloc(cfg0):
+    import torch
+
+    P = make(cfg0, B.CORR_CG, level_merge=2)
+    f = oracle_factor(cfg0, oracle.CG)
+    xs, infos, code = B.batch_solve([P], [cfg0.b])
+    ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
+    assert code == 0 and rel(xs[0], ref.x) <= 1e-6
+    b = np.random.default_rng(10).standard_normal(cfg0.n)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.empty_like(bd)
+    B.trsv_noalloc(P, B.SYS_U, bd, xd)
+    torch.cuda.synchronize()
+    assert rel(xd.cpu().numpy(), f.solve_U(b)) <= 1e-12
