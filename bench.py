@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     ap.add_argument("--cpu-scale", type=float, default=0.1, help="oracle sample size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sampled sparse-dense, batched and served measurements")
+    ap.add_argument("--workload", default="cfg1", choices=["cfg1", "sparse-dense", "batched", "served"],
+                    help="cfg1: the headline line; the others print one line of their own at full size")
+    ap.add_argument("--count", type=int, default=0, help="batched/served: problems or matrices (0 = recipe)")
+    ap.add_argument("--requests", type=int, default=0, help="served: requests per arrival rate")
     return ap.parse_args()
 
 
@@ -282,6 +288,12 @@ def run_ours(args):
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }
+    del P
+    if rank == 0 and not args.no_extras:
+        # the other forms, sampled so the default run stays within minutes
+        out["sparse_dense"] = measure_sparse_dense(args.scale)
+        out["batched_sample"] = measure_batched(512, first=64, sample=8)
+        out["served_sample"] = measure_served(16, n_hi=20000, rates=(100, 1000, 5000), requests=200)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_sample(args.cpu_scale, prob.nnz)
     if rank == 0:
@@ -290,10 +302,150 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# the other forms: sparse-dense, batched, served
+# ---------------------------------------------------------------------------
+def factor_all(problems, threads=None, **kw):
+    """Creates and factors problems concurrently (the host set-up releases the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2603_28642_gb300 import binding as B
+
+    def one(p):
+        P = B.Problem.from_problem(p)
+        P.factor(**kw)
+        return P
+
+    with ThreadPoolExecutor(threads or os.cpu_count() or 4) as ex:
+        return list(ex.map(one, problems))
+
+
+def measure_sparse_dense(scale=1.0):
+    """Sparse-dense problem (n = 500,000, 1,000,000 sparse rows, 200 dense rows):
+    float32 apply, float64 recurrences, CG(2)."""
+    from paper_2603_28642_gb300 import binding as B
+    from paper_2603_28642_gb300 import synth
+
+    prob = synth.config_problem(2, scale=scale)
+    P = B.Problem.from_problem(prob)
+    info = P.factor(**FACTOR, precision=B.PREC_FP32, autotune=1)
+    prow, a2, _, _ = P.split()
+    in_a2 = bool(set(prob.dense_rows.tolist()) <= set(a2.tolist()))
+    prof = P.profile(prob.b, warmup=3, iters=20)
+    tol = P.solve(prob.b)
+    cls = prof["classes"]
+    dense = cls.get("dense", {"ms": 0.0, "bytes": 0.0})
+    return {
+        "m": prob.m, "n": prob.n, "dense_rows": info["n_dense_rows"], "dense_rows_in_A2": in_a2,
+        "iter_per_s": 1000.0 / prof["ms_per_iter"], "ms_per_iter": prof["ms_per_iter"],
+        "time_to_tol_s": tol.info["solve_seconds"], "iterations": tol.info["iterations"],
+        "ratio": tol.info["ratio"], "status": tol.status,
+        "dense_gemv_GBps": dense["bytes"] / (dense["ms"] / 1000.0) / 1e9 if dense["ms"] else None,
+        "iteration_GBps": prof["bytes_per_iter"] / (prof["ms_per_iter"] / 1000.0) / 1e9,
+    }
+
+
+def measure_batched(count=512, first=None, sample=16):
+    """Batched form: the first `first` problems of the 512-problem recipe solved
+    together (float32 apply, float64 recurrences), against the same problems
+    solved one at a time in float64 (timed on `sample` of them)."""
+    from paper_2603_28642_gb300 import binding as B
+    from paper_2603_28642_gb300 import synth
+
+    probs = synth.batch_problems(count, first=first)
+    hs = factor_all(probs, mu=1.0, p=10, tau=1e-2, correction=B.CORR_AUTO, cg_steps=2,
+                    precision=B.PREC_FP32)
+    B.batch_solve(hs[:2], [p.b for p in probs[:2]])  # warm-up (graph capture, lazy loading)
+    t0 = time.perf_counter()
+    xs, infos, code = B.batch_solve(hs, [p.b for p in probs])
+    wall = time.perf_counter() - t0
+    its = sum(i["iterations"] for i in infos)
+    # one at a time, float64 apply, the same problems (a sample)
+    step = max(1, len(probs) // sample)
+    idx = list(range(0, len(probs), step))[:sample]
+    t_one, its_one = 0.0, 0
+    for k in idx:
+        hs[k].factor(mu=1.0, p=10, tau=1e-2, correction=B.CORR_AUTO, cg_steps=2, precision=B.PREC_FP64)
+        hs[k].solve(probs[k].b)  # warm-up of this handle's graph
+        t1 = time.perf_counter()
+        r = hs[k].solve(probs[k].b)
+        t_one += time.perf_counter() - t1
+        its_one += r.info["iterations"]
+    one_total = t_one / len(idx) * len(probs)
+    return {
+        "problems": len(probs), "sum_n": int(sum(p.n for p in probs)), "sum_nnz": int(sum(p.nnz for p in probs)),
+        "status": code, "iterations_total": its, "batched_wall_s": wall,
+        "aggregate_iter_per_s": its / wall,
+        "one_at_a_time_fp64_s_estimated": one_total, "one_at_a_time_sample": len(idx),
+        "one_at_a_time_iter_per_s": its_one / t_one if t_one else None,
+        "speedup_time_to_tol": one_total / wall if wall else None,
+        "max_ratio": max(i["ratio"] for i in infos),
+    }
+
+
+def measure_served(nmat=64, n_hi=200000, rates=(100, 1000, 5000), requests=500):
+    """Served form: Poisson arrivals of new right-hand sides for resident
+    matrices (m = 1.5 n), float32 apply, float64 recurrences, 150 GB budget."""
+    import numpy as np
+
+    from paper_2603_28642_gb300 import binding as B
+    from paper_2603_28642_gb300 import synth
+
+    mats = synth.serving_matrices(nmat, n_hi=n_hi)
+    hs = factor_all(mats, mu=1.0, p=10, tau=1e-2, correction=B.CORR_AUTO, cg_steps=2,
+                    precision=B.PREC_FP32)
+    out = {"matrices": nmat, "n_max": int(max(p.n for p in mats)), "sum_n": int(sum(p.n for p in mats)),
+           "budget_bytes": 150 * 2**30, "rates": []}
+    for rate in rates:
+        srv = B.Server(hbm_budget_bytes=150 * 2**30, max_slots=64)
+        ids = [srv.register(P) for P in hs]
+        rng = np.random.default_rng(rate)
+        which = rng.integers(0, nmat, size=requests)
+        rhs = [synth.serving_rhs(mats[w], r) for r, w in enumerate(which)]
+        arrive = synth.poisson_arrivals(rate, requests, seed=rate)
+        pending = {}
+        t0 = time.perf_counter()
+        sent = 0
+        while sent < requests or pending:
+            now = time.perf_counter() - t0
+            while sent < requests and arrive[sent] <= now:
+                pending[srv.submit(ids[int(which[sent])], rhs[sent])] = int(which[sent])
+                sent += 1
+            for t, w in list(pending.items()):
+                if srv.poll(t, mats[w].n) is not None:
+                    del pending[t]
+            time.sleep(0.0005)
+        st = srv.stats()
+        out["rates"].append({"rate_per_s": rate, "requests": requests, "p50_ms": st["p50_ms"],
+                             "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                             "solves_per_s": st["solves_per_s"], "ticks": st["ticks"],
+                             "peak_state_bytes": st["peak_bytes"]})
+        srv.close()
+    return out
+
+
+def run_workload(args):
+    """One JSON line for a non-default workload at its full recipe size."""
+    if args.workload == "sparse-dense":
+        r = measure_sparse_dense(args.scale)
+        metric, value, unit = "preconditioned LSMR iterations/s (sparse-dense)", r["iter_per_s"], "iter/s"
+    elif args.workload == "batched":
+        r = measure_batched(args.count or 512)
+        metric, value, unit = "batched aggregate LSMR iterations/s", r["aggregate_iter_per_s"], "iter/s"
+    else:
+        r = measure_served(args.count or 64, requests=args.requests or 2000, rates=(100, 300, 1000, 3000, 5000))
+        metric, value, unit = "served solves/s at the highest rate", r["rates"][-1]["solves_per_s"], "solves/s"
+    print(json.dumps({"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "higher_is_better": True,
+                      "dtype": "f32 apply / f64 recurrences", "data": "synthetic",
+                      "config": {"workload": args.workload}, "result": r}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "cfg1":
+        run_workload(args)
     else:
         run_ours(args)
 

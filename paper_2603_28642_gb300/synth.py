@@ -247,12 +247,14 @@ def batch_problem_sizes(count: int = 512, master_seed: int = 3, n_lo: int = 2000
 
 
 def batch_problems(count: int = 512, master_seed: int = 3, n_lo: int = 2000,
-                   n_hi: int = 50000, seed_base: int = 3000):
+                   n_hi: int = 50000, seed_base: int = 3000, first: int | None = None):
     """Independent problems of uneven size; problem k uses seed seed_base + k
-    with the first-n-rows diagonal rule."""
+    with the first-n-rows diagonal rule.  ``first`` keeps only the first
+    problems of the ``count``-problem recipe (same sizes and seeds)."""
     n, m, d = batch_problem_sizes(count, master_seed, n_lo, n_hi)
+    take = count if first is None else min(first, count)
     return [sparse_problem(int(m[k]), int(n[k]), int(d[k]), seed=seed_base + k)
-            for k in range(count)]
+            for k in range(take)]
 
 
 def serving_matrices(count: int = 64, master_seed: int = 4, n_lo: int = 1000,
