@@ -291,9 +291,14 @@ def run_ours(args):
     del P
     if rank == 0 and not args.no_extras:
         # the other forms, sampled so the default run stays within minutes
-        out["sparse_dense"] = measure_sparse_dense(args.scale)
-        out["batched_sample"] = measure_batched(512, first=64, sample=8)
-        out["served_sample"] = measure_served(16, n_hi=20000, rates=(100, 1000, 5000), requests=200)
+        for key, fn in (("sparse_dense", lambda: measure_sparse_dense(args.scale)),
+                        ("batched_sample", lambda: measure_batched(512, first=64, sample=8)),
+                        ("served_sample", lambda: measure_served(16, n_hi=20000, rates=(100, 1000, 5000),
+                                                                 requests=200))):
+            try:
+                out[key] = fn()
+            except Exception as e:  # recorded, so the headline line still prints
+                out[key] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_oracle_sample(args.cpu_scale, prob.nnz)
     if rank == 0:

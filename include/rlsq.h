@@ -76,6 +76,8 @@ extern "C" {
 #define RLSQ_TRSV_LEVEL 1    /* one launch per level set */
 #define RLSQ_TRSV_SYNCFREE 2 /* one launch, rows wait on the values they need (bounded waits) */
 #define RLSQ_TRSV_COOP 3     /* one persistent launch, grid barrier between levels (bounded waits) */
+#define RLSQ_TRSV_WAVE 4     /* one co-resident launch, a fixed row sequence per thread, rows wait on
+                                their inputs and levels overlap (bounded waits) */
 
 /* triangular systems for rlsq_trsv */
 #define RLSQ_SYS_L1 0   /* L1 x = b   (unit lower)      */
@@ -139,6 +141,7 @@ typedef struct {
     double bytes_per_iter; /* algorithmic HBM bytes of one LSMR iteration */
     int32_t solve_levels[4]; /* levels the GPU walks per system after fusing (RLSQ_SYS_* order) */
     int32_t level_merge[4];  /* fused levels per group, per system */
+    int32_t trsv_schedule[4]; /* RLSQ_TRSV_* each system runs with (after autotuning) */
 } rlsq_info;
 
 /* Server options and statistics (continuous batching of right-hand sides). */

@@ -26,7 +26,7 @@ ERR_BREAKDOWN, ERR_MAXIT, ERR_DEVICE_TIMEOUT = -7, -8, -9
 HOST_PTRS, DEVICE_PTRS = 0, 1
 CORR_NONE, CORR_SI, CORR_CG, CORR_DENSE, CORR_AUTO = 0, 1, 2, 3, 4
 PREC_FP64, PREC_FP32 = 0, 1
-TRSV_AUTO, TRSV_LEVEL, TRSV_SYNCFREE, TRSV_COOP = 0, 1, 2, 3
+TRSV_AUTO, TRSV_LEVEL, TRSV_SYNCFREE, TRSV_COOP, TRSV_WAVE = 0, 1, 2, 3, 4
 SYS_L1, SYS_L1T, SYS_U, SYS_UT = 0, 1, 2, 3
 PART_L1, PART_L2, PART_U = 0, 1, 2
 
@@ -65,6 +65,7 @@ class Info(C.Structure):
         ("levels_L1", C.c_int32), ("levels_L1t", C.c_int32), ("levels_U", C.c_int32),
         ("levels_Ut", C.c_int32), ("correction", C.c_int32), ("precision", C.c_int32),
         ("bytes_per_iter", C.c_double), ("solve_levels", C.c_int32 * 4), ("level_merge", C.c_int32 * 4),
+        ("trsv_schedule", C.c_int32 * 4),
     ]
 
     def as_dict(self):

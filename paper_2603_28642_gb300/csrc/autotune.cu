@@ -94,22 +94,27 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
     for (int w = 0; w < 4; ++w) {
         int bestG = P->map.G_tri[w], bestS = P->map.sched[w];
         float tbest = 1e30f;
-        int bestB = P->map.sf_blocks[w];
-        for (int sched : {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_LEVEL, RLSQ_TRSV_COOP}) {
+        int bestB = P->map.sf_blocks[w], bestK = P->map.wave_kp[w];
+        for (int sched : {RLSQ_TRSV_WAVE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_LEVEL, RLSQ_TRSV_COOP}) {
             for (int G : cands) {
-                if (sched == RLSQ_TRSV_COOP && G != 1) continue;  // one thread per row
+                // the persistent and wavefront solves run one thread per row
+                if ((sched == RLSQ_TRSV_COOP || sched == RLSQ_TRSV_WAVE) && G != 1) continue;
                 for (int nb : {1, 2, 3, 6}) {
-                    if (sched != RLSQ_TRSV_SYNCFREE && nb != 1) continue;
+                    // nb: resident blocks per SM (sync-free) or entries loaded ahead (wavefront: 4, 8)
+                    if (sched == RLSQ_TRSV_WAVE ? (nb != 1 && nb != 2) : (sched != RLSQ_TRSV_SYNCFREE && nb != 1))
+                        continue;
                     P->map.sched[w] = sched;
                     P->map.G_tri[w] = G;
-                    P->map.sf_blocks[w] = nb;
+                    if (sched == RLSQ_TRSV_WAVE) P->map.wave_kp[w] = 4 * nb;
+                    else P->map.sf_blocks[w] = nb;
                     float ms = 0.f;
                     if (rlsq_trsv_time(P, w, &ms) != RLSQ_OK) continue;
                     if (ms < tbest) {
                         tbest = ms;
                         bestG = G;
                         bestS = sched;
-                        bestB = nb;
+                        if (sched == RLSQ_TRSV_WAVE) bestK = 4 * nb;
+                        else bestB = nb;
                     }
                 }
             }
@@ -117,6 +122,7 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
         P->map.G_tri[w] = bestG;
         P->map.sched[w] = bestS;
         P->map.sf_blocks[w] = bestB;
+        P->map.wave_kp[w] = bestK;
     }
 }
 

@@ -92,6 +92,7 @@ struct Mapping {
     int sched[4] = {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE};
     int G_L2 = 4, G_L2t = 4;
     int sf_blocks[4] = {2, 2, 2, 2};    // sync-free solve: resident blocks per SM (bounds the polling rows)
+    int wave_kp[4] = {4, 4, 4, 4};      // wavefront solve: entries per row loaded ahead (4 or 8)
 };
 
 template <typename T>
@@ -102,6 +103,12 @@ struct DevFactor {
     DevArray<int32_t> order[4];
     std::vector<int32_t> level_ptr[4];
     DevArray<int32_t> level_ptr_d[4];  // device copies for the persistent solve
+    // first ell_kp[w] entries of every row, position-major ([q * n + t];
+    // idx -1 and value 0 past the row's end): the persistent solve loads a
+    // level's structure with independent, coalesced reads
+    DevArray<int32_t> ell_idx[4];
+    DevArray<T> ell_val[4];
+    int ell_kp[4] = {4, 4, 4, 4};
     DevCsr<T> L2, L2t;
     DevArray<T> d;
     DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
@@ -112,6 +119,7 @@ struct DevFactor {
             tri[w].ptr.release(); tri[w].idx.release(); tri[w].val.release();
             rtri[w].ptr.release(); rtri[w].idx.release(); rtri[w].val.release(); rtri[w].nnz = 0;
             diag[w].release(); order[w].release(); level_ptr[w].clear(); level_ptr_d[w].release();
+            ell_idx[w].release(); ell_val[w].release();
         }
         for (auto* c : {&L2, &L2t}) { c->ptr.release(); c->idx.release(); c->val.release(); }
         d.release(); sinv.release();
@@ -124,7 +132,7 @@ struct DevFactor {
         return Tri<T>{tri[which].rows, tri[which].ptr.p, tri[which].idx.p, tri[which].val.p,
                       (which >= 2) ? diag[which].p : nullptr, order[which].p,
                       fused ? rtri[which].ptr.p : nullptr, fused ? rtri[which].idx.p : nullptr,
-                      fused ? rtri[which].val.p : nullptr};
+                      fused ? rtri[which].val.p : nullptr, ell_idx[which].p, ell_val[which].p};
     }
 };
 

@@ -455,6 +455,9 @@ struct Tri {
     const int32_t* rptr;
     const int32_t* ridx;
     const T* rval;
+    // the first entries of every row again, position-major (see DevFactor)
+    const int32_t* eidx;
+    const T* eval;
 };
 
 template <typename T, int K>
@@ -462,7 +465,18 @@ __device__ __forceinline__ T rhs_full(const Tri<T>& tri, const Rhs<T>& rhs, int 
     T rv = rhs_at<T, K>(rhs, row);
     if (tri.rptr) {
         const int q1 = tri.rptr[t + 1];
-        for (int q = tri.rptr[t]; q < q1; ++q) rv += tri.rval[q] * rhs_at<T, K>(rhs, tri.ridx[q]);
+        int q = tri.rptr[t];
+        for (; q + 3 < q1; q += 4) {
+            const int i0 = tri.ridx[q], i1 = tri.ridx[q + 1], i2 = tri.ridx[q + 2], i3 = tri.ridx[q + 3];
+            const T c0 = tri.rval[q], c1 = tri.rval[q + 1], c2 = tri.rval[q + 2], c3 = tri.rval[q + 3];
+            const T r0 = rhs_at<T, K>(rhs, i0), r1 = rhs_at<T, K>(rhs, i1), r2 = rhs_at<T, K>(rhs, i2),
+                    r3 = rhs_at<T, K>(rhs, i3);
+            rv += c0 * r0;
+            rv += c1 * r1;
+            rv += c2 * r2;
+            rv += c3 * r3;
+        }
+        for (; q < q1; ++q) rv += tri.rval[q] * rhs_at<T, K>(rhs, tri.ridx[q]);
     }
     return rv;
 }
@@ -655,18 +669,33 @@ k_trsv_sentinel(Tri<T> tri, Rhs<T> rhs, T* x, int slot, unsigned* tickets, const
 }
 
 // Persistent level-synchronous solve: one co-resident block of kCoopBlock
-// threads per SM walks the levels in order; inside a level the rows are dealt
-// out block-cyclically, and a grid-wide barrier separates levels.  The barrier
-// counter only grows (arrivals = level * blocks), so it needs no reset within
-// a launch; waits are bounded like every other wait here.  x is read through
-// L2 (__ldcg) because other SMs wrote it.
+// threads per SM walks the levels in order, with a grid-wide barrier between
+// levels.  The barrier is split: a block arrives as soon as its rows of level
+// l are stored, then starts loading the structure of its rows of level l + 1
+// (which depends on no unknown) while the other blocks finish, and only then
+// waits.  The first KP entries of a row come from the position-major copy
+// (Tri::eidx / eval) through cp.async into shared memory, so they cost no
+// registers and a warp's loads are coalesced; only rows longer than KP read
+// the CSR arrays as well.  Chunks of 32 consecutive positions go to warps in
+// grid-cyclic order, so a level is spread over every SM.
+// The barrier counter only grows (arrivals = level * blocks) and needs no
+// reset within a launch; waits are bounded like every other wait here.  x is
+// read through L2 (__ldcg) because other SMs wrote it.
 constexpr int kCoopBlock = 1024;
 
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int* err) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// every thread of the block has stored its level; one release-add per block
+__device__ __forceinline__ void grid_arrive(unsigned* bar) {
     __syncthreads();
+    if (threadIdx.x == 0) red_release_add(bar, 1u);
+}
+
+// one acquire-spin per block, then the block barrier hands the ordering on
+__device__ __forceinline__ void grid_wait(unsigned* bar, unsigned target, int* err) {
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
         const unsigned long long t0 = globaltimer();
         while ((unsigned)ld_acquire(reinterpret_cast<const int*>(bar)) < target) {
             if (*(volatile int*)err != 0) break;
@@ -675,13 +704,11 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int
                 break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
 }
 
-// The first row a thread owns in a level, read before the barrier that
-// opens the level: nothing here depends on the unknowns being solved.
+// One row's structure and right-hand side, loaded ahead (wavefront solve).
 template <typename T, int KP>
 struct RowAhead {
     int row, e0, e1;
@@ -690,6 +717,7 @@ struct RowAhead {
     T a[KP];
 };
 
+// From the CSR arrays (entries past the row's end: column 0, value 0).
 template <typename T, int K, int KP>
 __device__ __forceinline__ void read_ahead(const Tri<T>& tri, const Rhs<T>& rhs, int t, RowAhead<T, KP>& r) {
     r.row = tri.order[t];
@@ -705,47 +733,195 @@ __device__ __forceinline__ void read_ahead(const Tri<T>& tri, const Rhs<T>& rhs,
     }
 }
 
+// Asynchronous global -> shared copies (no registers involved).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
+    if constexpr (sizeof(T) == 8) cp_async8(smem, gmem);
+    else cp_async4(smem, gmem);
+}
+
+// The part of a row kept in registers while its level waits.
+template <typename T>
+struct RowHead {
+    int row, e0, e1;  // e0: where the CSR remainder (entries past KP) starts
+    T rv, dg;
+};
+
+// Shared-memory slots of one thread: KP values, then KP column ids, strided
+// by the block size so that a warp's accesses hit distinct banks.
+template <typename T, int K, int KP>
+__device__ __forceinline__ void stage_row(const Tri<T>& tri, const Rhs<T>& rhs, int t, int32_t* js, T* as,
+                                          RowHead<T>& h) {
+    const size_t n = (size_t)tri.n;
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+        cp_async4(&js[q * kCoopBlock], &tri.eidx[q * n + t]);
+        cp_async_t<T>(&as[q * kCoopBlock], &tri.eval[q * n + t]);
+    }
+    cp_async_commit();
+    h.row = __ldg(&tri.order[t]);
+    h.e0 = __ldg(&tri.ptr[t]) + KP;
+    h.e1 = __ldg(&tri.ptr[t + 1]);
+    h.dg = tri.diag ? __ldg(&tri.diag[t]) : (T)1;
+    h.rv = rhs_full<T, K>(tri, rhs, t, h.row);
+}
+
+template <typename T, int KP>
+__device__ __forceinline__ void solve_staged(const Tri<T>& tri, const RowHead<T>& h, const int32_t* js,
+                                             const T* as, T* x) {
+    cp_async_wait_all();
+    int j[KP];
+    T v[KP];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) j[q] = js[q * kCoopBlock];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) v[q] = j[q] >= 0 ? __ldcg(&x[j[q]]) : (T)0;
+    T sum = (T)0;
+#pragma unroll
+    for (int q = 0; q < KP; ++q) sum += as[q * kCoopBlock] * v[q];
+    // the CSR remainder (rows longer than KP), four gathers in flight
+    int e = h.e0;
+    for (; e + 3 < h.e1; e += 4) {
+        const int j0 = __ldg(&tri.idx[e]), j1 = __ldg(&tri.idx[e + 1]), j2 = __ldg(&tri.idx[e + 2]),
+                  j3 = __ldg(&tri.idx[e + 3]);
+        const T a0 = __ldg(&tri.val[e]), a1 = __ldg(&tri.val[e + 1]), a2 = __ldg(&tri.val[e + 2]),
+                a3 = __ldg(&tri.val[e + 3]);
+        const T v0 = __ldcg(&x[j0]), v1 = __ldcg(&x[j1]), v2 = __ldcg(&x[j2]), v3 = __ldcg(&x[j3]);
+        sum += a0 * v0;
+        sum += a1 * v1;
+        sum += a2 * v2;
+        sum += a3 * v3;
+    }
+    for (; e < h.e1; ++e) sum += __ldg(&tri.val[e]) * __ldcg(&x[__ldg(&tri.idx[e])]);
+    T res = h.rv - sum;
+    if (tri.diag) res = res / h.dg;
+    x[h.row] = res;
+}
+
+// A row straight from the CSR arrays (rows past the first of a wide level).
 template <typename T, int K>
+__device__ __forceinline__ void solve_row_csr(const Tri<T>& tri, const Rhs<T>& rhs, int t, T* x) {
+    const int row = __ldg(&tri.order[t]);
+    const int e1 = __ldg(&tri.ptr[t + 1]);
+    int e = __ldg(&tri.ptr[t]);
+    const T dg = tri.diag ? __ldg(&tri.diag[t]) : (T)1;
+    T sum = (T)0;
+    for (; e + 3 < e1; e += 4) {
+        const int j0 = __ldg(&tri.idx[e]), j1 = __ldg(&tri.idx[e + 1]), j2 = __ldg(&tri.idx[e + 2]),
+                  j3 = __ldg(&tri.idx[e + 3]);
+        const T a0 = __ldg(&tri.val[e]), a1 = __ldg(&tri.val[e + 1]), a2 = __ldg(&tri.val[e + 2]),
+                a3 = __ldg(&tri.val[e + 3]);
+        const T v0 = __ldcg(&x[j0]), v1 = __ldcg(&x[j1]), v2 = __ldcg(&x[j2]), v3 = __ldcg(&x[j3]);
+        sum += a0 * v0;
+        sum += a1 * v1;
+        sum += a2 * v2;
+        sum += a3 * v3;
+    }
+    for (; e < e1; ++e) sum += __ldg(&tri.val[e]) * __ldcg(&x[__ldg(&tri.idx[e])]);
+    T res = rhs_full<T, K>(tri, rhs, t, row) - sum;
+    if (tri.diag) res = res / dg;
+    x[row] = res;
+}
+
+// Dynamic shared memory of k_trsv_coop.
+template <typename T>
+constexpr size_t coop_smem_bytes(int kp) {
+    return (size_t)kp * kCoopBlock * (sizeof(int32_t) + sizeof(T));
+}
+
+template <typename T, int K, int KP>
 __global__ void __launch_bounds__(kCoopBlock, 1)
 k_trsv_coop(Tri<T> tri, Rhs<T> rhs, T* x, const int32_t* __restrict__ level_ptr, int nlevels, unsigned* bar,
             const LsmrState* S, int* err) {
-    constexpr int KP = 8;
     if (S->done) return;
+    extern __shared__ __align__(16) unsigned char coop_smem[];
+    T* as = reinterpret_cast<T*>(coop_smem) + threadIdx.x;
+    int32_t* js = reinterpret_cast<int32_t*>(coop_smem + (size_t)KP * kCoopBlock * sizeof(T)) + threadIdx.x;
     const int nthreads = gridDim.x * kCoopBlock;
-    // block-cyclic: consecutive rows of a level go to different SMs, so every
-    // SM's load/store unit carries 1/gridDim of the level's gathers
-    const int tid = threadIdx.x * gridDim.x + blockIdx.x;
-    RowAhead<T, KP> ra;
-    int lo = level_ptr[0], hi = level_ptr[1];
-    if (lo + tid < hi) read_ahead<T, K, KP>(tri, rhs, lo + tid, ra);
+    const int tid = (((threadIdx.x >> 5) * gridDim.x + blockIdx.x) << 5) + (threadIdx.x & 31);
+    RowHead<T> h;
+    int lo = __ldg(&level_ptr[0]), hi = __ldg(&level_ptr[1]);
+    if (lo + tid < hi) stage_row<T, K, KP>(tri, rhs, lo + tid, js, as, h);
     for (int l = 0; l < nlevels; ++l) {
-        int t = lo + tid;
+        const int t = lo + tid;
         if (t < hi) {
-            // first row: its structure is already in registers, so all its
-            // gathers of solved unknowns go out at once
-            T sum = (T)0;
-#pragma unroll
-            for (int q = 0; q < KP; ++q) sum += ra.a[q] * __ldcg(&x[ra.j[q]]);
-            for (int e = ra.e0 + KP; e < ra.e1; ++e) sum += tri.val[e] * __ldcg(&x[tri.idx[e]]);
-            T v = ra.rv - sum;
-            if (tri.diag) v = v / ra.dg;
-            x[ra.row] = v;
-            // further rows of a wide level
-            for (t += nthreads; t < hi; t += nthreads) {
-                const int row = tri.order[t];
-                T s2 = (T)0;
-                for (int e = tri.ptr[t]; e < tri.ptr[t + 1]; ++e) s2 += tri.val[e] * __ldcg(&x[tri.idx[e]]);
-                T w = rhs_full<T, K>(tri, rhs, t, row) - s2;
-                if (tri.diag) w = w / tri.diag[t];
-                x[row] = w;
-            }
+            solve_staged<T, KP>(tri, h, js, as, x);
+            for (int t2 = t + nthreads; t2 < hi; t2 += nthreads) solve_row_csr<T, K>(tri, rhs, t2, x);
         }
         if (l + 1 < nlevels) {
+            grid_arrive(bar);
             lo = hi;
-            hi = level_ptr[l + 2];
-            if (lo + tid < hi) read_ahead<T, K, KP>(tri, rhs, lo + tid, ra);
-            grid_barrier(bar, (unsigned)(l + 1) * gridDim.x, err);
+            hi = __ldg(&level_ptr[l + 2]);
+            if (lo + tid < hi) stage_row<T, K, KP>(tri, rhs, lo + tid, js, as, h);
+            grid_wait(bar, (unsigned)(l + 1) * gridDim.x, err);
         }
+    }
+}
+
+// Wavefront solve: a co-resident grid in which every thread owns a fixed,
+// increasing sequence of level-ordered positions and solves them one after
+// another, waiting on each unknown it reads (all-one bit pattern = not yet
+// written, as in k_trsv_sentinel).  There are no tickets and no barriers:
+// a row starts as soon as its own inputs exist, so rows of many levels are in
+// flight at once and the solve pipelines across levels.  Chunks of 32
+// consecutive positions go to warps in grid-cyclic order (warp ids run across
+// blocks first), which keeps the structure reads coalesced and spreads each
+// level over all SMs.  While a row waits, the structure of the thread's next
+// row is already loading (it does not depend on any unknown).
+// Progress: the smallest unsolved position has all its inputs solved and its
+// thread has finished every earlier position it owns, so it is being worked
+// on; this needs every thread resident, hence the cooperative launch.
+constexpr int kWaveBlock = 256;
+
+template <typename T, int K, int KP>
+__global__ void __launch_bounds__(kWaveBlock)
+k_trsv_wave(Tri<T> tri, Rhs<T> rhs, T* x, const LsmrState* S, int* err) {
+    if (S->done) return;
+    const int n = tri.n;
+    const int lane = threadIdx.x & 31;
+    const int warp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int stride = 32 * gridDim.x * (kWaveBlock / 32);
+    int t = 32 * warp + lane;
+    if (t >= n) return;
+    RowAhead<T, KP> cur;
+    read_ahead<T, K, KP>(tri, rhs, t, cur);
+    bool ok = true;
+    for (;;) {
+        const int tn = t + stride;
+        RowAhead<T, KP> nxt;
+        if (tn < n) read_ahead<T, K, KP>(tri, rhs, tn, nxt);
+        T v[KP];
+#pragma unroll
+        for (int q = 0; q < KP; ++q) v[q] = (cur.e0 + q < cur.e1) ? ld_relaxed(&x[cur.j[q]]) : (T)0;
+        T sum = (T)0;
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            if (is_pending(v[q])) v[q] = wait_value(&x[cur.j[q]], err, ok);
+            sum += cur.a[q] * v[q];
+        }
+        for (int e = cur.e0 + KP; e < cur.e1; ++e) {
+            const int j = tri.idx[e];
+            T w = ld_relaxed(&x[j]);
+            if (is_pending(w)) w = wait_value(&x[j], err, ok);
+            sum += tri.val[e] * w;
+        }
+        T r = cur.rv - sum;
+        if (tri.diag) r = r / cur.dg;
+        if (!ok) r = (T)NAN;
+        st_relaxed(&x[cur.row], r);
+        if (tn >= n) break;
+        cur = nxt;
+        t = tn;
     }
 }
 

@@ -79,7 +79,24 @@ void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const st
             }
             return lo;
         };
-        tri[w].upload(permute(M.T), s);
+        const HostCSR T_pos = permute(M.T);
+        tri[w].upload(T_pos, s);
+        {
+            const size_t nn = static_cast<size_t>(T_pos.rows);
+            const int kp = (static_cast<double>(T_pos.nnz()) <= 4.5 * static_cast<double>(std::max<size_t>(nn, 1))) ? 4 : 8;
+            std::vector<int32_t> ei(static_cast<size_t>(kp) * std::max<size_t>(nn, 1), -1);
+            std::vector<double> ev(ei.size(), 0.0);
+            for (size_t t = 0; t < nn; ++t) {
+                const int64_t e0 = T_pos.ptr[t], e1 = std::min<int64_t>(T_pos.ptr[t + 1], e0 + kp);
+                for (int64_t e = e0; e < e1; ++e) {
+                    ei[static_cast<size_t>(e - e0) * nn + t] = T_pos.idx[e];
+                    ev[static_cast<size_t>(e - e0) * nn + t] = T_pos.val[e];
+                }
+            }
+            ell_kp[w] = kp;
+            ell_idx[w].upload(ei.data(), ei.size(), s);
+            upload_vec(ell_val[w], ev, s);
+        }
         if (M.R.nnz() > 0) rtri[w].upload(permute(M.R), s);
         else { rtri[w].ptr.release(); rtri[w].idx.release(); rtri[w].val.release(); rtri[w].nnz = 0; }
         order[w].upload(ord.data(), ord.size(), s);
@@ -180,6 +197,22 @@ static double mv_bytes(const DevCsr<T>& M, double in_bytes_per_col, double out_b
            in_bytes_per_col * M.cols + out_bytes_per_row * M.rows;
 }
 
+// Opt-in shared memory of the persistent solve (more than the default 48 KB
+// for 8 entries in float64); set outside any stream capture.
+template <typename T>
+static void coop_attributes() {
+    auto set = [](auto kern, int kp) {
+        RLSQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(coop_smem_bytes<T>(kp))));
+    };
+    set(k_trsv_coop<T, RHS_VEC, 4>, 4);
+    set(k_trsv_coop<T, RHS_VEC, 8>, 8);
+    set(k_trsv_coop<T, RHS_SUB, 4>, 4);
+    set(k_trsv_coop<T, RHS_SUB, 8>, 8);
+    set(k_trsv_coop<T, RHS_SCALED, 4>, 4);
+    set(k_trsv_coop<T, RHS_SCALED, 8>, 8);
+}
+
 template <typename T>
 static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, Rhs<T> rhs, T* x,
                         int slot, LsmrState* S, cudaStream_t st) {
@@ -204,11 +237,12 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
         if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
         const int nlev = static_cast<int>(F.level_ptr[which].size()) - 1;
         with_rhs(rk, [&](auto k) {
-            auto kern = k_trsv_coop<T, decltype(k)::value>;
+            const int kp = F.ell_kp[which] >= 8 ? 8 : 4;
+            auto kern = kp == 8 ? k_trsv_coop<T, decltype(k)::value, 8> : k_trsv_coop<T, decltype(k)::value, 4>;
             cudaLaunchConfig_t cfg{};
             cfg.gridDim = dim3(static_cast<unsigned>(P->coop_blocks));
             cfg.blockDim = dim3(kCoopBlock);
-            cfg.dynamicSmemBytes = 0;
+            cfg.dynamicSmemBytes = coop_smem_bytes<T>(kp);
             cfg.stream = st;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeCooperative;
@@ -217,6 +251,31 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
             cfg.numAttrs = 1;
             RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, F.level_ptr_d[which].p, nlev,
                                          P->barriers.p + slot, static_cast<const LsmrState*>(S), error_word(S)));
+        });
+    } else if (P->map.sched[which] == RLSQ_TRSV_WAVE) {
+        // all-one bytes mark "not yet solved" (see k_trsv_wave)
+        RLSQ_CUDA(cudaMemsetAsync(x, 0xff, sizeof(T) * static_cast<size_t>(n), st));
+        const int kp = P->map.wave_kp[which];
+        with_rhs(rk, [&](auto k) {
+            auto run = [&](auto kern) {
+                int occ = 0;
+                RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWaveBlock, 0));
+                const int need = (n + kWaveBlock - 1) / kWaveBlock;
+                const int grid = std::max(1, std::min(need, std::max(1, occ) * P->num_sms));
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = dim3(static_cast<unsigned>(grid));
+                cfg.blockDim = dim3(kWaveBlock);
+                cfg.stream = st;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeCooperative;
+                attr[0].val.cooperative = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, static_cast<const LsmrState*>(S),
+                                             error_word(S)));
+            };
+            if (kp >= 8) run(k_trsv_wave<T, decltype(k)::value, 8>);
+            else run(k_trsv_wave<T, decltype(k)::value, 4>);
         });
     } else {
         if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
@@ -513,6 +572,7 @@ static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
     for (size_t w = 0; w < P->merged.size() && w < 4; ++w) {
         info->solve_levels[w] = P->merged[w].lev.nlevels;
         info->level_merge[w] = P->merged[w].k;
+        info->trsv_schedule[w] = P->map.sched[w];
     }
     info->bytes_per_iter = algorithmic_bytes(P, !P->factored);
 }
@@ -925,10 +985,14 @@ int rlsq_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* coli
         P->tickets.alloc(kMaxSlots);
         P->barriers.alloc(kMaxSlots);
         {
+            coop_attributes<double>();
+            coop_attributes<float>();
             int occ = 0;
-            RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trsv_coop<double, RHS_VEC>, kCoopBlock, 0));
+            RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trsv_coop<double, RHS_VEC, 8>, kCoopBlock,
+                                                                    coop_smem_bytes<double>(8)));
             int occ32 = 0;
-            RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_trsv_coop<float, RHS_VEC>, kCoopBlock, 0));
+            RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_trsv_coop<float, RHS_VEC, 8>, kCoopBlock,
+                                                                    coop_smem_bytes<float>(8)));
             P->coop_blocks = std::max(1, std::min(occ, occ32)) * P->num_sms;
         }
         default_mapping(P.get());
@@ -1031,7 +1095,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         h->precision = opts.precision;
         default_mapping(h);
         if (opts.trsv_schedule == RLSQ_TRSV_LEVEL || opts.trsv_schedule == RLSQ_TRSV_SYNCFREE ||
-            opts.trsv_schedule == RLSQ_TRSV_COOP)
+            opts.trsv_schedule == RLSQ_TRSV_COOP || opts.trsv_schedule == RLSQ_TRSV_WAVE)
             for (int w = 0; w < 4; ++w) h->map.sched[w] = opts.trsv_schedule;
         h->factored = true;
         if (opts.autotune) autotune(h);

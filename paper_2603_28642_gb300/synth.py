@@ -36,6 +36,7 @@ __all__ = [
     "serving_matrices",
     "serving_rhs",
     "random_rhs",
+    "poisson_arrivals",
 ]
 
 
@@ -279,3 +280,10 @@ def random_rhs(prob: Problem, seed: int, noise: float = 1e-3) -> np.ndarray:
 def serving_rhs(prob: Problem, request_id: int) -> np.ndarray:
     """Right-hand side of serving request ``request_id`` (seed 10**6 + id)."""
     return random_rhs(prob, 10**6 + request_id)
+
+
+def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate: cumulative
+    sums of exponential(1/rate) gaps drawn from PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))

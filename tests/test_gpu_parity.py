@@ -112,7 +112,7 @@ SOLVES = [(B.SYS_L1, "solve_L1"), (B.SYS_L1T, "solve_L1t"), (B.SYS_U, "solve_U")
           (B.SYS_UT, "solve_Ut")]
 
 
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE])
 @pytest.mark.parametrize("which", ["cfg0", "mid"])
 def test_triangular_solves(sched, which, request):
     prob = request.getfixturevalue(which)
@@ -124,6 +124,26 @@ def test_triangular_solves(sched, which, request):
         x = P.trsv(sys_id, b)
         ref = getattr(f, name)(b)
         assert rel(x, ref) <= 1e-12, (sys_id, rel(x, ref))
+
+
+@pytest.fixture(scope="module")
+def wide():
+    # more rows than the wavefront solve has resident threads, so every thread
+    # walks several positions (and the sync-free solve many ticket rounds)
+    prob = synth.sparse_problem(900_001, 600_001, 3, seed=77, hidden_diag=True)
+    return prob, oracle_factor(prob, oracle.CG)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("sched", [B.TRSV_WAVE, B.TRSV_SYNCFREE])
+def test_triangular_solves_many_rounds(wide, sched, k):
+    prob, f = wide
+    P = make(prob, B.CORR_CG, sched=sched, level_merge=k)
+    b = np.random.default_rng(11).standard_normal(prob.n)
+    for sys_id, name in SOLVES:
+        x = P.trsv(sys_id, b)
+        assert rel(x, getattr(f, name)(b)) <= 1e-12, (sys_id, rel(x, getattr(f, name)(b)))
+    assert rel(P.apply(b), f.apply(b)) <= 1e-12
 
 
 def test_triangular_solves_all_lane_counts(cfg0):
@@ -140,7 +160,7 @@ def test_triangular_solves_all_lane_counts(cfg0):
 # one preconditioner application, every correction mode
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("modes", MODES, ids=["NONE", "SI", "CG", "DENSE"])
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE])
 def test_apply_fp64(cfg0, modes, sched):
     bm, om = modes
     P = make(cfg0, bm, sched=sched)
@@ -335,7 +355,7 @@ def test_dense_block_off_gives_same_solution(sparse_dense):
 # fused levels: same solutions, fewer levels
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("k", [1, 2, 3])
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE])
 def test_fused_levels_solves(mid, k, sched):
     P = make(mid, B.CORR_CG, sched=sched, level_merge=k)
     info = P.info()
