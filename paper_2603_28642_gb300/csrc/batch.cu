@@ -223,12 +223,12 @@ kb_trsv_level(const BSlot<T>* slots, const int32_t* phase, int want, int cond, i
     for (int t = lo + blockIdx.x * kBlock + threadIdx.x; t < hi; t += gridDim.x * kBlock) {
         const int row = tri.order[t];
         const T rv = rhs_full<T, K>(tri, rhs, t, row);
-        const T dg = tri.diag ? tri.diag[t] : (T)1;
+        const T dg = tri.idiag ? tri.idiag[t] : (T)1;
         T sum = (T)0;
         const int e1 = tri.ptr[t + 1];
         for (int e = tri.ptr[t]; e < e1; ++e) sum += tri.val[e] * x[tri.idx[e]];
         T v = rv - sum;
-        if (tri.diag) v = v / dg;
+        if (tri.idiag) v = v * dg;
         x[row] = v;
     }
 }

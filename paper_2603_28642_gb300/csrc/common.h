@@ -99,7 +99,7 @@ template <typename T>
 struct DevFactor {
     DevCsr<T> tri[4];          // strictly triangular parts: L1, L1^T, U, U^T (after level fusing)
     DevCsr<T> rtri[4];         // right-hand-side terms of fused rows (empty when not fused)
-    DevArray<T> diag[4];       // U diagonal for U and U^T (unit for L1, L1^T)
+    DevArray<T> diag[4];       // inverse U diagonal for U and U^T, by position (unit for L1, L1^T)
     DevArray<int32_t> order[4];
     std::vector<int32_t> level_ptr[4];
     DevArray<int32_t> level_ptr_d[4];  // device copies for the persistent solve

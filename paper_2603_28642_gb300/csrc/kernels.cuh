@@ -186,8 +186,12 @@ __device__ __forceinline__ void row_dot(const Csr<TV>& a, int row, int lane, con
     int e = a.ptr[row] + lane;
     for (; e + 3 * G < e1; e += 4 * G) {
         const int j0 = a.idx[e], j1 = a.idx[e + G], j2 = a.idx[e + 2 * G], j3 = a.idx[e + 3 * G];
-        s += (TA)a.val[e] * (TA)x[j0] + (TA)a.val[e + G] * (TA)x[j1] + (TA)a.val[e + 2 * G] * (TA)x[j2] +
-             (TA)a.val[e + 3 * G] * (TA)x[j3];
+        const TA a0 = (TA)a.val[e], a1 = (TA)a.val[e + G], a2 = (TA)a.val[e + 2 * G], a3 = (TA)a.val[e + 3 * G];
+        const TA x0 = (TA)x[j0], x1 = (TA)x[j1], x2 = (TA)x[j2], x3 = (TA)x[j3];
+        s = fma(a0, x0, s);
+        s = fma(a1, x1, s);
+        s = fma(a2, x2, s);
+        s = fma(a3, x3, s);
     }
     for (; e < e1; e += G) s += (TA)a.val[e] * (TA)x[a.idx[e]];
 }
@@ -208,8 +212,16 @@ __device__ __forceinline__ void row_dot_pair(const Csr<TV>& a, int row, int lane
         const int j0 = a.idx[e], j1 = a.idx[e + G], j2 = a.idx[e + 2 * G], j3 = a.idx[e + 3 * G];
         const double a0 = a.val[e], a1 = a.val[e + G], a2 = a.val[e + 2 * G], a3 = a.val[e + 3 * G];
         const double2 p0 = p[j0], p1 = p[j1], p2 = p[j2], p3 = p[j3];
-        s1 += a0 * p0.x + a1 * p1.x + a2 * p2.x + a3 * p3.x;
-        s2 += a0 * p0.y + a1 * p1.y + a2 * p2.y + a3 * p3.y;
+        // one fused multiply-add per entry and vector: float64 issue slots
+        // are the scarce resource of these products on this GPU
+        s1 = fma(a0, p0.x, s1);
+        s2 = fma(a0, p0.y, s2);
+        s1 = fma(a1, p1.x, s1);
+        s2 = fma(a1, p1.y, s2);
+        s1 = fma(a2, p2.x, s1);
+        s2 = fma(a2, p2.y, s2);
+        s1 = fma(a3, p3.x, s1);
+        s2 = fma(a3, p3.y, s2);
     }
     for (; e < e1; e += G) {
         const double2 pj = p[a.idx[e]];
@@ -447,7 +459,7 @@ struct Tri {
     const int32_t* ptr;    // n + 1, by position
     const int32_t* idx;    // unknown ids of the entries
     const T* val;
-    const T* diag;         // by position; nullptr: unit diagonal
+    const T* idiag;        // inverse diagonal by position; nullptr: unit diagonal
     const int32_t* order;  // order[t]: unknown solved at position t
     // right-hand-side terms of rows whose same-group dependencies were
     // substituted (fused levels): x_i uses rhs_i + sum rval * rhs(ridx);
@@ -547,7 +559,7 @@ k_trsv_syncfree(Tri<T> tri, Rhs<T> rhs, T* x, int* flags, int slot, unsigned* ti
             ok = __all_sync(mask, ok);
             if (lane == 0) {
                 T v = rhs_full<T, K>(tri, rhs, (int)tpos, row) - sum;
-                if (tri.diag) v = v / tri.diag[tpos];
+                if (tri.idiag) v = v * tri.idiag[tpos];
                 if (!ok) v = (T)NAN;
                 x[row] = v;
                 st_release(&flags[row], epoch);
@@ -635,7 +647,7 @@ k_trsv_sentinel(Tri<T> tri, Rhs<T> rhs, T* x, int slot, unsigned* tickets, const
             // everything that does not depend on other rows, loaded up front
             const int row = tri.order[tpos];
             const T rv = rhs_full<T, K>(tri, rhs, (int)tpos, row);
-            const T dg = tri.diag ? tri.diag[tpos] : (T)1;
+            const T dg = tri.idiag ? tri.idiag[tpos] : (T)1;
             T sum = (T)0;
             bool ok = true;
             for (; e + 3 * G < e1; e += 4 * G) {
@@ -660,7 +672,7 @@ k_trsv_sentinel(Tri<T> tri, Rhs<T> rhs, T* x, int slot, unsigned* tickets, const
             }
             if (lane == 0) {
                 T v = rv - sum;
-                if (tri.diag) v = v / dg;
+                if (tri.idiag) v = v * dg;
                 if (!ok) v = (T)NAN;
                 st_relaxed(&x[row], v);
             }
@@ -724,7 +736,7 @@ __device__ __forceinline__ void read_ahead(const Tri<T>& tri, const Rhs<T>& rhs,
     r.e0 = tri.ptr[t];
     r.e1 = tri.ptr[t + 1];
     r.rv = rhs_full<T, K>(tri, rhs, t, r.row);
-    r.dg = tri.diag ? tri.diag[t] : (T)1;
+    r.dg = tri.idiag ? tri.idiag[t] : (T)1;
 #pragma unroll
     for (int q = 0; q < KP; ++q) {
         const bool in = r.e0 + q < r.e1;
@@ -772,7 +784,7 @@ __device__ __forceinline__ void stage_row(const Tri<T>& tri, const Rhs<T>& rhs, 
     h.row = __ldg(&tri.order[t]);
     h.e0 = __ldg(&tri.ptr[t]) + KP;
     h.e1 = __ldg(&tri.ptr[t + 1]);
-    h.dg = tri.diag ? __ldg(&tri.diag[t]) : (T)1;
+    h.dg = tri.idiag ? __ldg(&tri.idiag[t]) : (T)1;
     h.rv = rhs_full<T, K>(tri, rhs, t, h.row);
 }
 
@@ -804,7 +816,7 @@ __device__ __forceinline__ void solve_staged(const Tri<T>& tri, const RowHead<T>
     }
     for (; e < h.e1; ++e) sum += __ldg(&tri.val[e]) * __ldcg(&x[__ldg(&tri.idx[e])]);
     T res = h.rv - sum;
-    if (tri.diag) res = res / h.dg;
+    if (tri.idiag) res = res * h.dg;
     x[h.row] = res;
 }
 
@@ -814,7 +826,7 @@ __device__ __forceinline__ void solve_row_csr(const Tri<T>& tri, const Rhs<T>& r
     const int row = __ldg(&tri.order[t]);
     const int e1 = __ldg(&tri.ptr[t + 1]);
     int e = __ldg(&tri.ptr[t]);
-    const T dg = tri.diag ? __ldg(&tri.diag[t]) : (T)1;
+    const T dg = tri.idiag ? __ldg(&tri.idiag[t]) : (T)1;
     T sum = (T)0;
     for (; e + 3 < e1; e += 4) {
         const int j0 = __ldg(&tri.idx[e]), j1 = __ldg(&tri.idx[e + 1]), j2 = __ldg(&tri.idx[e + 2]),
@@ -829,7 +841,7 @@ __device__ __forceinline__ void solve_row_csr(const Tri<T>& tri, const Rhs<T>& r
     }
     for (; e < e1; ++e) sum += __ldg(&tri.val[e]) * __ldcg(&x[__ldg(&tri.idx[e])]);
     T res = rhs_full<T, K>(tri, rhs, t, row) - sum;
-    if (tri.diag) res = res / dg;
+    if (tri.idiag) res = res * dg;
     x[row] = res;
 }
 
@@ -916,7 +928,7 @@ k_trsv_wave(Tri<T> tri, Rhs<T> rhs, T* x, const LsmrState* S, int* err) {
             sum += tri.val[e] * w;
         }
         T r = cur.rv - sum;
-        if (tri.diag) r = r / cur.dg;
+        if (tri.idiag) r = r * cur.dg;
         if (!ok) r = (T)NAN;
         st_relaxed(&x[cur.row], r);
         if (tn >= n) break;
@@ -936,14 +948,14 @@ k_trsv_level(Tri<T> tri, Rhs<T> rhs, T* x, int lo, int hi, const LsmrState* S) {
     for (int tpos = lo + (blockIdx.x * kBlock + threadIdx.x) / G; tpos < hi; tpos += groups) {
         const int row = tri.order[tpos];
         const T rv = rhs_full<T, K>(tri, rhs, tpos, row);
-        const T dg = tri.diag ? tri.diag[tpos] : (T)1;
+        const T dg = tri.idiag ? tri.idiag[tpos] : (T)1;
         T sum = (T)0;
         const int e1 = tri.ptr[tpos + 1];
         for (int e = tri.ptr[tpos] + lane; e < e1; e += G) sum += tri.val[e] * x[tri.idx[e]];
         if (G > 1) sum = group_sum<G>(sum, mask);
         if (lane == 0) {
             T v = rv - sum;
-            if (tri.diag) v = v / dg;
+            if (tri.idiag) v = v * dg;
             x[row] = v;
         }
     }
@@ -995,7 +1007,9 @@ k_l2_start(Csr<T> L2, const T* __restrict__ q1, T* __restrict__ r, LsmrState* S,
     }
 }
 
-// c1 = L2^T p' with p' = r (first step) or r + beta p
+// c1 = L2^T p' with p' = r (first step) or r + beta p.  After the first step
+// L2^T p' = L2^T r + beta (L2^T p), and c1 still holds L2^T p from the step
+// before, so only L2^T r is formed (one multiply-add per entry).
 template <typename T, int G, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
 k_l2t_cg(Csr<T> L2t, const T* __restrict__ r, const T* __restrict__ p, T* __restrict__ c1,
@@ -1007,22 +1021,11 @@ k_l2t_cg(Csr<T> L2t, const T* __restrict__ r, const T* __restrict__ p, T* __rest
     const int groups = (gridDim.x * kBlock) / G;
     for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2t.rows; row += groups) {
         T s = (T)0;
-        const int e1 = L2t.ptr[row + 1];
-        int e = L2t.ptr[row] + lane;
-        for (; e + G < e1; e += 2 * G) {
-            const int j0 = L2t.idx[e], j1 = L2t.idx[e + G];
-            const T p0 = FIRST ? r[j0] : r[j0] + beta * p[j0];
-            const T p1 = FIRST ? r[j1] : r[j1] + beta * p[j1];
-            s += L2t.val[e] * p0 + L2t.val[e + G] * p1;
-        }
-        for (; e < e1; e += G) {
-            const int j = L2t.idx[e];
-            const T pj = FIRST ? r[j] : r[j] + beta * p[j];
-            s += L2t.val[e] * pj;
-        }
+        row_dot<G>(L2t, row, lane, r, s);
         s = group_sum<G>(s, mask);
-        if (lane == 0) c1[row] = s;
+        if (lane == 0) c1[row] = FIRST ? s : s + beta * c1[row];
     }
+    (void)p;
 }
 
 // p <- r (+ beta p); Sp = p + L2 c3; totals: a = rr / <p, Sp>

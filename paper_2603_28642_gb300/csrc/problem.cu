@@ -104,7 +104,9 @@ void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const st
         level_ptr_d[w].upload(level_ptr[w].data(), level_ptr[w].size(), s);
         if (w >= 2) {
             std::vector<double> dl(ord.size());
-            for (size_t t = 0; t < ord.size(); ++t) dl[t] = F.Udiag[ord[t]];
+            // the solves multiply by the inverse diagonal (a float64 division is
+            // a long instruction sequence on this GPU)
+            for (size_t t = 0; t < ord.size(); ++t) dl[t] = 1.0 / F.Udiag[ord[t]];
             upload_vec(diag[w], dl, s);
         }
     }
@@ -335,7 +337,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
             for (int it = 0; it < P->opts.cg_steps; ++it) {
                 const bool first = (it == 0);
                 {
-                    RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, first ? sizeof(T) : 2 * sizeof(T), sizeof(T)), st);
+                    RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, sizeof(T), first ? sizeof(T) : 2 * sizeof(T)), st);
                     with_G(P->map.G_L2t, [&](auto g) {
                         constexpr int GG = decltype(g)::value;
                         if (first) k_l2t_cg<T, GG, true><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S);
