@@ -112,7 +112,10 @@ typedef struct {
     int32_t host_threads;  /* threads for the dense S set-up (0 = hardware concurrency) */
     int32_t level_merge;   /* levels fused per group in the triangular solves: 1 = none,
                               k > 1 = groups of k levels (same-group dependencies are
-                              substituted on the host), 0 = chosen per system */
+                              substituted on the host), 0 = chosen per system by a
+                              cost model (per level and per stored entry) among
+                              k = 1..4 and groups grown level by level (a level
+                              joins while the fill it adds costs less than a level) */
 } rlsq_factor_opts;
 
 /* Options of a solve. */
@@ -140,7 +143,8 @@ typedef struct {
     int32_t precision;
     double bytes_per_iter; /* algorithmic HBM bytes of one LSMR iteration */
     int32_t solve_levels[4]; /* levels the GPU walks per system after fusing (RLSQ_SYS_* order) */
-    int32_t level_merge[4];  /* fused levels per group, per system */
+    int32_t level_merge[4];  /* fused levels per group, per system (groups chosen level by level:
+                                the largest group) */
     int32_t trsv_schedule[4]; /* RLSQ_TRSV_* each system runs with (after autotuning) */
 } rlsq_info;
 

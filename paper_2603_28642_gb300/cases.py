@@ -1,0 +1,76 @@
+"""Small, self-contained runs of single pieces of the path, for profilers.
+
+Each case builds the 2M x 1M workload recipe (scaled by --scale), factors it
+(p = 10, tau = 1e-2, mu = 1, CG(2)) and runs one piece on the GPU, with the
+part worth capturing inside an NVTX range named `timed`:
+
+    python -m paper_2603_28642_gb300.cases trsv --system U --schedule coop --scale 0.25
+    python -m paper_2603_28642_gb300.cases iteration --scale 0.75
+
+`trsv` calls rlsq_trsv on one system a few times; `iteration` autotunes and
+profiles one preconditioned LSMR iteration.  Everything runs through the C ABI.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import numpy as np
+
+from . import binding as B
+from . import synth
+
+SYSTEMS = {"L1": B.SYS_L1, "L1t": B.SYS_L1T, "U": B.SYS_U, "Ut": B.SYS_UT}
+SCHEDULES = {"auto": B.TRSV_AUTO, "level": B.TRSV_LEVEL, "syncfree": B.TRSV_SYNCFREE, "coop": B.TRSV_COOP,
+             "wave": B.TRSV_WAVE}
+FACTOR = dict(p=10, tau=1e-2, mu=1.0, correction=B.CORR_CG, cg_steps=2)
+
+
+def _nvtx(push: bool):
+    try:
+        import torch
+
+        if push:
+            torch.cuda.nvtx.range_push("timed")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(prog="python -m paper_2603_28642_gb300.cases")
+    sub = ap.add_subparsers(dest="case", required=True)
+    t = sub.add_parser("trsv")
+    t.add_argument("--system", choices=list(SYSTEMS), default="U")
+    t.add_argument("--schedule", choices=list(SCHEDULES), default="coop")
+    t.add_argument("--merge", type=int, default=1)
+    t.add_argument("--repeat", type=int, default=3)
+    t.add_argument("--scale", type=float, default=0.25)
+    it = sub.add_parser("iteration")
+    it.add_argument("--scale", type=float, default=0.75)
+    it.add_argument("--fp32", action="store_true")
+    args = ap.parse_args(argv)
+
+    prob = synth.config_problem(1, scale=args.scale)
+    P = B.Problem.from_problem(prob)
+    if args.case == "trsv":
+        P.factor(**FACTOR, trsv_schedule=SCHEDULES[args.schedule], level_merge=args.merge)
+        b = np.random.default_rng(0).standard_normal(prob.n)
+        _nvtx(True)
+        for _ in range(args.repeat):
+            x = P.trsv(SYSTEMS[args.system], b)
+        _nvtx(False)
+        print(f"trsv {args.system} ({args.schedule}, merge {args.merge}): |x| = {np.linalg.norm(x):.6e}")
+    else:
+        info = P.factor(**FACTOR, precision=B.PREC_FP32 if args.fp32 else B.PREC_FP64, autotune=1)
+        _nvtx(True)
+        prof = P.profile(prob.b, warmup=1, iters=1)
+        _nvtx(False)
+        print(f"iteration: {prof['ms_per_iter']:.4f} ms, schedules {info['trsv_schedule']}, "
+              f"levels {info['solve_levels']}")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -226,7 +226,17 @@ kb_trsv_level(const BSlot<T>* slots, const int32_t* phase, int want, int cond, i
         const T dg = tri.idiag ? tri.idiag[t] : (T)1;
         T sum = (T)0;
         const int e1 = tri.ptr[t + 1];
-        for (int e = tri.ptr[t]; e < e1; ++e) sum += tri.val[e] * x[tri.idx[e]];
+        int e = tri.ptr[t];
+        for (; e + 3 < e1; e += 4) {
+            const int j0 = tri.idx[e], j1 = tri.idx[e + 1], j2 = tri.idx[e + 2], j3 = tri.idx[e + 3];
+            const T a0 = tri.val[e], a1 = tri.val[e + 1], a2 = tri.val[e + 2], a3 = tri.val[e + 3];
+            const T v0 = x[j0], v1 = x[j1], v2 = x[j2], v3 = x[j3];
+            sum += a0 * v0;
+            sum += a1 * v1;
+            sum += a2 * v2;
+            sum += a3 * v3;
+        }
+        for (; e < e1; ++e) sum += tri.val[e] * x[tri.idx[e]];
         T v = rv - sum;
         if (tri.idiag) v = v * dg;
         x[row] = v;
@@ -538,8 +548,11 @@ struct Engine {
 
     // cover a matrix (its levels, sizes, correction) in the captured graphs
     void cover(const rlsq_problem_s* P) {
+        // the solves walk the fused levels (the ones uploaded with the factor)
         const IlupResult& F = *P->F;
         const Levels* L[4] = {&F.lev_L1, &F.lev_L1t, &F.lev_U, &F.lev_Ut};
+        if (P->merged.size() == 4)
+            for (int w = 0; w < 4; ++w) L[w] = &P->merged[w].lev;
         bool grow = false;
         for (int w = 0; w < 4; ++w) {
             if (L[w]->nlevels > maxlev[w]) { maxlev[w] = L[w]->nlevels; grow = true; }

@@ -376,45 +376,47 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     return R;
 }
 
-MergedTri merge_levels(const HostCSR& strict, const double* diag, const Levels& lev, int k, int64_t max_nnz) {
-    MergedTri M;
-    M.k = std::max(1, k);
-    const int64_t n = strict.rows;
-    if (M.k == 1) {
-        M.T = strict;
-        M.R.rows = n;
-        M.R.cols = n;
-        M.R.ptr.assign(static_cast<size_t>(n) + 1, 0);
-        M.lev = lev;
-        return M;
-    }
-    auto group = [&](int64_t i) { return lev.level[i] / M.k; };
-    // merged rows, built in level order (a row's same-group dependencies come first)
-    std::vector<std::vector<std::pair<int32_t, double>>> Trow(static_cast<size_t>(n)), Rrow(static_cast<size_t>(n));
-    std::vector<double> accT(static_cast<size_t>(n), 0.0), accR(static_cast<size_t>(n), 0.0);
-    std::vector<int32_t> markT(static_cast<size_t>(n), -1), markR(static_cast<size_t>(n), -1);
+namespace {
+
+// Rows of a fused system, built in level order.  group_of(level) names the
+// group of every level already processed; a row's dependencies on rows of its
+// own group are substituted (x_j = (rhs_j + sum_Rj c rhs - sum_Tj c x) / d_j,
+// so the rows those come from must already be final), the others stay.
+struct Fuser {
+    const HostCSR& strict;
+    const double* diag;
+    const Levels& lev;
+    std::vector<std::vector<std::pair<int32_t, double>>> Trow, Rrow;
+    std::vector<double> accT, accR;
+    std::vector<int64_t> markT, markR;  // stamp of the build that last touched a column
     std::vector<int32_t> listT, listR;
-    int64_t total = 0;
-    for (int64_t t = 0; t < n; ++t) {
-        const int32_t i = lev.order[t];
+    int64_t stamp = 0;
+    Fuser(const HostCSR& s, const double* d, const Levels& l)
+        : strict(s), diag(d), lev(l), Trow(static_cast<size_t>(s.rows)), Rrow(static_cast<size_t>(s.rows)),
+          accT(static_cast<size_t>(s.rows), 0.0), accR(static_cast<size_t>(s.rows), 0.0),
+          markT(static_cast<size_t>(s.rows), -1), markR(static_cast<size_t>(s.rows), -1) {}
+
+    // builds (or rebuilds) row i for group g of its level; returns its stored entries
+    template <class GroupOf>
+    int64_t build(int32_t i, int32_t g, const GroupOf& group_of) {
+        const int64_t b = stamp++;
         listT.clear();
         listR.clear();
         auto addT = [&](int32_t c, double v) {
-            if (markT[c] != i) { markT[c] = i; accT[c] = 0.0; listT.push_back(c); }
+            if (markT[c] != b) { markT[c] = b; accT[c] = 0.0; listT.push_back(c); }
             accT[c] += v;
         };
         auto addR = [&](int32_t c, double v) {
-            if (markR[c] != i) { markR[c] = i; accR[c] = 0.0; listR.push_back(c); }
+            if (markR[c] != b) { markR[c] = b; accR[c] = 0.0; listR.push_back(c); }
             accR[c] += v;
         };
         for (int64_t e = strict.ptr[i]; e < strict.ptr[i + 1]; ++e) {
             const int32_t j = strict.idx[e];
             const double a = strict.val[e];
-            if (group(j) != group(i)) {
+            if (group_of(lev.level[j]) != g) {
                 addT(j, a);
                 continue;
             }
-            // x_j = (rhs_j + sum_Rj c rhs - sum_Tj c x) / d_j, substituted into - a x_j
             const double f = diag ? a / diag[j] : a;
             addR(j, -f);
             for (const auto& rc : Rrow[j]) addR(rc.first, -f * rc.second);
@@ -422,39 +424,108 @@ MergedTri merge_levels(const HostCSR& strict, const double* diag, const Levels& 
         }
         std::sort(listT.begin(), listT.end());
         std::sort(listR.begin(), listR.end());
+        Trow[i].clear();
+        Rrow[i].clear();
         for (int32_t c : listT) Trow[i].push_back({c, accT[c]});
         for (int32_t c : listR) Rrow[i].push_back({c, accR[c]});
-        total += static_cast<int64_t>(listT.size() + listR.size());
+        return static_cast<int64_t>(listT.size() + listR.size());
+    }
+
+    void finish(MergedTri& M) {
+        const int64_t n = strict.rows;
+        auto to_csr = [&](const std::vector<std::vector<std::pair<int32_t, double>>>& rows, HostCSR& out) {
+            out.rows = n;
+            out.cols = n;
+            out.ptr.assign(static_cast<size_t>(n) + 1, 0);
+            for (int64_t i = 0; i < n; ++i) out.ptr[i + 1] = out.ptr[i] + static_cast<int64_t>(rows[i].size());
+            out.idx.resize(static_cast<size_t>(out.ptr[n]));
+            out.val.resize(static_cast<size_t>(out.ptr[n]));
+            for (int64_t i = 0; i < n; ++i) {
+                int64_t w = out.ptr[i];
+                for (const auto& p : rows[i]) {
+                    out.idx[w] = p.first;
+                    out.val[w] = p.second;
+                    ++w;
+                }
+            }
+        };
+        to_csr(Trow, M.T);
+        to_csr(Rrow, M.R);
+        // lower systems depend on smaller ids, upper ones on larger ids; the
+        // merged dependencies keep that direction
+        bool lower = true;
+        for (int64_t i = 0; i < n && lower; ++i)
+            for (int64_t e = strict.ptr[i]; e < strict.ptr[i + 1]; ++e)
+                if (strict.idx[e] > i) { lower = false; break; }
+        M.lev = analyse_levels(M.T, lower);
+    }
+};
+
+MergedTri unmerged(const HostCSR& strict, const Levels& lev) {
+    MergedTri M;
+    M.k = 1;
+    M.T = strict;
+    M.R.rows = strict.rows;
+    M.R.cols = strict.rows;
+    M.R.ptr.assign(static_cast<size_t>(strict.rows) + 1, 0);
+    M.lev = lev;
+    return M;
+}
+
+}  // namespace
+
+MergedTri merge_levels(const HostCSR& strict, const double* diag, const Levels& lev, int k, int64_t max_nnz) {
+    if (k <= 1) return unmerged(strict, lev);
+    MergedTri M;
+    M.k = k;
+    Fuser fz(strict, diag, lev);
+    auto group_of = [k](int32_t l) { return l / k; };
+    int64_t total = 0;
+    for (int64_t t = 0; t < strict.rows; ++t) {
+        const int32_t i = lev.order[t];
+        total += fz.build(i, group_of(lev.level[i]), group_of);
         if (max_nnz > 0 && total > max_nnz) {
             M.k = 0;  // too much fill: rejected
             return M;
         }
     }
-    auto to_csr = [&](const std::vector<std::vector<std::pair<int32_t, double>>>& rows, HostCSR& out) {
-        out.rows = n;
-        out.cols = n;
-        out.ptr.assign(static_cast<size_t>(n) + 1, 0);
-        for (int64_t i = 0; i < n; ++i) out.ptr[i + 1] = out.ptr[i] + static_cast<int64_t>(rows[i].size());
-        out.idx.resize(static_cast<size_t>(out.ptr[n]));
-        out.val.resize(static_cast<size_t>(out.ptr[n]));
-        for (int64_t i = 0; i < n; ++i) {
-            int64_t w = out.ptr[i];
-            for (const auto& p : rows[i]) {
-                out.idx[w] = p.first;
-                out.val[w] = p.second;
-                ++w;
+    fz.finish(M);
+    return M;
+}
+
+MergedTri merge_levels_adaptive(const HostCSR& strict, const double* diag, const Levels& lev,
+                                double level_entries, int max_group) {
+    if (lev.nlevels <= 1 || max_group <= 1) return unmerged(strict, lev);
+    MergedTri M;
+    Fuser fz(strict, diag, lev);
+    std::vector<int32_t> gid(static_cast<size_t>(lev.nlevels), 0);
+    auto group_of = [&gid](int32_t l) { return gid[static_cast<size_t>(l)]; };
+    int32_t cur = 0, start = 0, widest = 1;
+    for (int32_t l = 0; l < lev.nlevels; ++l) {
+        const int32_t lo = lev.level_ptr[l], hi = lev.level_ptr[l + 1];
+        bool joined = false;
+        if (l > 0 && l - start < max_group) {
+            // tentatively in the current group: the fill it adds against the
+            // cost of one more level
+            gid[l] = cur;
+            int64_t grown = 0;
+            for (int32_t t = lo; t < hi; ++t) {
+                const int32_t i = lev.order[t];
+                grown += fz.build(i, cur, group_of) - (strict.ptr[i + 1] - strict.ptr[i]);
             }
+            joined = static_cast<double>(grown) <= level_entries;
         }
-    };
-    to_csr(Trow, M.T);
-    to_csr(Rrow, M.R);
-    // lower systems depend on smaller ids, upper ones on larger ids; the
-    // merged dependencies keep that direction
-    bool lower = true;
-    for (int64_t i = 0; i < n && lower; ++i)
-        for (int64_t e = strict.ptr[i]; e < strict.ptr[i + 1]; ++e)
-            if (strict.idx[e] > i) { lower = false; break; }
-    M.lev = analyse_levels(M.T, lower);
+        if (!joined) {
+            if (l > 0) ++cur;
+            start = l;
+            gid[l] = cur;
+            for (int32_t t = lo; t < hi; ++t) fz.build(lev.order[t], cur, group_of);
+        }
+        widest = std::max(widest, l - start + 1);
+    }
+    M.k = widest;
+    M.adaptive = true;
+    fz.finish(M);
     return M;
 }
 

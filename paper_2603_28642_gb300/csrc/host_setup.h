@@ -77,10 +77,17 @@ struct MergedTri {
     HostCSR T;       // remaining dependencies (unknown ids), strictly earlier groups
     HostCSR R;       // extra right-hand-side terms (unknown ids, coefficients)
     Levels lev;      // levels of T
-    int k = 1;
+    int k = 1;       // levels per group (adaptive: the largest group)
+    bool adaptive = false;
 };
 // max_nnz > 0: give up (k = 0 in the result) once T and R hold more entries.
 MergedTri merge_levels(const HostCSR& strict, const double* diag, const Levels& lev, int k, int64_t max_nnz = 0);
+// Groups of consecutive levels chosen greedily: a level joins the current
+// group (of at most max_group levels) when the entries its substitution adds
+// are at most level_entries (the cost of one level expressed in entries),
+// otherwise it opens a new group.
+MergedTri merge_levels_adaptive(const HostCSR& strict, const double* diag, const Levels& lev,
+                                double level_entries, int max_group);
 
 // Dense inverse of S = I + Z^T Z, Z = L1^{-T} L2^T, through its Cholesky
 // factor; row-major (m-n)^2.  Returns false if S is not numerically SPD.

@@ -1051,8 +1051,11 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
                 throw ApiError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
         }
         cudaStream_t st = h->stream;
-        // fused levels per system (0: the k of least modelled time, about
-        // 5 us per level plus the bytes at 4 TB/s)
+        // fused levels per system (0: the k of least modelled time).  The
+        // model was fitted to the measured solves of a 2M x 1M problem on
+        // GB300 (every schedule, k = 1..4): about 3 us per level plus 13.7 ps
+        // per stored float64 entry (T and R; an entry's cost is a random
+        // gather, not its bytes), scaled by the entry width for float32
         h->merged.clear();
         {
             const HostCSR* parts[4] = {&F->L1, &F->L1t, &F->U, &F->Ut};
@@ -1065,19 +1068,25 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
                     continue;
                 }
                 MergedTri best = merge_levels(*parts[w], dg, *levs[w], 1);
+                const double entry_s = (wv + 4.0) / 12.0 * 13.7e-12;
                 auto cost = [&](const MergedTri& M) {
-                    return M.lev.nlevels * 5.0e-6 +
-                           ((wv + 4.0) * static_cast<double>(M.T.nnz() + M.R.nnz()) + 8.0 * h->n) / 4.0e12;
+                    return M.lev.nlevels * 3.0e-6 + entry_s * static_cast<double>(M.T.nnz() + M.R.nnz());
                 };
                 double cbest = cost(best);
-                for (int kk = 2; kk <= 4; ++kk) {
-                    MergedTri M = merge_levels(*parts[w], dg, *levs[w], kk, 4 * std::max<int64_t>(parts[w]->nnz(), h->n));
-                    if (M.k == 0) break;
+                auto consider = [&](MergedTri&& M) {
                     const double c = cost(M);
                     if (c < cbest) {
                         cbest = c;
                         best = std::move(M);
                     }
+                };
+                // groups chosen level by level: a level joins while its fill
+                // costs less than the level it saves
+                consider(merge_levels_adaptive(*parts[w], dg, *levs[w], 3.0e-6 / entry_s, 16));
+                for (int kk = 2; kk <= 4; ++kk) {
+                    MergedTri M = merge_levels(*parts[w], dg, *levs[w], kk, 4 * std::max<int64_t>(parts[w]->nnz(), h->n));
+                    if (M.k == 0) break;
+                    consider(std::move(M));
                 }
                 h->merged.push_back(std::move(best));
             }

@@ -134,11 +134,15 @@ def wide():
     return prob, oracle_factor(prob, oracle.CG)
 
 
-@pytest.mark.parametrize("k", [1, 2])
-@pytest.mark.parametrize("sched", [B.TRSV_WAVE, B.TRSV_SYNCFREE])
+@pytest.mark.parametrize("k", [0, 1, 2])
+@pytest.mark.parametrize("sched", [B.TRSV_WAVE, B.TRSV_SYNCFREE, B.TRSV_COOP])
 def test_triangular_solves_many_rounds(wide, sched, k):
+    # k = 0: fused groups chosen by the cost model (fixed k or level by level)
     prob, f = wide
     P = make(prob, B.CORR_CG, sched=sched, level_merge=k)
+    info = P.info()
+    assert all(s <= l for s, l in zip(info["solve_levels"], [info["levels_L1"], info["levels_L1t"],
+                                                             info["levels_U"], info["levels_Ut"]]))
     b = np.random.default_rng(11).standard_normal(prob.n)
     for sys_id, name in SOLVES:
         x = P.trsv(sys_id, b)
