@@ -424,6 +424,7 @@ def measure_served(nmat=64, n_hi=200000, rates=(100, 1000, 5000), requests=500):
         out["rates"].append({"rate_per_s": rate, "requests": requests, "p50_ms": st["p50_ms"],
                              "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                              "solves_per_s": st["solves_per_s"], "ticks": st["ticks"],
+                             "tick_ms": st["tick_ms"], "tick_device_ms": st["tick_device_ms"],
                              "peak_state_bytes": st["peak_bytes"]})
         srv.close()
     return out

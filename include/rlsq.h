@@ -162,6 +162,8 @@ typedef struct {
     double solves_per_s;             /* completed / (last completion - first submit) */
     int64_t ticks;                   /* batched iterations run */
     int64_t peak_bytes;              /* largest admitted state footprint */
+    double tick_ms;                  /* mean wall time of a tick (admission, launch, results) */
+    double tick_device_ms;           /* mean part of it from graph launch to the device finishing */
 } rlsq_server_stats;
 
 /* ---- defaults -------------------------------------------------------------- */

@@ -86,7 +86,7 @@ class ServerStats(C.Structure):
         ("submitted", C.c_int64), ("completed", C.c_int64), ("queued", C.c_int64),
         ("active", C.c_int64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
         ("mean_ms", C.c_double), ("solves_per_s", C.c_double), ("ticks", C.c_int64),
-        ("peak_bytes", C.c_int64),
+        ("peak_bytes", C.c_int64), ("tick_ms", C.c_double), ("tick_device_ms", C.c_double),
     ]
 
     def as_dict(self):

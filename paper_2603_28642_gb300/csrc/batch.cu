@@ -9,9 +9,11 @@
 // slot's own reduction scratch, so a problem's iterates do not depend on the
 // other slots: a problem gives the same bits alone and in any mix.
 //
-// The triangular solves are level-scheduled across all slots (one launch per
-// level).  One LSMR iteration for the whole table is captured in one CUDA
-// graph and replayed.
+// The triangular solves run as one persistent launch per solve for all slots
+// (grid barrier per level), or, for more slots than a block has threads, one
+// launch per level.  One LSMR iteration for the whole table is captured in one
+// CUDA graph and replayed; a server tick that admits requests runs one graph
+// in which the new slots start while the others iterate.
 //
 // rlsq_batch_solve points the slots at the problems' own buffers;
 // the server (rlsq_server_*) points them at slot-owned buffers over shared,
@@ -63,6 +65,16 @@ struct BSlot {
     unsigned* counter;
 };
 
+// Blocks a slot may use in one launch.  A constant, so a problem's launch
+// shape (and its bits) never depends on the mix; small enough that a launch
+// over many slots stays a few waves of blocks (every slot's share of the grid
+// is launched even when that slot has less work).
+constexpr int kSlotBlocks = 64;
+
+// phase selector of the preconditioner application shared by starting
+// (phase 1) and iterating (phase 2) slots in one server tick
+constexpr int kPhaseActive = 3;
+
 __device__ __forceinline__ int own_blocks(long long rows, int G, int cap) {
     const long long g = (rows * G + kBlock - 1) / kBlock;
     return (int)max(1LL, min(g, (long long)cap));
@@ -84,7 +96,8 @@ __device__ __forceinline__ bool cond_ok(const BSlot<T>& D, int cond) {
 template <typename T>
 __device__ __forceinline__ const BSlot<T>* gate(const BSlot<T>* slots, const int32_t* phase, int want,
                                                 int cond) {
-    if (phase[blockIdx.y] != want) return nullptr;
+    const int ph = phase[blockIdx.y];
+    if (want == kPhaseActive ? (ph != 1 && ph != 2) : ph != want) return nullptr;
     const BSlot<T>* D = &slots[blockIdx.y];
     if (D->S->done || !cond_ok(*D, cond)) return nullptr;
     return D;
@@ -200,6 +213,57 @@ kb_spmvt(const BSlot<T>* slots, const int32_t* phase, int cap) {
     }
 }
 
+// slot s if it takes part (phase, not done, condition), else nullptr
+template <typename T>
+__device__ __forceinline__ const BSlot<T>* gate_s(const BSlot<T>* slots, const int32_t* phase, int s, int want,
+                                                  int cond) {
+    const int ph = phase[s];
+    if (want == kPhaseActive ? (ph != 1 && ph != 2) : ph != want) return nullptr;
+    const BSlot<T>* D = &slots[s];
+    if (D->S->done || !cond_ok(*D, cond)) return nullptr;
+    return D;
+}
+
+// position t of triangular system `which` of one slot; the right-hand side is
+// selected as in the single-problem apply.  x is read through L2: in the
+// persistent solve other SMs wrote it during the same launch.
+template <typename T, int K>
+__device__ __forceinline__ void kb_solve_row(const BSlot<T>& D, int which, int t, int ia, int ib, int io) {
+    // local copies: stores to x could otherwise alias the slot table, and
+    // every structure pointer would be reloaded inside the loops
+    const Tri<T> tri = D.tri[which];
+    Rhs<T> rhs;
+    if (K == RHS_SCALED) {
+        rhs.a = D.d;
+        rhs.b = nullptr;
+        rhs.s = D.s;
+    } else {
+        rhs.a = D.vn[ia];
+        rhs.b = (K == RHS_SUB) ? D.vn[ib] : nullptr;
+        rhs.s = nullptr;
+    }
+    T* const x = D.vn[io];
+    const int row = tri.order[t];
+    const T rv = rhs_full<T, K>(tri, rhs, t, row);
+    const T dg = tri.idiag ? tri.idiag[t] : (T)1;
+    T sum = (T)0;
+    const int e1 = tri.ptr[t + 1];
+    int e = tri.ptr[t];
+    for (; e + 3 < e1; e += 4) {
+        const int j0 = tri.idx[e], j1 = tri.idx[e + 1], j2 = tri.idx[e + 2], j3 = tri.idx[e + 3];
+        const T a0 = tri.val[e], a1 = tri.val[e + 1], a2 = tri.val[e + 2], a3 = tri.val[e + 3];
+        const T v0 = __ldcg(&x[j0]), v1 = __ldcg(&x[j1]), v2 = __ldcg(&x[j2]), v3 = __ldcg(&x[j3]);
+        sum += a0 * v0;
+        sum += a1 * v1;
+        sum += a2 * v2;
+        sum += a3 * v3;
+    }
+    for (; e < e1; ++e) sum += tri.val[e] * __ldcg(&x[tri.idx[e]]);
+    T v = rv - sum;
+    if (tri.idiag) v = v * dg;
+    x[row] = v;
+}
+
 // one level of a triangular solve for every slot (positions lp[level]..lp[level+1])
 template <typename T, int K>
 __global__ void __launch_bounds__(kBlock)
@@ -207,39 +271,70 @@ kb_trsv_level(const BSlot<T>* slots, const int32_t* phase, int want, int cond, i
               int ib, int io) {
     const BSlot<T>* D = gate(slots, phase, want, cond);
     if (!D || level >= D->nlev[which]) return;
-    const Tri<T>& tri = D->tri[which];
     const int lo = D->lp[which][level], hi = D->lp[which][level + 1];
-    Rhs<T> rhs;
-    if (K == RHS_SCALED) {
-        rhs.a = D->d;
-        rhs.b = nullptr;
-        rhs.s = D->s;
-    } else {
-        rhs.a = D->vn[ia];
-        rhs.b = (K == RHS_SUB) ? D->vn[ib] : nullptr;
-        rhs.s = nullptr;
-    }
-    T* x = D->vn[io];
-    for (int t = lo + blockIdx.x * kBlock + threadIdx.x; t < hi; t += gridDim.x * kBlock) {
-        const int row = tri.order[t];
-        const T rv = rhs_full<T, K>(tri, rhs, t, row);
-        const T dg = tri.idiag ? tri.idiag[t] : (T)1;
-        T sum = (T)0;
-        const int e1 = tri.ptr[t + 1];
-        int e = tri.ptr[t];
-        for (; e + 3 < e1; e += 4) {
-            const int j0 = tri.idx[e], j1 = tri.idx[e + 1], j2 = tri.idx[e + 2], j3 = tri.idx[e + 3];
-            const T a0 = tri.val[e], a1 = tri.val[e + 1], a2 = tri.val[e + 2], a3 = tri.val[e + 3];
-            const T v0 = x[j0], v1 = x[j1], v2 = x[j2], v3 = x[j3];
-            sum += a0 * v0;
-            sum += a1 * v1;
-            sum += a2 * v2;
-            sum += a3 * v3;
+    for (int t = lo + blockIdx.x * kBlock + threadIdx.x; t < hi; t += gridDim.x * kBlock)
+        kb_solve_row<T, K>(*D, which, t, ia, ib, io);
+}
+
+// One persistent launch solves system `which` for every slot: the co-resident
+// grid walks the levels 0..nlev-1 with a grid barrier between them; inside a
+// level the rows of all taking-part slots form one index range (a prefix of
+// the slots' level widths, built in shared memory by every block) that the
+// threads stride over.  A row is solved exactly as in kb_trsv_level, so the
+// bits do not depend on the schedule or the mix.  At most kCoopBlock slots.
+template <typename T, int K>
+__global__ void __launch_bounds__(kCoopBlock, 1)
+kb_trsv_coop(const BSlot<T>* slots, const int32_t* phase, int nslots, int want, int cond, int which, int nlev,
+             int ia, int ib, int io, unsigned* bar, int* err) {
+    __shared__ int pre[kCoopBlock + 1];
+    __shared__ int wsum[kCoopBlock / 32];
+    const int nthreads = gridDim.x * kCoopBlock;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = ((warp * gridDim.x + blockIdx.x) << 5) + lane;
+    for (int l = 0; l < nlev; ++l) {
+        int w = 0;
+        if ((int)threadIdx.x < nslots) {
+            const BSlot<T>* D = gate_s(slots, phase, threadIdx.x, want, cond);
+            if (D && l < D->nlev[which]) w = D->lp[which][l + 1] - D->lp[which][l];
         }
-        for (; e < e1; ++e) sum += tri.val[e] * x[tri.idx[e]];
-        T v = rv - sum;
-        if (tri.idiag) v = v * dg;
-        x[row] = v;
+        // inclusive scan of the widths over the block (slot = thread)
+        int v = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += y;
+        }
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            int z = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, z, off);
+                if (lane >= off) z += y;
+            }
+            wsum[lane] = z;
+        }
+        __syncthreads();
+        pre[threadIdx.x + 1] = v + (warp > 0 ? wsum[warp - 1] : 0);
+        if (threadIdx.x == 0) pre[0] = 0;
+        __syncthreads();
+        const int total = pre[nslots];
+        for (int idx = tid; idx < total; idx += nthreads) {
+            // the last slot s with pre[s] <= idx (empty slots have pre[s] == pre[s + 1])
+            int lo = 0, hi = nslots;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[mid] <= idx) lo = mid;
+                else hi = mid;
+            }
+            const BSlot<T>& D = slots[lo];
+            kb_solve_row<T, K>(D, which, D.lp[which][l] + (idx - pre[lo]), ia, ib, io);
+        }
+        if (l + 1 < nlev) {
+            grid_arrive(bar);
+            grid_wait(bar, (unsigned)(l + 1) * gridDim.x, err);
+        }
     }
 }
 
@@ -519,31 +614,52 @@ struct Engine {
     DevArray<BSlot<T>> d_slots;
     std::vector<int32_t> h_phase;
     DevArray<int32_t> d_phase, d_needs;
-    int32_t* pinned_needs = nullptr;
+    int32_t* pinned_needs = nullptr;  // nslots flags, then the device error word
+    DevArray<unsigned> d_bars;        // grid-barrier counters of the persistent solves of one apply
+    DevArray<int> d_err;              // set when a bounded device wait gave up
+    int bar_next = 0;
+    int coop_grid = 0;                // co-resident blocks of kb_trsv_coop (0: level launches only)
     // maxima over everything the graphs must cover
     int maxlev[4] = {0, 0, 0, 0};
     int maxcg = 0;
     int64_t max_m = 0, max_n = 0, max_m2 = 0, max_levw = 0;
     bool any_corr = false, any_none = false, any_cg = false, any_e = false, any_dense = false;
-    cudaGraphExec_t g_start = nullptr, g_iter = nullptr;
+    cudaGraphExec_t g_start = nullptr, g_iter = nullptr, g_tick = nullptr;
     int iter_reps = 0;
 
     ~Engine() {
         if (g_start) cudaGraphExecDestroy(g_start);
         if (g_iter) cudaGraphExecDestroy(g_iter);
+        if (g_tick) cudaGraphExecDestroy(g_tick);
         if (pinned_needs) cudaFreeHost(pinned_needs);
     }
 
-    void init(int slots, int max_blocks, cudaStream_t stream) {
+    void init(int slots, int max_blocks, cudaStream_t stream, int num_sms) {
         nslots = slots;
         cap = max_blocks;
         st = stream;
+        d_bars.alloc(kMaxSlots);
+        d_err.alloc(1);
+        RLSQ_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int), st));
+        coop_grid = 0;
+        if (slots <= kCoopBlock) {
+            int occ = 1 << 30;
+            auto prep = [&](auto kern) {
+                int o = 0;
+                RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kCoopBlock, 0));
+                occ = std::min(occ, o);
+            };
+            prep(kb_trsv_coop<T, RHS_VEC>);
+            prep(kb_trsv_coop<T, RHS_SCALED>);
+            prep(kb_trsv_coop<T, RHS_SUB>);
+            coop_grid = occ * num_sms;
+        }
         h_slots.assign(static_cast<size_t>(slots), BSlot<T>{});
         h_phase.assign(static_cast<size_t>(slots), 0);
         d_slots.alloc(slots);
         d_phase.alloc(slots);
         d_needs.alloc(slots);
-        RLSQ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&pinned_needs), sizeof(int32_t) * slots));
+        RLSQ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&pinned_needs), sizeof(int32_t) * (slots + 1)));
     }
 
     // cover a matrix (its levels, sizes, correction) in the captured graphs
@@ -575,7 +691,8 @@ struct Engine {
     void drop_graphs() {
         if (g_start) cudaGraphExecDestroy(g_start);
         if (g_iter) cudaGraphExecDestroy(g_iter);
-        g_start = g_iter = nullptr;
+        if (g_tick) cudaGraphExecDestroy(g_tick);
+        g_start = g_iter = g_tick = nullptr;
     }
 
     // descriptor of slot s: matrix from P, vectors from P (own == nullptr) or own
@@ -623,7 +740,34 @@ struct Engine {
     }
 
     void trsv(int want, int cond, int which, int kind, int ia, int ib, int io) {
-        const dim3 grid(static_cast<unsigned>(gx(max_levw, 1)), static_cast<unsigned>(nslots));
+        if (coop_grid > 0 && maxlev[which] > 0) {
+            // one persistent launch for every level of every slot
+            if (bar_next >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
+            unsigned* bar = d_bars.p + bar_next++;
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(static_cast<unsigned>(coop_grid));
+            cfg.blockDim = dim3(kCoopBlock);
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const BSlot<T>* sl = d_slots.p;
+            const int32_t* ph = d_phase.p;
+            const int nl = maxlev[which];
+            if (kind == RHS_SCALED)
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_coop<T, RHS_SCALED>, sl, ph, nslots, want, cond, which, nl,
+                                             ia, ib, io, bar, d_err.p));
+            else if (kind == RHS_SUB)
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_coop<T, RHS_SUB>, sl, ph, nslots, want, cond, which, nl, ia,
+                                             ib, io, bar, d_err.p));
+            else
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_coop<T, RHS_VEC>, sl, ph, nslots, want, cond, which, nl, ia,
+                                             ib, io, bar, d_err.p));
+            return;
+        }
+        const dim3 grid(static_cast<unsigned>(std::min(gx(max_levw, 1), 64)), static_cast<unsigned>(nslots));
         for (int l = 0; l < maxlev[which]; ++l) {
             if (kind == RHS_SCALED)
                 kb_trsv_level<T, RHS_SCALED><<<grid, kBlock, 0, st>>>(d_slots.p, d_phase.p, want, cond, which, l, ia, ib, io);
@@ -637,6 +781,8 @@ struct Engine {
     // t = M^{-1} s for every slot in phase `want` (same sequence as the single path)
     void apply(int want) {
         const unsigned ns = static_cast<unsigned>(nslots);
+        RLSQ_CUDA(cudaMemsetAsync(d_bars.p, 0, sizeof(unsigned) * kMaxSlots, st));
+        bar_next = 0;
         trsv(want, C_ALL, 3, RHS_SCALED, 0, 0, 0);  // U^{-T} D s -> vn0
         trsv(want, C_ALL, 1, RHS_VEC, 0, 0, 1);     // L1^{-T} -> vn1
         if (any_corr) {
@@ -691,10 +837,28 @@ struct Engine {
         kb_update<T, false><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
     }
 
-    cudaGraphExec_t capture(bool start, int reps) {
+    // one server tick: newly admitted slots (phase 1) start while the others
+    // (phase 2) iterate, sharing one preconditioner application
+    void enqueue_tick() {
+        const unsigned ns = static_cast<unsigned>(nslots);
+        kb_start<T><<<dim3(gx(max_m, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmv<T><<<dim3(gx(max_m, kBG_A), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmvt<T, true><<<dim3(gx(max_n, kBG_At), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmvt<T, false><<<dim3(gx(max_n, kBG_At), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        apply(kPhaseActive);
+        kb_finish<T, true><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_finish<T, false><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_update<T, true><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_update<T, false><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_begin<<<(nslots + kBlock - 1) / kBlock, kBlock, 0, st>>>(nslots, d_phase.p);
+    }
+
+    // start (0), reps iterations (1) or one tick (2)
+    cudaGraphExec_t capture(int kind, int reps) {
         RLSQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         try {
-            if (start) enqueue_start();
+            if (kind == 0) enqueue_start();
+            else if (kind == 2) enqueue_tick();
             else
                 for (int i = 0; i < reps; ++i) enqueue_iteration();
             kb_collect<T><<<(nslots + kBlock - 1) / kBlock, kBlock, 0, st>>>(d_slots.p, d_phase.p, nslots, d_needs.p);
@@ -714,13 +878,17 @@ struct Engine {
     }
 
     void launch_start() {
-        if (!g_start) g_start = capture(true, 0);
+        if (!g_start) g_start = capture(0, 0);
         RLSQ_CUDA(cudaGraphLaunch(g_start, st));
+    }
+    void launch_tick() {
+        if (!g_tick) g_tick = capture(2, 1);
+        RLSQ_CUDA(cudaGraphLaunch(g_tick, st));
     }
     void launch_iterations(int reps) {
         if (!g_iter || iter_reps != reps) {
             if (g_iter) cudaGraphExecDestroy(g_iter);
-            g_iter = capture(false, reps);
+            g_iter = capture(1, reps);
             iter_reps = reps;
         }
         RLSQ_CUDA(cudaGraphLaunch(g_iter, st));
@@ -728,6 +896,7 @@ struct Engine {
     // copies the per-slot "still iterating" flags to the host (after sync)
     void read_needs() {
         RLSQ_CUDA(cudaMemcpyAsync(pinned_needs, d_needs.p, sizeof(int32_t) * nslots, cudaMemcpyDeviceToHost, st));
+        RLSQ_CUDA(cudaMemcpyAsync(pinned_needs + nslots, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         RLSQ_CUDA(cudaStreamSynchronize(st));
     }
 };
@@ -769,7 +938,7 @@ int batch_solve_impl(rlsq_problem const* hs, const double* const* bs, double* co
     // finish whatever the problems' own streams still hold
     for (int i = 0; i < count; ++i) RLSQ_CUDA(cudaStreamSynchronize(hs[i]->stream));
     Engine<T> E;
-    E.init(count, std::max(1, P0->num_sms * 32), st);
+    E.init(count, kSlotBlocks, st, P0->num_sms);
     for (int i = 0; i < count; ++i) {
         rlsq_problem_s* P = hs[i];
         E.cover(P);
@@ -788,6 +957,8 @@ int batch_solve_impl(rlsq_problem const* hs, const double* const* bs, double* co
     for (int64_t l = 0;; ++l) {
         E.launch_iterations(reps);
         E.read_needs();
+        if (E.pinned_needs[count] != 0)
+            throw ApiError(RLSQ_ERR_DEVICE_TIMEOUT, "a bounded wait of the batched triangular solve gave up");
         bool any = false;
         for (int i = 0; i < count; ++i) any |= E.pinned_needs[i] != 0;
         if (!any) break;
@@ -797,9 +968,7 @@ int batch_solve_impl(rlsq_problem const* hs, const double* const* bs, double* co
     int first_bad = RLSQ_OK;
     for (int i = 0; i < count; ++i) {
         rlsq_problem_s* P = hs[i];
-        RLSQ_CUDA(cudaMemcpy2DAsync(xs[i], sizeof(double), reinterpret_cast<const double*>(P->tx.p) + 1, sizeof(double2),
-                                    sizeof(double), static_cast<size_t>(P->n),
-                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        copy_half(xs[i], P->tx.p, P->n, 1, dev, P->s.p, st);
         LsmrState h;
         RLSQ_CUDA(cudaMemcpyAsync(&h, P->S.p, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
         RLSQ_CUDA(cudaStreamSynchronize(st));
@@ -846,6 +1015,7 @@ struct rlsq_server_s {
     std::unordered_map<int64_t, Result> results;
     int64_t next_ticket = 1;
     int64_t submitted = 0, completed = 0, ticks = 0, peak_bytes = 0, active = 0;
+    double tick_s = 0.0, tick_device_s = 0.0;  // summed over ticks
     std::vector<double> latencies_ms;
     std::chrono::steady_clock::time_point first_submit, last_done;
     bool any_submit = false;
@@ -902,7 +1072,7 @@ void rlsq_server_s::run_loop(std::unique_ptr<Engine<T>>& E, std::vector<std::uni
                 } else {
                     if (!E) {
                         E.reset(new Engine<T>());
-                        E->init(nslots, std::max(1, num_sms * 32), st);
+                        E->init(nslots, kSlotBlocks, st, num_sms);
                         bufs.resize(nslots);
                         slots.assign(nslots, SlotInfo{});
                     }
@@ -915,7 +1085,7 @@ void rlsq_server_s::run_loop(std::unique_ptr<Engine<T>>& E, std::vector<std::uni
                     }
                     for (auto& b : bufs) {
                         if (!b) b.reset(new SlotBuffers<T>());
-                        b->ensure(mm, mn, mm2, std::max(1, num_sms * 32));
+                        b->ensure(mm, mn, mm2, kSlotBlocks);
                     }
                     dirty = false;
                 }
@@ -943,6 +1113,7 @@ void rlsq_server_s::run_loop(std::unique_ptr<Engine<T>>& E, std::vector<std::uni
             }
         }
         if (!E) continue;
+        const auto tick0 = std::chrono::steady_clock::now();
         if (!admitted.empty()) {
             for (int s : admitted) {
                 rlsq_problem_s* P = matrices[slots[s].req.matrix];
@@ -955,31 +1126,37 @@ void rlsq_server_s::run_loop(std::unique_ptr<Engine<T>>& E, std::vector<std::uni
                 RLSQ_CUDA(cudaStreamSynchronize(st));
             }
             E->push_table();
-            E->launch_start();
-            for (int s : admitted) E->h_phase[s] = 2;
         }
         bool running = false;
         for (int s = 0; s < nslots; ++s) running |= slots[s].busy;
         if (!running) continue;
-        E->launch_iterations(1);
+        const auto dev0 = std::chrono::steady_clock::now();
+        if (!admitted.empty()) {
+            E->launch_tick();  // the new slots start, the others iterate
+            for (int s : admitted) E->h_phase[s] = 2;
+        } else {
+            E->launch_iterations(1);
+        }
         E->read_needs();
+        const auto dev1 = std::chrono::steady_clock::now();
         ++ticks;
+        // a bounded device wait gave up: every running request ends with that error
+        const bool dev_err = E->pinned_needs[nslots] != 0;
+        if (dev_err) RLSQ_CUDA(cudaMemsetAsync(E->d_err.p, 0, sizeof(int), st));
         // finished slots: results out, slot freed
         for (int s = 0; s < nslots; ++s) {
-            if (!slots[s].busy || E->pinned_needs[s]) continue;
+            if (!slots[s].busy || (E->pinned_needs[s] && !dev_err)) continue;
             rlsq_problem_s* P = matrices[slots[s].req.matrix];
             Result res;
             res.x.resize(static_cast<size_t>(P->n));
-            RLSQ_CUDA(cudaMemcpy2DAsync(res.x.data(), sizeof(double), reinterpret_cast<const double*>(bufs[s]->tx.p) + 1,
-                                        sizeof(double2), sizeof(double), static_cast<size_t>(P->n),
-                                        cudaMemcpyDeviceToHost, st));
+            copy_half(res.x.data(), bufs[s]->tx.p, P->n, 1, false, bufs[s]->s.p, st);
             LsmrState h;
             RLSQ_CUDA(cudaMemcpyAsync(&h, bufs[s]->S.p, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
             RLSQ_CUDA(cudaStreamSynchronize(st));
             const auto now = std::chrono::steady_clock::now();
             const double lat = std::chrono::duration<double, std::milli>(now - slots[s].req.submitted).count();
             fill_info(P, h, lat / 1000.0, &res.info);
-            res.status = res.info.status;
+            res.status = dev_err ? RLSQ_ERR_DEVICE_TIMEOUT : res.info.status;
             E->h_phase[s] = 0;
             {
                 std::lock_guard<std::mutex> lock(mu);
@@ -995,6 +1172,12 @@ void rlsq_server_s::run_loop(std::unique_ptr<Engine<T>>& E, std::vector<std::uni
         }
         // the phase table changed for freed slots
         RLSQ_CUDA(cudaMemcpyAsync(E->d_phase.p, E->h_phase.data(), sizeof(int32_t) * nslots, cudaMemcpyHostToDevice, st));
+        {
+            const auto tick1 = std::chrono::steady_clock::now();
+            std::lock_guard<std::mutex> lock(mu);
+            tick_s += std::chrono::duration<double>(tick1 - tick0).count();
+            tick_device_s += std::chrono::duration<double>(dev1 - dev0).count();
+        }
     }
 }
 
@@ -1136,6 +1319,8 @@ int rlsq_server_get_stats(rlsq_server s, rlsq_server_stats* st) {
         st->active = s->active;
         st->ticks = s->ticks;
         st->peak_bytes = s->peak_bytes;
+        st->tick_ms = s->ticks ? 1000.0 * s->tick_s / s->ticks : 0.0;
+        st->tick_device_ms = s->ticks ? 1000.0 * s->tick_device_s / s->ticks : 0.0;
         if (!s->latencies_ms.empty()) {
             std::vector<double> l = s->latencies_ms;
             std::sort(l.begin(), l.end());

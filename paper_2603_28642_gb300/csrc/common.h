@@ -153,6 +153,11 @@ struct Recorder {
     }
 };
 
+// dst[i] = pairs[i].x (half 0) or .y (half 1), i < n, on stream st: a kernel
+// writes either dst itself (device destination) or the device staging buffer,
+// which one contiguous copy then brings to the host
+void copy_half(double* dst, const double2* pairs, int64_t n, int half, bool dev, double* staging, cudaStream_t st);
+
 }  // namespace rlsq
 
 struct rlsq_problem_s {

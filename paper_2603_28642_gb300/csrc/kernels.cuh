@@ -418,6 +418,11 @@ static __global__ void k_put_dense(int md, int ms, const double2* __restrict__ d
     const int r = blockIdx.x * kBlock + threadIdx.x;
     if (r < md) y[ms + r] = d[r].x * (P ? P->inv_lambda : 1.0);
 }
+// out[i] = in[i].x (H = 0) or in[i].y (H = 1): one half of an interleaved pair
+template <int H>
+static __global__ void k_half(int n, const double2* __restrict__ in, double* __restrict__ out) {
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) out[i] = H ? in[i].y : in[i].x;
+}
 // out[i] = in[perm[i]]
 static __global__ void k_gather(int m, const int32_t* __restrict__ perm, const double* __restrict__ in,
                          double* __restrict__ out) {
@@ -951,7 +956,17 @@ k_trsv_level(Tri<T> tri, Rhs<T> rhs, T* x, int lo, int hi, const LsmrState* S) {
         const T dg = tri.idiag ? tri.idiag[tpos] : (T)1;
         T sum = (T)0;
         const int e1 = tri.ptr[tpos + 1];
-        for (int e = tri.ptr[tpos] + lane; e < e1; e += G) sum += tri.val[e] * x[tri.idx[e]];
+        int e = tri.ptr[tpos] + lane;
+        for (; e + 3 * G < e1; e += 4 * G) {
+            const int j0 = tri.idx[e], j1 = tri.idx[e + G], j2 = tri.idx[e + 2 * G], j3 = tri.idx[e + 3 * G];
+            const T a0 = tri.val[e], a1 = tri.val[e + G], a2 = tri.val[e + 2 * G], a3 = tri.val[e + 3 * G];
+            const T v0 = x[j0], v1 = x[j1], v2 = x[j2], v3 = x[j3];
+            sum += a0 * v0;
+            sum += a1 * v1;
+            sum += a2 * v2;
+            sum += a3 * v3;
+        }
+        for (; e < e1; e += G) sum += tri.val[e] * x[tri.idx[e]];
         if (G > 1) sum = group_sum<G>(sum, mask);
         if (lane == 0) {
             T v = rv - sum;

@@ -121,6 +121,17 @@ void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const st
     RLSQ_CUDA(cudaStreamSynchronize(s));
 }
 
+void copy_half(double* dst, const double2* pairs, int64_t n, int half, bool dev, double* staging,
+               cudaStream_t st) {
+    if (n <= 0) return;
+    double* out = dev ? dst : staging;
+    const int grid = static_cast<int>(std::min<int64_t>((n + kBlock - 1) / kBlock, 4096));
+    if (half) k_half<1><<<grid, kBlock, 0, st>>>(static_cast<int>(n), pairs, out);
+    else k_half<0><<<grid, kBlock, 0, st>>>(static_cast<int>(n), pairs, out);
+    RLSQ_CUDA(cudaGetLastError());
+    if (!dev) RLSQ_CUDA(cudaMemcpyAsync(dst, staging, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+}
+
 template struct DevCsr<double>;
 template struct DevCsr<float>;
 template struct DevFactor<double>;
@@ -237,8 +248,24 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
         if (P->rec && !P->rec->entries.empty()) P->rec->entries.back().launches = static_cast<int>(lp.size()) - 1;
     } else if (P->map.sched[which] == RLSQ_TRSV_COOP) {
         if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
-        const int nlev = static_cast<int>(F.level_ptr[which].size()) - 1;
-        with_rhs(rk, [&](auto k) {
+        // leading levels wider than the persistent grid go to full-occupancy
+        // level launches (each row of such a level would otherwise wait for
+        // the one before it on the same thread); the persistent kernel takes
+        // over at the first narrower level
+        const auto& lp = F.level_ptr[which];
+        const int nall = static_cast<int>(lp.size()) - 1;
+        const int64_t resident = static_cast<int64_t>(P->coop_blocks) * kCoopBlock;
+        int lead = 0;
+        while (lead < nall && lp[lead + 1] - lp[lead] > resident) ++lead;
+        for (int l = 0; l < lead; ++l) {
+            const int grid = grid_rows(P, lp[l + 1] - lp[l], 1);
+            with_rhs(rk, [&](auto k) {
+                k_trsv_level<T, 1, decltype(k)::value><<<grid, kBlock, 0, st>>>(tri, rhs, x, lp[l], lp[l + 1], S);
+            });
+        }
+        const int nlev = nall - lead;
+        if (P->rec && !P->rec->entries.empty()) P->rec->entries.back().launches = lead + (nlev > 0 ? 1 : 0);
+        if (nlev > 0) with_rhs(rk, [&](auto k) {
             const int kp = F.ell_kp[which] >= 8 ? 8 : 4;
             auto kern = kp == 8 ? k_trsv_coop<T, decltype(k)::value, 8> : k_trsv_coop<T, decltype(k)::value, 4>;
             cudaLaunchConfig_t cfg{};
@@ -251,7 +278,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, F.level_ptr_d[which].p, nlev,
+            RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, F.level_ptr_d[which].p + lead, nlev,
                                          P->barriers.p + slot, static_cast<const LsmrState*>(S), error_word(S)));
         });
     } else if (P->map.sched[which] == RLSQ_TRSV_WAVE) {
@@ -641,10 +668,8 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
     LsmrState hs;
     RLSQ_CUDA(cudaMemcpy(&hs, S, sizeof(LsmrState), cudaMemcpyDeviceToHost));
     if (!hs.done) throw ApiError(RLSQ_ERR_CUDA, "solver did not reach a stopping point");
-    // x_j lives at tx[j].y
-    RLSQ_CUDA(cudaMemcpy2DAsync(x, sizeof(double), reinterpret_cast<const double*>(P->tx.p) + 1,
-                                sizeof(double2), sizeof(double), static_cast<size_t>(P->n),
-                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    // x_j lives at tx[j].y; s is free once the solve has stopped
+    copy_half(x, P->tx.p, P->n, 1, dev, P->s.p, st);
     RLSQ_CUDA(cudaStreamSynchronize(st));
     if (dev) {
         RLSQ_CUDA(cudaEventRecord(P->ev[0], st));
@@ -1149,9 +1174,7 @@ int rlsq_apply(rlsq_problem h, const double* s, double* t, int32_t ptr_mode, voi
         enqueue_apply_any<true>(h, h->s.p, S, st, false);
         LsmrState hs;
         RLSQ_CUDA(cudaMemcpyAsync(h->pinned_state, S, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
-        RLSQ_CUDA(cudaMemcpy2DAsync(t, sizeof(double), reinterpret_cast<const double*>(h->tx.p),
-                                    sizeof(double2), sizeof(double), static_cast<size_t>(h->n),
-                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        copy_half(t, h->tx.p, h->n, 0, dev, h->s.p, st);  // t_j lives at tx[j].x
         RLSQ_CUDA(cudaStreamSynchronize(st));
         hs = *h->pinned_state;
         if (dev) {

@@ -134,10 +134,12 @@ def wide():
     return prob, oracle_factor(prob, oracle.CG)
 
 
-@pytest.mark.parametrize("k", [0, 1, 2])
+@pytest.mark.parametrize("k", [0, 1, 2, 4])
 @pytest.mark.parametrize("sched", [B.TRSV_WAVE, B.TRSV_SYNCFREE, B.TRSV_COOP])
 def test_triangular_solves_many_rounds(wide, sched, k):
-    # k = 0: fused groups chosen by the cost model (fixed k or level by level)
+    # k = 0: fused groups chosen by the cost model (fixed k or level by level);
+    # k = 4: the first groups are wider than the persistent grid, which then
+    # starts with level launches
     prob, f = wide
     P = make(prob, B.CORR_CG, sched=sched, level_merge=k)
     info = P.info()
