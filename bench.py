@@ -55,6 +55,14 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes (read + write) of one iteration's launches of a kernel class, from
+# the ncu capture summarised in profiles/trsv_L1_syncfree_cfg1_traffic.md (same
+# kernels and workload): keyed by (class, schedule the class ran with).  The
+# bench reports it only when its dominant class ran that way.
+MEASURED_TRAFFIC = {("trsv_L1", 2): 4 * 80.09e6}  # 4 L1 solves per iteration, sync-free schedule
+CLASS_SYSTEM = {"trsv_L1": 0, "trsv_L1t": 1, "trsv_U": 2, "trsv_Ut": 3}
+
+
 # ---------------------------------------------------------------------------
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -252,8 +260,11 @@ def run_ours(args):
     dom = max(cls, key=lambda k: cls[k]["ms"])
     d = cls[dom]
     achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+    sched = finfo["trsv_schedule"][CLASS_SYSTEM[dom]] if dom in CLASS_SYSTEM else None
+    traffic = MEASURED_TRAFFIC.get((dom, sched))
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "frac": achieved / hbm, "traffic": traffic, "traffic_unit": "bytes per iteration of the class",
+            "peak_source": src,
             "iteration_achieved": prof["bytes_per_iter"] / (ms_per_step / 1000.0) / 1e9,
             "iteration_frac": prof["bytes_per_iter"] / (ms_per_step / 1000.0) / 1e9 / hbm}
     launches = sum(c["launches"] for c in cls.values())

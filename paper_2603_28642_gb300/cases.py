@@ -5,6 +5,7 @@ Each case builds the 2M x 1M workload recipe (scaled by --scale), factors it
 part worth capturing inside an NVTX range named `timed`:
 
     python -m paper_2603_28642_gb300.cases trsv --system U --schedule coop --scale 0.25
+    python -m paper_2603_28642_gb300.cases trsv --system L1 --schedule auto --merge 0 --autotune --scale 1
     python -m paper_2603_28642_gb300.cases iteration --scale 0.75
 
 `trsv` calls rlsq_trsv on one system a few times; `iteration` autotunes and
@@ -44,7 +45,8 @@ def main(argv=None) -> int:
     t = sub.add_parser("trsv")
     t.add_argument("--system", choices=list(SYSTEMS), default="U")
     t.add_argument("--schedule", choices=list(SCHEDULES), default="coop")
-    t.add_argument("--merge", type=int, default=1)
+    t.add_argument("--merge", type=int, default=1, help="levels fused per group (0: chosen per system)")
+    t.add_argument("--autotune", action="store_true", help="autotune the mapping as the bench does")
     t.add_argument("--repeat", type=int, default=3)
     t.add_argument("--scale", type=float, default=0.25)
     it = sub.add_parser("iteration")
@@ -55,7 +57,8 @@ def main(argv=None) -> int:
     prob = synth.config_problem(1, scale=args.scale)
     P = B.Problem.from_problem(prob)
     if args.case == "trsv":
-        P.factor(**FACTOR, trsv_schedule=SCHEDULES[args.schedule], level_merge=args.merge)
+        P.factor(**FACTOR, trsv_schedule=SCHEDULES[args.schedule], level_merge=args.merge,
+                 autotune=1 if args.autotune else 0)
         b = np.random.default_rng(0).standard_normal(prob.n)
         _nvtx(True)
         for _ in range(args.repeat):
