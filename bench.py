@@ -64,6 +64,25 @@ CLASS_SYSTEM = {"trsv_L1": 0, "trsv_L1t": 1, "trsv_U": 2, "trsv_Ut": 3}
 
 
 # ---------------------------------------------------------------------------
+def max_over_ranks(value: float, dist) -> float:
+    """The largest `value` over all ranks (every rank gets it); `dist` is
+    torch.distributed or None for one process."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps_per_rank: int, world: int, max_ms: float) -> float:
+    """Iterations per second of the whole job: every rank runs its own replica
+    for `steps_per_rank` iterations, timed by the slowest rank."""
+    return world * steps_per_rank / (max_ms / 1000.0)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -229,13 +248,9 @@ def run_ours(args):
     torch.cuda.nvtx.range_pop()
     clocks = clk.stop()
     barrier()
-    total_ms = prof["total_ms"]
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(prof["total_ms"], dist)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(args.steps, world, total_ms)
 
     # end to end through the public call with host buffers (b in, x out)
     barrier()
