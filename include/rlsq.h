@@ -332,6 +332,20 @@ int rlsq_setup_sizes(rlsq_setup s, int64_t *sizes);
 int rlsq_setup_split(rlsq_setup s, int32_t *prow, int32_t *a2rows, double *d, double *udiag);
 int rlsq_setup_factor(rlsq_setup s, int32_t part, int64_t *ptr, int32_t *idx, double *val);
 int rlsq_setup_levels(rlsq_setup s, int32_t which, int32_t *level);
+/* Level fusion of triangular system `which` (RLSQ_SYS_*) as rlsq_factor does
+   it (no counterpart in the paper): k >= 1 fuses groups of k consecutive
+   levels, k = 0 grows groups level by level under the library's float64 cost
+   model.  Inside a group the dependencies on rows of the same group are
+   substituted, so row i reads x_i = (rhs_i + sum_R c rhs_j - sum_T c x_j) / d_i
+   (d = 1 for L1, L1^T; U's diagonal for U, U^T) with every T dependency in an
+   earlier group.  The result stays in the handle until the next call.
+   out[0..3] = stored entries of T, of R, levels of T, levels in the largest
+   group.  Errors: ARG. */
+int rlsq_setup_fuse(rlsq_setup s, int32_t which, int32_t k, int64_t *out);
+/* CSR of the last fused system, rows and columns = unknown ids: part 0 = T,
+   1 = R; ptr has n + 1 entries, idx / val the counts rlsq_setup_fuse gave.
+   Errors: ARG (bad part, no fused system). */
+int rlsq_setup_fused(rlsq_setup s, int32_t part, int64_t *ptr, int32_t *idx, double *val);
 void rlsq_setup_destroy(rlsq_setup s);
 
 /* Message of the last error on this thread ("" if none). */

@@ -102,6 +102,7 @@ EXPORTS = [
     "rlsq_server_poll", "rlsq_server_get_stats", "rlsq_server_destroy", "rlsq_last_error",
     "rlsq_setup_create", "rlsq_setup_sizes", "rlsq_setup_split", "rlsq_setup_factor",
     "rlsq_setup_levels", "rlsq_setup_destroy", "rlsq_profile", "rlsq_trsv_noalloc",
+    "rlsq_setup_fuse", "rlsq_setup_fused",
 ]
 
 KCLASS = ["spmv", "spmvt", "trsv_L1", "trsv_L1t", "trsv_U", "trsv_Ut", "l2", "l2t", "vec",
@@ -157,6 +158,8 @@ def load(build_if_missing: bool = True):
             "rlsq_setup_destroy": (None, [P]),
             "rlsq_profile": (C.c_int, [P, P, i32, i32, i32, P]),
             "rlsq_trsv_noalloc": (C.c_int, [P, i32, P, P, P]),
+            "rlsq_setup_fuse": (C.c_int, [P, i32, i32, P]),
+            "rlsq_setup_fused": (C.c_int, [P, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -482,3 +485,18 @@ class HostSetup:
         lev = np.zeros(self.n, dtype=np.int32)
         _check(load().rlsq_setup_levels(self._h, int(which), _ptr(lev)[0]))
         return lev
+
+    def fuse(self, which: int, k: int):
+        """Level fusion of one system (k >= 1 fixed groups, 0 chosen level by
+        level); returns sizes and the CSR of T and R (unknown ids)."""
+        out = np.zeros(4, dtype=np.int64)
+        _check(load().rlsq_setup_fuse(self._h, int(which), int(k), _ptr(out)[0]))
+        parts = []
+        for part, nnz in ((0, int(out[0])), (1, int(out[1]))):
+            ptr = np.zeros(self.n + 1, dtype=np.int64)
+            idx = np.zeros(max(nnz, 1), dtype=np.int32)
+            val = np.zeros(max(nnz, 1))
+            _check(load().rlsq_setup_fused(self._h, part, _ptr(ptr)[0], _ptr(idx)[0], _ptr(val)[0]))
+            parts.append((ptr, idx[:nnz], val[:nnz]))
+        sizes = {"nnz_T": int(out[0]), "nnz_R": int(out[1]), "levels": int(out[2]), "max_group": int(out[3])}
+        return sizes, parts[0], parts[1]

@@ -15,6 +15,7 @@ void set_last_error(const std::string& msg);
 
 struct rlsq_setup_s {
     rlsq::IlupResult F;
+    rlsq::MergedTri fused;  // the last rlsq_setup_fuse result
 };
 
 namespace {
@@ -157,6 +158,39 @@ int rlsq_setup_levels(rlsq_setup s, int32_t which, int32_t* level) {
             default: throw SetupError(RLSQ_ERR_ARG, "bad system id");
         }
         std::memcpy(level, L->level.data(), L->level.size() * sizeof(int32_t));
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_setup_fuse(rlsq_setup s, int32_t which, int32_t k, int64_t* out) {
+    return run([&]() -> int {
+        if (!s || !out) throw SetupError(RLSQ_ERR_ARG, "null argument");
+        if (k < 0) throw SetupError(RLSQ_ERR_ARG, "k must be >= 0");
+        const rlsq::IlupResult& F = s->F;
+        const rlsq::HostCSR* parts[4] = {&F.L1, &F.L1t, &F.U, &F.Ut};
+        const rlsq::Levels* levs[4] = {&F.lev_L1, &F.lev_L1t, &F.lev_U, &F.lev_Ut};
+        if (which < 0 || which > 3) throw SetupError(RLSQ_ERR_ARG, "bad system id");
+        const double* dg = which >= 2 ? F.Udiag.data() : nullptr;
+        s->fused = k >= 1 ? rlsq::merge_levels(*parts[which], dg, *levs[which], k)
+                          : rlsq::merge_levels_adaptive(*parts[which], dg, *levs[which],
+                                                        rlsq::kLevelCost / rlsq::kEntryCost, rlsq::kMaxFusedGroup);
+        out[0] = s->fused.T.nnz();
+        out[1] = s->fused.R.nnz();
+        out[2] = s->fused.lev.nlevels;
+        out[3] = s->fused.k;
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_setup_fused(rlsq_setup s, int32_t part, int64_t* ptr, int32_t* idx, double* val) {
+    return run([&]() -> int {
+        if (!s || !ptr || !idx || !val) throw SetupError(RLSQ_ERR_ARG, "null argument");
+        if (part != 0 && part != 1) throw SetupError(RLSQ_ERR_ARG, "part must be 0 (T) or 1 (R)");
+        const rlsq::HostCSR& M = part == 0 ? s->fused.T : s->fused.R;
+        if (M.ptr.empty()) throw SetupError(RLSQ_ERR_ARG, "no fused system: call rlsq_setup_fuse first");
+        std::memcpy(ptr, M.ptr.data(), M.ptr.size() * sizeof(int64_t));
+        std::memcpy(idx, M.idx.data(), M.idx.size() * sizeof(int32_t));
+        std::memcpy(val, M.val.data(), M.val.size() * sizeof(double));
         return RLSQ_OK;
     });
 }

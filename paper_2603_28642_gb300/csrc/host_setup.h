@@ -80,6 +80,15 @@ struct MergedTri {
     int k = 1;       // levels per group (adaptive: the largest group)
     bool adaptive = false;
 };
+// Cost model of a fused solve, fitted to the measured solves of a 2M x 1M
+// problem on GB300 (every schedule, k = 1..4): about kLevelCost seconds per
+// level plus kEntryCost seconds per stored float64 entry of T and R (an
+// entry's cost is a random gather, not its bytes; float32 entries scale by
+// width).  Groups grown level by level hold at most kMaxFusedGroup levels.
+constexpr double kLevelCost = 3.0e-6;
+constexpr double kEntryCost = 13.7e-12;
+constexpr int kMaxFusedGroup = 16;
+
 // max_nnz > 0: give up (k = 0 in the result) once T and R hold more entries.
 MergedTri merge_levels(const HostCSR& strict, const double* diag, const Levels& lev, int k, int64_t max_nnz = 0);
 // Groups of consecutive levels chosen greedily: a level joins the current

@@ -1076,11 +1076,8 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
                 throw ApiError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
         }
         cudaStream_t st = h->stream;
-        // fused levels per system (0: the k of least modelled time).  The
-        // model was fitted to the measured solves of a 2M x 1M problem on
-        // GB300 (every schedule, k = 1..4): about 3 us per level plus 13.7 ps
-        // per stored float64 entry (T and R; an entry's cost is a random
-        // gather, not its bytes), scaled by the entry width for float32
+        // fused levels per system (0: the grouping of least modelled time
+        // under the cost model of host_setup.h)
         h->merged.clear();
         {
             const HostCSR* parts[4] = {&F->L1, &F->L1t, &F->U, &F->Ut};
@@ -1093,9 +1090,9 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
                     continue;
                 }
                 MergedTri best = merge_levels(*parts[w], dg, *levs[w], 1);
-                const double entry_s = (wv + 4.0) / 12.0 * 13.7e-12;
+                const double entry_s = (wv + 4.0) / 12.0 * kEntryCost;
                 auto cost = [&](const MergedTri& M) {
-                    return M.lev.nlevels * 3.0e-6 + entry_s * static_cast<double>(M.T.nnz() + M.R.nnz());
+                    return M.lev.nlevels * kLevelCost + entry_s * static_cast<double>(M.T.nnz() + M.R.nnz());
                 };
                 double cbest = cost(best);
                 auto consider = [&](MergedTri&& M) {
@@ -1107,7 +1104,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
                 };
                 // groups chosen level by level: a level joins while its fill
                 // costs less than the level it saves
-                consider(merge_levels_adaptive(*parts[w], dg, *levs[w], 3.0e-6 / entry_s, 16));
+                consider(merge_levels_adaptive(*parts[w], dg, *levs[w], kLevelCost / entry_s, kMaxFusedGroup));
                 for (int kk = 2; kk <= 4; ++kk) {
                     MergedTri M = merge_levels(*parts[w], dg, *levs[w], kk, 4 * std::max<int64_t>(parts[w]->nnz(), h->n));
                     if (M.k == 0) break;
