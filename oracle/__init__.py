@@ -73,6 +73,9 @@ def _load():
         lib.orc_norm2.argtypes = [i64, i64, P, P, P, cint]
         lib.orc_lsmr.restype = cint
         lib.orc_lsmr.argtypes = [P, i64, i64, P, P, P, P, dbl, dbl, cint, P, P, P, P]
+        lib.orc_apply_residual.argtypes = [P, P, P]
+        lib.orc_cgls.restype = cint
+        lib.orc_cgls.argtypes = [P, cint, i64, i64, P, P, P, P, dbl, dbl, cint, P, P, P, P]
         _lib = lib
         return lib
 
@@ -186,6 +189,10 @@ class Factor:
     def apply(self, s):
         return self._vec(_load().orc_apply, s, self.n)
 
+    def apply_residual(self, r):
+        """Algorithm 3 on a residual r (length m): h = M^{-1} A^T r in the paper's form."""
+        return self._vec(_load().orc_apply_residual, r, self.n)
+
     def solve_L1(self, b):
         return self._vec(_load().orc_solve_L1, b, self.n)
 
@@ -264,4 +271,23 @@ def lsmr(factor, m, n, rowptr, colidx, vals, b, anorm=None, atol=1e-8, maxit=200
     st = lib.orc_lsmr(factor._h if factor is not None else None, m, n, _p(rp), _p(ci), _p(va),
                       _p(b), float(anorm), float(atol), int(maxit), _p(x), C.byref(its),
                       _p(hist), C.byref(fr))
+    return LsmrResult(x, its.value, int(st), fr.value, hist[: its.value + 1])
+
+
+def cgls(factor, m, n, rowptr, colidx, vals, b, anorm=None, atol=1e-8, maxit=2000, form="residual"):
+    """Algorithm 1 (left preconditioned CGLS).  form "residual": h from
+    Algorithm 3 fed the residual split (the paper's combination of M^{-1} with
+    A^T); "symmetric": h = M^{-1} A^T r with the x-space operator."""
+    lib = _load()
+    rp, ci, va = _csr_arrays(rowptr, colidx, vals)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if anorm is None:
+        anorm = norm2(m, n, rp, ci, va)
+    x = np.zeros(n)
+    its = C.c_int(0)
+    fr = C.c_double(0.0)
+    hist = np.zeros(maxit + 1)
+    st = lib.orc_cgls(factor._h, 0 if form == "residual" else 1, m, n, _p(rp), _p(ci), _p(va), _p(b),
+                      float(anorm), float(atol), int(maxit),
+                      _p(x), C.byref(its), _p(hist), C.byref(fr))
     return LsmrResult(x, its.value, int(st), fr.value, hist[: its.value + 1])

@@ -35,6 +35,13 @@
  *                       recomputed explicitly, ||A||_2 from the power method
  *                       (Sec. 5.1).
  *   orc_norm2           power method on A^T A.
+ *   orc_apply_residual  Algorithm 3 as printed, on a residual r (the paper's
+ *                       left preconditioner): r1 = the pivot rows of r in
+ *                       pivot order, r2 = the A2 rows; u = r2 - Y r1,
+ *                       S^ w = u, y = r1 + Y^T w, L1 v = y, U h = v, and the
+ *                       column scaling D back to x-space.
+ *   orc_cgls            Algorithm 1 (left preconditioned CGLS) with
+ *                       h = orc_apply_residual(r) in place of M^{-1} A^T r.
  *
  * Readings of points the paper leaves open (all also listed in the design
  * notes):
@@ -917,5 +924,96 @@ done:
     if (its_out) *its_out = k;
     if (final_ratio) *final_ratio = ratio;
     free(u); free(r); free(ax); free(s); free(t); free(vh); free(w); free(h); free(hb); free(z);
+    return status;
+}
+
+/*
+ * Algorithm 3 on the residual r (length m, original row order): the
+ * factors are those of the scaled matrix A D, so h = D h^ for the user's
+ * unknowns.  Mode 0 (NONE) takes w = 0, i.e. h = D U^{-1} L1^{-1} r1.
+ */
+void orc_apply_residual(const orc_factor *f, const double *r, double *h) {
+    int64_t n = f->n, m2 = f->m - f->n;
+    double *r1 = (double *)xmalloc((size_t)n * sizeof(double));
+    double *q1 = (double *)xmalloc((size_t)n * sizeof(double));
+    double *y = (double *)xmalloc((size_t)n * sizeof(double));
+    double *v = (double *)xmalloc((size_t)n * sizeof(double));
+    for (int64_t k = 0; k < n; k++) r1[k] = r[f->prow[k]];
+    for (int64_t k = 0; k < n; k++) y[k] = r1[k];
+    if (f->mode != 0 && m2 > 0) {
+        double *u = (double *)xmalloc((size_t)m2 * sizeof(double));
+        double *w = (double *)xmalloc((size_t)m2 * sizeof(double));
+        double *fv = (double *)xmalloc((size_t)n * sizeof(double));
+        double *g = (double *)xmalloc((size_t)n * sizeof(double));
+        /* step 1: u = r2 - Y r1, Y = L2 L1^{-1} */
+        solve_lower(n, f->L1p, f->L1i, f->L1v, NULL, r1, q1);
+        csr_mv(m2, f->L2p, f->L2i, f->L2v, q1, u);
+        for (int64_t i = 0; i < m2; i++) u[i] = r[f->a2rows[i]] - u[i];
+        /* step 2: S^ w = u */
+        s_solve(f, u, w);
+        /* step 3: y = r1 + Y^T w, Y^T = L1^{-T} L2^T */
+        csr_mv(n, f->L2tp, f->L2ti, f->L2tv, w, fv);
+        solve_upper(n, f->L1tp, f->L1ti, f->L1tv, NULL, fv, g);
+        for (int64_t k = 0; k < n; k++) y[k] = r1[k] + g[k];
+        free(u); free(w); free(fv); free(g);
+    }
+    /* step 4: L1 v = y, then U h = v */
+    solve_lower(n, f->L1p, f->L1i, f->L1v, NULL, y, v);
+    solve_upper(n, f->Up, f->Ui, f->Uv, f->Udiag, v, q1);
+    for (int64_t j = 0; j < n; j++) h[j] = f->d[j] * q1[j];
+    free(r1); free(q1); free(y); free(v);
+}
+
+/*
+ * Algorithm 1 from x0 = 0 (the printed step 3 overwrites z0; read as
+ * h0 = M^{-1} z0, rho0 = (z0, h0), p0 = h0).  form 0: h = orc_apply_residual(r)
+ * (Algorithm 3 fed the residual split, as the paper combines M^{-1} with A^T);
+ * form 1: h = orc_apply(A^T r) (the symmetric x-space operator used with LSMR).
+ * Stopping: for k = 0, 1, ...: ratio_k = ||z_k|| / (anorm ||r_k||) with the
+ * recurrence residual r_k and z_k = A^T r_k (Algorithm 1 step 11); stop when
+ * ratio_k < atol (or r_k = 0), or when k = maxit.
+ * Returns 0 converged, 1 iteration limit, -2 breakdown (rho <= 0, ||q|| = 0
+ * or not finite).  ratio_hist (optional, length maxit + 1).
+ */
+int orc_cgls(const orc_factor *f, int form, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+             const double *vals, const double *b, double anorm, double atol, int maxit, double *x,
+             int *its_out, double *ratio_hist, double *final_ratio) {
+    double *r = (double *)xmalloc((size_t)m * sizeof(double));
+    double *q = (double *)xmalloc((size_t)m * sizeof(double));
+    double *z = (double *)xmalloc((size_t)n * sizeof(double));
+    double *h = (double *)xmalloc((size_t)n * sizeof(double));
+    double *p = (double *)xmalloc((size_t)n * sizeof(double));
+    int status = 1, k = 0;
+    double ratio = 0.0;
+    for (int64_t j = 0; j < n; j++) x[j] = 0.0;
+    for (int64_t i = 0; i < m; i++) r[i] = b[i];                 /* step 1 */
+    csr_mtv(m, n, rowptr, colidx, vals, r, z);                    /* step 2 */
+    if (form == 0) orc_apply_residual(f, r, h); else orc_apply(f, z, h);   /* step 3 */
+    double rho = dot(n, z, h);                                    /* step 4 */
+    for (int64_t j = 0; j < n; j++) p[j] = h[j];                  /* step 5 */
+    for (k = 0;; k++) {
+        double rn = sqrt(dot(m, r, r));
+        double zn = sqrt(dot(n, z, z));
+        ratio = (rn > 0.0) ? zn / (anorm * rn) : 0.0;
+        if (ratio_hist) ratio_hist[k] = ratio;
+        if (ratio < atol) { status = 0; break; }
+        if (k == maxit) { status = 1; break; }
+        if (!(rho > 0.0) || !isfinite(rho)) { status = -2; break; }
+        csr_mv(m, rowptr, colidx, vals, p, q);                    /* step 7 */
+        double qq = dot(m, q, q);
+        if (!(qq > 0.0) || !isfinite(qq)) { status = -2; break; }
+        double alpha = rho / qq;                                  /* step 8 */
+        for (int64_t j = 0; j < n; j++) x[j] = x[j] + alpha * p[j];   /* step 9 */
+        for (int64_t i = 0; i < m; i++) r[i] = r[i] - alpha * q[i];   /* step 10 */
+        csr_mtv(m, n, rowptr, colidx, vals, r, z);                /* step 11 */
+        if (form == 0) orc_apply_residual(f, r, h); else orc_apply(f, z, h);   /* step 12 */
+        double rhon = dot(n, z, h);                               /* step 13 */
+        double beta = rhon / rho;                                 /* step 14 */
+        for (int64_t j = 0; j < n; j++) p[j] = h[j] + beta * p[j];    /* step 15 */
+        rho = rhon;
+    }
+    if (its_out) *its_out = k;
+    if (final_ratio) *final_ratio = ratio;
+    free(r); free(q); free(z); free(h); free(p);
     return status;
 }
