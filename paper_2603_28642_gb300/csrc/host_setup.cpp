@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <exception>
 #include <stdexcept>
 #include <thread>
 
@@ -366,13 +367,39 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
                 R.U.val[dst] = Uv[e];
             }
     }
-    R.L1t = transpose(R.L1);
-    R.L2t = transpose(R.L2);
-    R.Ut = transpose(R.U);
-    R.lev_L1 = analyse_levels(R.L1, true);
-    R.lev_L1t = analyse_levels(R.L1t, false);
-    R.lev_U = analyse_levels(R.U, false);
-    R.lev_Ut = analyse_levels(R.Ut, true);
+    // transposes and level sets: independent of each other, built on three
+    // threads (each result is deterministic)
+    {
+        std::exception_ptr e1, e2;
+        std::thread t1([&R, &e1]() {
+            try {
+                R.L1t = transpose(R.L1);
+                R.lev_L1 = analyse_levels(R.L1, true);
+                R.lev_L1t = analyse_levels(R.L1t, false);
+            } catch (...) {
+                e1 = std::current_exception();
+            }
+        });
+        std::thread t2([&R, &e2]() {
+            try {
+                R.Ut = transpose(R.U);
+                R.lev_U = analyse_levels(R.U, false);
+                R.lev_Ut = analyse_levels(R.Ut, true);
+            } catch (...) {
+                e2 = std::current_exception();
+            }
+        });
+        std::exception_ptr e0;
+        try {
+            R.L2t = transpose(R.L2);
+        } catch (...) {
+            e0 = std::current_exception();
+        }
+        t1.join();
+        t2.join();
+        for (const auto& e : {e0, e1, e2})
+            if (e) std::rethrow_exception(e);
+    }
     return R;
 }
 

@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cstddef>
 #include <cstring>
+#include <mutex>
+#include <exception>
 #include <thread>
 #include <type_traits>
 
@@ -1083,34 +1085,52 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
             const HostCSR* parts[4] = {&F->L1, &F->L1t, &F->U, &F->Ut};
             const Levels* levs[4] = {&F->lev_L1, &F->lev_L1t, &F->lev_U, &F->lev_Ut};
             const double wv = opts.precision == RLSQ_PREC_FP32 ? 4.0 : 8.0;
+            const double entry_s = (wv + 4.0) / 12.0 * kEntryCost;
+            // candidates per system: 0 = as is, 1 = groups grown level by level
+            // (a level joins while its fill costs less than the level it saves),
+            // 2..4 = fixed k; every candidate is a pure function of the factor,
+            // so they are built on separate host threads
+            const int ncand = opts.level_merge >= 1 ? 1 : 5;
+            std::vector<std::vector<MergedTri>> cand(4, std::vector<MergedTri>(static_cast<size_t>(ncand)));
+            std::exception_ptr failed;
+            std::mutex fail_mu;
+            std::vector<std::thread> pool;
+            for (int w = 0; w < 4; ++w)
+                for (int c = 0; c < ncand; ++c)
+                    pool.emplace_back([&, w, c]() {
+                        try {
+                            const double* dg = w >= 2 ? F->Udiag.data() : nullptr;
+                            MergedTri& out = cand[static_cast<size_t>(w)][static_cast<size_t>(c)];
+                            if (opts.level_merge >= 1) out = merge_levels(*parts[w], dg, *levs[w], opts.level_merge);
+                            else if (c == 0) out = merge_levels(*parts[w], dg, *levs[w], 1);
+                            else if (c == 1)
+                                out = merge_levels_adaptive(*parts[w], dg, *levs[w], kLevelCost / entry_s, kMaxFusedGroup);
+                            else
+                                out = merge_levels(*parts[w], dg, *levs[w], c, 4 * std::max<int64_t>(parts[w]->nnz(), h->n));
+                        } catch (...) {
+                            std::lock_guard<std::mutex> lock(fail_mu);
+                            if (!failed) failed = std::current_exception();
+                        }
+                    });
+            for (auto& t : pool) t.join();
+            if (failed) std::rethrow_exception(failed);
+            auto cost = [&](const MergedTri& M) {
+                return M.lev.nlevels * kLevelCost + entry_s * static_cast<double>(M.T.nnz() + M.R.nnz());
+            };
             for (int w = 0; w < 4; ++w) {
-                const double* dg = w >= 2 ? F->Udiag.data() : nullptr;
-                if (opts.level_merge >= 1) {
-                    h->merged.push_back(merge_levels(*parts[w], dg, *levs[w], opts.level_merge));
-                    continue;
-                }
-                MergedTri best = merge_levels(*parts[w], dg, *levs[w], 1);
-                const double entry_s = (wv + 4.0) / 12.0 * kEntryCost;
-                auto cost = [&](const MergedTri& M) {
-                    return M.lev.nlevels * kLevelCost + entry_s * static_cast<double>(M.T.nnz() + M.R.nnz());
-                };
-                double cbest = cost(best);
-                auto consider = [&](MergedTri&& M) {
-                    const double c = cost(M);
-                    if (c < cbest) {
-                        cbest = c;
-                        best = std::move(M);
+                auto& cw = cand[static_cast<size_t>(w)];
+                size_t best = 0;
+                double cbest = cost(cw[0]);
+                // earlier candidates win ties; fixed k stops at the first k the fill cap rejects
+                for (size_t c = 1; c < cw.size(); ++c) {
+                    if (c >= 2 && cw[c].k == 0) break;
+                    const double cc = cost(cw[c]);
+                    if (cc < cbest) {
+                        cbest = cc;
+                        best = c;
                     }
-                };
-                // groups chosen level by level: a level joins while its fill
-                // costs less than the level it saves
-                consider(merge_levels_adaptive(*parts[w], dg, *levs[w], kLevelCost / entry_s, kMaxFusedGroup));
-                for (int kk = 2; kk <= 4; ++kk) {
-                    MergedTri M = merge_levels(*parts[w], dg, *levs[w], kk, 4 * std::max<int64_t>(parts[w]->nnz(), h->n));
-                    if (M.k == 0) break;
-                    consider(std::move(M));
                 }
-                h->merged.push_back(std::move(best));
+                h->merged.push_back(std::move(cw[best]));
             }
         }
         h->f64.clear();
