@@ -263,6 +263,7 @@ def run_ours(args):
     # host factor is reused; only the device copy changes precision)
     tol64 = P.solve(prob.b)
     plain = P.solve(prob.b, plain=True)
+    cgls = P.solve(prob.b, solver=B.SOLVER_CGLS, allow_fail=True)  # Algorithm 1, same preconditioner
     P.factor(**FACTOR, precision=B.PREC_FP32, autotune=1)
     tol32 = P.solve(prob.b)
     prof32 = P.profile(prob.b, warmup=3, iters=args.steps)
@@ -306,6 +307,9 @@ def run_ours(args):
                            "iter_per_s": 1000.0 / prof32["ms_per_iter"]},
             "unpreconditioned": {"iterations": plain.info["iterations"],
                                  "seconds": plain.info["solve_seconds"], "status": plain.status},
+            "cgls_fp64": {"iterations": cgls.info["iterations"], "seconds": cgls.info["solve_seconds"],
+                          "ratio": cgls.info["ratio"], "status": cgls.status,
+                          "x_rel_diff_vs_lsmr": float(np.linalg.norm(cgls.x - tol64.x) / np.linalg.norm(tol64.x))},
         },
         "factor_seconds": finfo["factor_seconds"],
         "roofline": roof,

@@ -79,6 +79,12 @@ extern "C" {
 #define RLSQ_TRSV_WAVE 4     /* one co-resident launch, a fixed row sequence per thread, rows wait on
                                 their inputs and levels overlap (bounded waits) */
 
+/* Krylov solvers of rlsq_solve */
+#define RLSQ_SOLVER_LSMR 0  /* LSMR in x-space (the default) */
+#define RLSQ_SOLVER_CGLS 1  /* preconditioned CGLS (Algorithm 1) with h = M^{-1} A^T r; no dense-row
+                               problems.  The paper feeds Algorithm 3 the residual split instead,
+                               which stalls once entries are dropped (see the oracle's orc_cgls). */
+
 /* triangular systems for rlsq_trsv */
 #define RLSQ_SYS_L1 0   /* L1 x = b   (unit lower)      */
 #define RLSQ_SYS_L1T 1  /* L1^T x = b (unit upper)      */
@@ -125,6 +131,8 @@ typedef struct {
     int32_t ptr_mode;    /* RLSQ_HOST_PTRS or RLSQ_DEVICE_PTRS for b and x */
     void *stream;        /* cudaStream_t */
     int32_t check_every; /* iterations per captured CUDA graph between host checks (>= 1) */
+    int32_t solver;      /* RLSQ_SOLVER_*; stopping test the same for both (the CGLS residual is the
+                            recurrence one of Algorithm 1) */
 } rlsq_solve_opts;
 
 /* Result and statistics of a factorisation / solve. */
@@ -172,7 +180,7 @@ typedef struct {
    precision = FP64, trsv_schedule = AUTO, autotune = 0, dense_row_min = 0,
    level_merge = 0. */
 void rlsq_factor_opts_default(rlsq_factor_opts *opts);
-/* atol = 1e-8, maxit = 2000, host pointers, default stream, check_every = 8 */
+/* atol = 1e-8, maxit = 2000, host pointers, default stream, check_every = 8, LSMR */
 void rlsq_solve_opts_default(rlsq_solve_opts *opts);
 
 /* ---- problem handle ------------------------------------------------------- */

@@ -287,7 +287,8 @@ def cgls(factor, m, n, rowptr, colidx, vals, b, anorm=None, atol=1e-8, maxit=200
     its = C.c_int(0)
     fr = C.c_double(0.0)
     hist = np.zeros(maxit + 1)
-    st = lib.orc_cgls(factor._h, 0 if form == "residual" else 1, m, n, _p(rp), _p(ci), _p(va), _p(b),
+    st = lib.orc_cgls(factor._h if factor is not None else None, 0 if form == "residual" else 1, m, n,
+                      _p(rp), _p(ci), _p(va), _p(b),
                       float(anorm), float(atol), int(maxit),
                       _p(x), C.byref(its), _p(hist), C.byref(fr))
     return LsmrResult(x, its.value, int(st), fr.value, hist[: its.value + 1])

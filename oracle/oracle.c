@@ -968,7 +968,8 @@ void orc_apply_residual(const orc_factor *f, const double *r, double *h) {
  * Algorithm 1 from x0 = 0 (the printed step 3 overwrites z0; read as
  * h0 = M^{-1} z0, rho0 = (z0, h0), p0 = h0).  form 0: h = orc_apply_residual(r)
  * (Algorithm 3 fed the residual split, as the paper combines M^{-1} with A^T);
- * form 1: h = orc_apply(A^T r) (the symmetric x-space operator used with LSMR).
+ * form 1: h = orc_apply(A^T r) (the symmetric x-space operator used with LSMR);
+ * f == NULL: M = I (plain CGLS).
  * Stopping: for k = 0, 1, ...: ratio_k = ||z_k|| / (anorm ||r_k||) with the
  * recurrence residual r_k and z_k = A^T r_k (Algorithm 1 step 11); stop when
  * ratio_k < atol (or r_k = 0), or when k = maxit.
@@ -988,7 +989,8 @@ int orc_cgls(const orc_factor *f, int form, int64_t m, int64_t n, const int64_t 
     for (int64_t j = 0; j < n; j++) x[j] = 0.0;
     for (int64_t i = 0; i < m; i++) r[i] = b[i];                 /* step 1 */
     csr_mtv(m, n, rowptr, colidx, vals, r, z);                    /* step 2 */
-    if (form == 0) orc_apply_residual(f, r, h); else orc_apply(f, z, h);   /* step 3 */
+    if (!f) memcpy(h, z, (size_t)n * sizeof(double));               /* M = I */
+    else if (form == 0) orc_apply_residual(f, r, h); else orc_apply(f, z, h);   /* step 3 */
     double rho = dot(n, z, h);                                    /* step 4 */
     for (int64_t j = 0; j < n; j++) p[j] = h[j];                  /* step 5 */
     for (k = 0;; k++) {
@@ -1006,7 +1008,8 @@ int orc_cgls(const orc_factor *f, int form, int64_t m, int64_t n, const int64_t 
         for (int64_t j = 0; j < n; j++) x[j] = x[j] + alpha * p[j];   /* step 9 */
         for (int64_t i = 0; i < m; i++) r[i] = r[i] - alpha * q[i];   /* step 10 */
         csr_mtv(m, n, rowptr, colidx, vals, r, z);                /* step 11 */
-        if (form == 0) orc_apply_residual(f, r, h); else orc_apply(f, z, h);   /* step 12 */
+        if (!f) memcpy(h, z, (size_t)n * sizeof(double));
+        else if (form == 0) orc_apply_residual(f, r, h); else orc_apply(f, z, h);   /* step 12 */
         double rhon = dot(n, z, h);                               /* step 13 */
         double beta = rhon / rho;                                 /* step 14 */
         for (int64_t j = 0; j < n; j++) p[j] = h[j] + beta * p[j];    /* step 15 */

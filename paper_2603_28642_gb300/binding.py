@@ -27,6 +27,7 @@ HOST_PTRS, DEVICE_PTRS = 0, 1
 CORR_NONE, CORR_SI, CORR_CG, CORR_DENSE, CORR_AUTO = 0, 1, 2, 3, 4
 PREC_FP64, PREC_FP32 = 0, 1
 TRSV_AUTO, TRSV_LEVEL, TRSV_SYNCFREE, TRSV_COOP, TRSV_WAVE = 0, 1, 2, 3, 4
+SOLVER_LSMR, SOLVER_CGLS = 0, 1
 SYS_L1, SYS_L1T, SYS_U, SYS_UT = 0, 1, 2, 3
 PART_L1, PART_L2, PART_U = 0, 1, 2
 
@@ -50,7 +51,7 @@ class FactorOpts(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [
         ("atol", C.c_double), ("maxit", C.c_int32), ("ptr_mode", C.c_int32),
-        ("stream", C.c_void_p), ("check_every", C.c_int32),
+        ("stream", C.c_void_p), ("check_every", C.c_int32), ("solver", C.c_int32),
     ]
 
 

@@ -200,8 +200,8 @@ struct rlsq_problem_s {
     cudaEvent_t ev[2] = {nullptr, nullptr};
 
     rlsq::Recorder* rec = nullptr;                  // set while profiling one eager iteration
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [plain] iteration graphs
-    int graph_iters[2] = {0, 0};
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // [plain + 2 cgls] iteration graphs
+    int graph_iters[4] = {0, 0, 0, 0};
 
     ~rlsq_problem_s();
 };

@@ -1173,7 +1173,30 @@ __device__ void lsmr_scalar_step(LsmrState* S, double ts) {
 
 // t = d * g5 (IDENT: t = s, the unpreconditioned case), <t, s>; INIT: start the recurrences, else one LSMR
 // rotation step; either way the apply counter advances.
-template <typename T, bool INIT, bool IDENT = false>
+// CGLS (Algorithm 1) scalars after h = M^{-1} z: rho' = <z, h> (step 13),
+// beta = rho' / rho (step 14; INIT: the first rho, beta = 0).  The CGLS
+// quantities reuse LsmrState fields: rho -> alphabar, beta -> zetabar,
+// the step length alpha -> alpha.
+template <bool INIT>
+__device__ void cgls_scalar_step(LsmrState* S, double rho_new) {
+    S->apply_count += 1;
+    if (S->error != 0) {
+        S->done = 1;
+        S->status = kErrTimeout;
+        return;
+    }
+    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        S->done = 1;
+        S->status = kErrBreakdown;
+        return;
+    }
+    S->zetabar = INIT ? 0.0 : rho_new / S->alphabar;
+    S->alphabar = rho_new;
+}
+
+// t = D g5 (IDENT: t = s) into tx[i].x and <t, s>; the last block runs the
+// solver's scalar step (LSMR, or CGLS when CGLS is set).
+template <typename T, bool INIT, bool IDENT = false, bool CGLS = false>
 __global__ void __launch_bounds__(kBlock)
 k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const double* __restrict__ s,
                double2* __restrict__ tx, LsmrState* S, double* part, unsigned* counter) {
@@ -1187,7 +1210,143 @@ k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const d
     }
     double tot[1];
     if (!(last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0)) return;
-    lsmr_scalar_step<INIT>(S, tot[0]);
+    if (CGLS) cgls_scalar_step<INIT>(S, tot[0]);
+    else lsmr_scalar_step<INIT>(S, tot[0]);
+}
+
+// ---- preconditioned CGLS (Algorithm 1) ------------------------------------
+// Vectors: (q, r) interleaved in qr, (h, x) in tx (h = the preconditioner's
+// output t), z = A^T r in s, p in pv.
+
+// step 1 from x0 = 0: r = b, x = 0; rnorm = ||r||
+static __global__ void __launch_bounds__(kBlock)
+k_cgls_begin(int m, int n, const double* __restrict__ b, double2* __restrict__ qr, double2* __restrict__ tx,
+             LsmrState* S, double* part, unsigned* counter) {
+    double acc[1] = {0.0};
+    const int len = m > n ? m : n;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) {
+        if (i < m) {
+            const double v = b[i];
+            qr[i] = make_double2(0.0, v);
+            acc[0] += v * v;
+        }
+        if (i < n) tx[i] = make_double2(0.0, 0.0);
+    }
+    double tot[1];
+    if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0) S->rnorm = sqrt(tot[0]);
+}
+
+// step 11: z = A^T r (columns of A = rows of At, r = qr[i].y); the stopping
+// test on the current iterate: ratio = ||z|| / (||A|| ||r||)
+template <int G>
+__global__ void __launch_bounds__(kBlock, kMinBlocks)
+k_cgls_z(Csr<double> At, const double2* __restrict__ qr, double* __restrict__ z, LsmrState* S, double* part,
+         unsigned* counter) {
+    if (S->done) return;
+    const unsigned mask = group_mask<G>();
+    const int lane = threadIdx.x & (G - 1);
+    const int groups = (gridDim.x * kBlock) / G;
+    const double* r = reinterpret_cast<const double*>(qr) + 1;  // r_i at r[2 i]
+    double acc[1] = {0.0};
+    for (int col = (blockIdx.x * kBlock + threadIdx.x) / G; col < At.rows; col += groups) {
+        double sum = 0.0;
+        const int e1 = At.ptr[col + 1];
+        int e = At.ptr[col] + lane;
+        for (; e + 3 * G < e1; e += 4 * G) {
+            const int j0 = At.idx[e], j1 = At.idx[e + G], j2 = At.idx[e + 2 * G], j3 = At.idx[e + 3 * G];
+            const double a0 = At.val[e], a1 = At.val[e + G], a2 = At.val[e + 2 * G], a3 = At.val[e + 3 * G];
+            const double v0 = r[2 * j0], v1 = r[2 * j1], v2 = r[2 * j2], v3 = r[2 * j3];
+            sum = fma(a0, v0, sum);
+            sum = fma(a1, v1, sum);
+            sum = fma(a2, v2, sum);
+            sum = fma(a3, v3, sum);
+        }
+        for (; e < e1; e += G) sum = fma(At.val[e], r[2 * At.idx[e]], sum);
+        if (G > 1) sum = group_sum<G>(sum, mask);
+        if (lane == 0) {
+            z[col] = sum;
+            acc[0] += sum * sum;
+        }
+    }
+    double tot[1];
+    if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0) {
+        const double zn = sqrt(tot[0]);
+        S->arnorm = zn;
+        const double ratio = S->rnorm > 0.0 ? zn / (S->anorm * S->rnorm) : 0.0;
+        S->ratio = ratio;
+        if (ratio < S->atol) {
+            S->done = 1;
+            S->status = kOk;
+        } else if (S->k >= S->maxit) {
+            S->done = 1;
+            S->status = kErrMaxit;
+        }
+    }
+}
+
+// step 15: p = h + beta p (INIT: step 5, p = h)
+template <bool INIT>
+__global__ void __launch_bounds__(kBlock)
+k_cgls_p(int n, const double2* __restrict__ tx, double* __restrict__ pv, const LsmrState* S) {
+    if (S->done) return;
+    const double beta = S->zetabar;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+        pv[i] = INIT ? tx[i].x : tx[i].x + beta * pv[i];
+}
+
+// steps 7-8: q = A p, alpha = rho / <q, q>
+template <int G>
+__global__ void __launch_bounds__(kBlock, kMinBlocks)
+k_cgls_q(Csr<double> A, const double* __restrict__ pv, double2* __restrict__ qr, LsmrState* S, double* part,
+         unsigned* counter) {
+    if (S->done) return;
+    const unsigned mask = group_mask<G>();
+    const int lane = threadIdx.x & (G - 1);
+    const int groups = (gridDim.x * kBlock) / G;
+    double acc[1] = {0.0};
+    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < A.rows; row += groups) {
+        double sum = 0.0;
+        row_dot<G>(A, row, lane, pv, sum);
+        if (G > 1) sum = group_sum<G>(sum, mask);
+        if (lane == 0) {
+            qr[row].x = sum;
+            acc[0] += sum * sum;
+        }
+    }
+    double tot[1];
+    if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0) {
+        const double qq = tot[0];
+        if (!(qq > 0.0) || !isfinite(qq)) {
+            S->done = 1;
+            S->status = kErrBreakdown;
+        } else {
+            S->alpha = S->alphabar / qq;
+        }
+    }
+}
+
+// steps 9-10: x += alpha p, r -= alpha q; rnorm = ||r||, k += 1
+static __global__ void __launch_bounds__(kBlock)
+k_cgls_xr(int m, int n, const double* __restrict__ pv, double2* __restrict__ qr, double2* __restrict__ tx,
+          LsmrState* S, double* part, unsigned* counter) {
+    if (S->done) return;
+    const double a = S->alpha;
+    double acc[1] = {0.0};
+    const int len = m > n ? m : n;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) {
+        if (i < m) {
+            double2 v = qr[i];
+            v.y = v.y - a * v.x;
+            qr[i] = v;
+            acc[0] += v.y * v.y;
+        }
+        if (i < n) tx[i].y = tx[i].y + a * pv[i];
+    }
+    double tot[1];
+    if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0) {
+        S->rnorm = sqrt(tot[0]);
+        S->k += 1;
+    }
 }
 
 // INIT: h = v^_1, h-bar = 0, x = 0.  Else: h-bar, x, h updates, k += 1.

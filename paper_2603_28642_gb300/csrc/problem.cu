@@ -332,8 +332,9 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
 }
 
 // t = M^{-1} s for the float64 vector s, result in P->t; advances the LSMR
-// scalars (INIT: the first alpha) or only the apply count (standalone).
-template <typename T, bool INIT>
+// scalars (INIT: the first alpha), or the CGLS ones (CGLS), or only the apply
+// count (standalone).
+template <typename T, bool INIT, bool CGLS = false>
 static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, LsmrState* S,
                           cudaStream_t st) {
     const int n = static_cast<int>(P->n);
@@ -426,28 +427,28 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
     T* g5 = F.vn[2].p;
     launch_trsv<T>(P, F, 2, RHS_VEC, Rhs<T>{g4, nullptr, nullptr}, g5, slot++, S, st);    // U^{-1}
     RecScope rs(P, RLSQ_KCLASS_FINISH, (2.0 * sizeof(T) + 16.0) * n, st);
-    k_finish_apply<T, INIT><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, F.d.p, g5, s, P->tx.p, S,
-                                                                   P->part.p, P->counter.p);
+    k_finish_apply<T, INIT, false, CGLS><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, F.d.p, g5, s, P->tx.p, S,
+                                                                                P->part.p, P->counter.p);
 }
 
-template <bool INIT>
+template <bool INIT, bool CGLS = false>
 static void enqueue_identity_apply(rlsq_problem_s* P, const double* s, LsmrState* S, cudaStream_t st) {
     // M = I: t = s (the unpreconditioned baseline)
     const int n = static_cast<int>(P->n);
     RecScope rs(P, RLSQ_KCLASS_FINISH, 24.0 * n, st);
-    k_finish_apply<double, INIT, true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, nullptr, s, s, P->tx.p, S,
-                                                                              P->part.p, P->counter.p);
+    k_finish_apply<double, INIT, true, CGLS><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, nullptr, s, s, P->tx.p,
+                                                                                    S, P->part.p, P->counter.p);
 }
 
-template <bool INIT>
+template <bool INIT, bool CGLS = false>
 static void enqueue_apply_any(rlsq_problem_s* P, const double* s, LsmrState* S, cudaStream_t st,
                               bool plain) {
     if (plain) {
-        enqueue_identity_apply<INIT>(P, s, S, st);
+        enqueue_identity_apply<INIT, CGLS>(P, s, S, st);
     } else if (P->precision == RLSQ_PREC_FP32) {
-        enqueue_apply<float, INIT>(P, P->f32, s, S, st);
+        enqueue_apply<float, INIT, CGLS>(P, P->f32, s, S, st);
     } else {
-        enqueue_apply<double, INIT>(P, P->f64, s, S, st);
+        enqueue_apply<double, INIT, CGLS>(P, P->f64, s, S, st);
     }
 }
 
@@ -500,6 +501,47 @@ static void enqueue_start(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool
     k_lsmr_update<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, P->hb.p, S);
 }
 
+// Preconditioned CGLS (Algorithm 1) with h = M^{-1} A^T r, M^{-1} the same
+// x-space operator LSMR uses.  Vectors: (q, r) in qr, (h, x) in tx, z in s,
+// p in h.  No dense-row block.
+static void enqueue_cgls_z(rlsq_problem_s* P, LsmrState* S, cudaStream_t st) {
+    const int n = static_cast<int>(P->n);
+    RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 8.0, 8.0), st);
+    with_G(P->map.G_At, [&](auto g) {
+        k_cgls_z<decltype(g)::value><<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(
+            P->dAt.view(), P->qr.p, P->s.p, S, P->part.p, P->counter.p);
+    });
+}
+
+static void enqueue_start_cgls(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
+    const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
+    k_cgls_begin<<<grid_rows(P, std::max(m, n), 1), kBlock, 0, st>>>(m, n, P->b.p, P->qr.p, P->tx.p, S, P->part.p,
+                                                                     P->counter.p);
+    enqueue_cgls_z(P, S, st);                                      // z0 = A^T r0, ratio_0
+    enqueue_apply_any<true, true>(P, P->s.p, S, st, plain);       // h0 = M^{-1} z0, rho0
+    k_cgls_p<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, S);  // p0 = h0
+}
+
+static void enqueue_iteration_cgls(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
+    const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
+    {
+        RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 8.0, 16.0), st);
+        with_G(P->map.G_A, [&](auto g) {
+            k_cgls_q<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
+                P->dA.view(), P->h.p, P->qr.p, S, P->part.p, P->counter.p);
+        });
+    }
+    {
+        RecScope rs(P, RLSQ_KCLASS_UPDATE, 32.0 * m + 24.0 * n, st);
+        k_cgls_xr<<<grid_rows(P, std::max(m, n), 1), kBlock, 0, st>>>(m, n, P->h.p, P->qr.p, P->tx.p, S,
+                                                                       P->part.p, P->counter.p);
+    }
+    enqueue_cgls_z(P, S, st);
+    enqueue_apply_any<false, true>(P, P->s.p, S, st, plain);
+    RecScope rs(P, RLSQ_KCLASS_VEC, 24.0 * n, st);
+    k_cgls_p<false><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, S);
+}
+
 static LsmrState initial_state(const rlsq_problem_s* P, double atol, int maxit) {
     LsmrState s;
     std::memset(&s, 0, sizeof(s));
@@ -517,15 +559,15 @@ static void put_state(rlsq_problem_s* P, LsmrState* S, const LsmrState& h, cudaS
 }
 
 static void drop_graphs(rlsq_problem_s* P) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
         if (P->graph[i]) cudaGraphExecDestroy(P->graph[i]);
         P->graph[i] = nullptr;
         P->graph_iters[i] = 0;
     }
 }
 
-static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain) {
-    const int gi = plain ? 1 : 0;
+static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain, bool cgls = false) {
+    const int gi = (plain ? 1 : 0) + (cgls ? 2 : 0);
     if (P->graph[gi] && P->graph_iters[gi] == iters) return P->graph[gi];
     if (P->graph[gi]) cudaGraphExecDestroy(P->graph[gi]);
     P->graph[gi] = nullptr;
@@ -533,7 +575,10 @@ static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain)
     LsmrState* S = state_ptr(P, 0);
     RLSQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     try {
-        for (int i = 0; i < iters; ++i) enqueue_iteration(P, S, st, plain);
+        for (int i = 0; i < iters; ++i) {
+            if (cgls) enqueue_iteration_cgls(P, S, st, plain);
+            else enqueue_iteration(P, S, st, plain);
+        }
     } catch (...) {
         cudaGraph_t g = nullptr;
         cudaStreamEndCapture(st, &g);
@@ -630,6 +675,9 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
     if (!b || !x) throw ApiError(RLSQ_ERR_ARG, "null b or x");
     if (!(opts.atol >= 0.0) || opts.maxit < 0) throw ApiError(RLSQ_ERR_ARG, "bad atol or maxit");
     if (!plain && !P->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+    if (opts.solver != RLSQ_SOLVER_LSMR && opts.solver != RLSQ_SOLVER_CGLS) throw ApiError(RLSQ_ERR_ARG, "bad solver");
+    const bool cgls = opts.solver == RLSQ_SOLVER_CGLS;
+    if (cgls && P->md > 0) throw ApiError(RLSQ_ERR_ARG, "the CGLS solver does not take dense-row problems");
     const int iters = std::max(1, opts.check_every);
     cudaStream_t st = P->stream;
     cudaStream_t user = static_cast<cudaStream_t>(opts.stream);
@@ -641,8 +689,9 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
     upload_b(P, b, dev, st);
     LsmrState* S = state_ptr(P, 0);
     put_state(P, S, initial_state(P, opts.atol, opts.maxit), st);
-    enqueue_start(P, S, st, plain);
-    cudaGraphExec_t g = iteration_graph(P, iters, plain);
+    if (cgls) enqueue_start_cgls(P, S, st, plain);
+    else enqueue_start(P, S, st, plain);
+    cudaGraphExec_t g = iteration_graph(P, iters, plain, cgls);
     const int64_t max_launches = static_cast<int64_t>(opts.maxit) / iters + 4;
     int64_t launches = 0;
     // two graphs in flight; read `done` of the older one
@@ -939,6 +988,7 @@ void rlsq_solve_opts_default(rlsq_solve_opts* o) {
     o->ptr_mode = RLSQ_HOST_PTRS;
     o->stream = nullptr;
     o->check_every = 8;
+    o->solver = RLSQ_SOLVER_LSMR;
 }
 
 const char* rlsq_last_error(void) { return g_last_error.c_str(); }
