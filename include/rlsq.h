@@ -354,6 +354,17 @@ int rlsq_setup_fuse(rlsq_setup s, int32_t which, int32_t k, int64_t *out);
    1 = R; ptr has n + 1 entries, idx / val the counts rlsq_setup_fuse gave.
    Errors: ARG (bad part, no fused system). */
 int rlsq_setup_fused(rlsq_setup s, int32_t part, int64_t *ptr, int32_t *idx, double *val);
+/* Sec. 3.4, adding rows: k rows (host CSR over the n columns, the user's
+   values) join A2 with ids m .. m+k-1; each gets the L2 row l solving
+   l U = a D with L1, U, D and the pivots unchanged, dropped by the factor's
+   (tau, p) rule.  Later rlsq_setup_* getters see the updated factor
+   (rlsq_setup_sizes, _split with the new m, _factor).  Errors: ARG, CSR, SHAPE. */
+int rlsq_setup_add_rows(rlsq_setup s, int64_t k, const int64_t *rowptr, const int32_t *colidx,
+                        const double *vals);
+/* Sec. 3.4, removing rows of A2: ids ascending and distinct; their L2 rows go
+   and the remaining rows are renumbered in order (ids above a removed row move
+   down).  A pivot row cannot be removed this way: ARG (refactorise). */
+int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t *ids);
 void rlsq_setup_destroy(rlsq_setup s);
 
 /* Message of the last error on this thread ("" if none). */

@@ -74,6 +74,10 @@ def _load():
         lib.orc_lsmr.restype = cint
         lib.orc_lsmr.argtypes = [P, i64, i64, P, P, P, P, dbl, dbl, cint, P, P, P, P]
         lib.orc_apply_residual.argtypes = [P, P, P]
+        lib.orc_factor_add_rows.restype = cint
+        lib.orc_factor_add_rows.argtypes = [P, i64, P, P, P, cint, dbl]
+        lib.orc_factor_remove_rows.restype = cint
+        lib.orc_factor_remove_rows.argtypes = [P, i64, P]
         lib.orc_cgls.restype = cint
         lib.orc_cgls.argtypes = [P, cint, i64, i64, P, P, P, P, dbl, dbl, cint, P, P, P, P]
         _lib = lib
@@ -188,6 +192,22 @@ class Factor:
 
     def apply(self, s):
         return self._vec(_load().orc_apply, s, self.n)
+
+    def add_rows(self, rowptr, colidx, vals, p=10, tau=1e-2):
+        """Sec. 3.4: append rows (CSR, the user's values) to A2; returns the status."""
+        rp, ci, va = _csr_arrays(rowptr, colidx, vals)
+        k = len(rp) - 1
+        st = _load().orc_factor_add_rows(self._h, k, _p(rp), _p(ci), _p(va), int(p), float(tau))
+        self.m += k
+        return int(st)
+
+    def remove_rows(self, ids):
+        """Sec. 3.4: remove rows of A2 (ascending ids); -1 if one is a pivot row."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        st = _load().orc_factor_remove_rows(self._h, len(ids), _p(ids))
+        if st >= 0:
+            self.m -= len(ids)
+        return int(st)
 
     def apply_residual(self, r):
         """Algorithm 3 on a residual r (length m): h = M^{-1} A^T r in the paper's form."""

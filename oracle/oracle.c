@@ -42,6 +42,10 @@
  *                       column scaling D back to x-space.
  *   orc_cgls            Algorithm 1 (left preconditioned CGLS) with
  *                       h = orc_apply_residual(r) in place of M^{-1} A^T r.
+ *   orc_factor_add_rows / orc_factor_remove_rows
+ *                       Sec. 3.4: rows appended to A2 get an L2 row l
+ *                       solving U^T l = (a D)^T with L1, U, D and the pivots
+ *                       kept; removed A2 rows lose their L2 row.
  *
  * Readings of points the paper leaves open (all also listed in the design
  * notes):
@@ -1019,4 +1023,107 @@ int orc_cgls(const orc_factor *f, int form, int64_t m, int64_t n, const int64_t 
     if (final_ratio) *final_ratio = ratio;
     free(r); free(q); free(z); free(h); free(p);
     return status;
+}
+
+/*
+ * Sec. 3.4, adding rows: each new row a (the user's values, columns of A) is
+ * scaled by the existing D and gets the L2 row l with l U = a D, i.e.
+ * U^T l^T = (a D)^T (lower solve, position order), dropped by the rule of
+ * Algorithm 4 (|l| >= tau, then at most p of the largest, ties to the smaller
+ * position).  L1, U, D and the pivots stay; the new rows take ids m .. m+k-1
+ * and join A2 at its end (A2 rows stay in ascending id).  With the dense
+ * correction the dense S is set up again.  Returns orc_correction's status.
+ */
+int orc_factor_add_rows(orc_factor *f, int64_t k, const int64_t *rp, const int32_t *ci, const double *v,
+                        int p, double tau) {
+    int64_t n = f->n, m = f->m, m2 = m - n;
+    int64_t old_nnz = f->L2p[m2];
+    double *ah = (double *)xcalloc((size_t)n, sizeof(double));
+    double *l = (double *)xmalloc((size_t)n * sizeof(double));
+    cand *c = (cand *)xmalloc((size_t)n * sizeof(cand));
+    /* new rows collected first, then the CSR grown once */
+    int64_t cap = old_nnz + k * (p >= 0 ? p : n) + 1;
+    int64_t *np = (int64_t *)xmalloc((size_t)(m2 + k + 1) * sizeof(int64_t));
+    int32_t *ni = (int32_t *)xmalloc((size_t)cap * sizeof(int32_t));
+    double *nv = (double *)xmalloc((size_t)cap * sizeof(double));
+    memcpy(np, f->L2p, (size_t)(m2 + 1) * sizeof(int64_t));
+    memcpy(ni, f->L2i, (size_t)old_nnz * sizeof(int32_t));
+    memcpy(nv, f->L2v, (size_t)old_nnz * sizeof(double));
+    int64_t w = old_nnz;
+    for (int64_t t = 0; t < k; t++) {
+        for (int64_t j = 0; j < n; j++) ah[j] = 0.0;
+        for (int64_t e = rp[t]; e < rp[t + 1]; e++) ah[ci[e]] = v[e] * f->d[ci[e]];
+        solve_lower(n, f->Utp, f->Uti, f->Utv, f->Udiag, ah, l);
+        int64_t len = 0;
+        for (int64_t q = 0; q < n; q++)
+            if (l[q] != 0.0) { c[len].mag = fabs(l[q]); c[len].key = (int32_t)q; c[len].val = l[q]; len++; }
+        int64_t kept = drop_keep(c, len, p, tau);
+        for (int64_t q = 0; q < kept; q++) { ni[w] = c[q].key; nv[w] = c[q].val; w++; }
+        np[m2 + t + 1] = w;
+    }
+    free(ah); free(l); free(c);
+    free(f->L2p); free(f->L2i); free(f->L2v);
+    f->L2p = np; f->L2i = ni; f->L2v = nv;
+    free(f->L2tp); free(f->L2ti); free(f->L2tv);
+    csr_transpose(m2 + k, n, f->L2p, f->L2i, f->L2v, &f->L2tp, &f->L2ti, &f->L2tv);
+    f->a2rows = (int32_t *)realloc(f->a2rows, (size_t)(m2 + k) * sizeof(int32_t));
+    f->pivpos = (int32_t *)realloc(f->pivpos, (size_t)(m + k) * sizeof(int32_t));
+    f->a2idx = (int32_t *)realloc(f->a2idx, (size_t)(m + k) * sizeof(int32_t));
+    for (int64_t t = 0; t < k; t++) {
+        f->a2rows[m2 + t] = (int32_t)(m + t);
+        f->pivpos[m + t] = -1;
+        f->a2idx[m + t] = (int32_t)(m2 + t);
+    }
+    f->m = m + k;
+    if (f->mode == 3) return orc_correction(f, 3, f->cg_steps);
+    return 0;
+}
+
+/*
+ * Sec. 3.4, removing rows of A2 (ids ascending, distinct): their L2 rows go;
+ * the remaining rows keep their order and are renumbered (ids above a removed
+ * one move down).  A pivot row cannot be removed this way (-1: refactorise).
+ * With the dense correction the dense S is set up again.
+ */
+int orc_factor_remove_rows(orc_factor *f, int64_t k, const int32_t *ids) {
+    int64_t n = f->n, m = f->m, m2 = m - n;
+    for (int64_t t = 0; t < k; t++) {
+        if (ids[t] < 0 || ids[t] >= m || f->pivpos[ids[t]] >= 0) return -1;
+        if (t > 0 && ids[t] <= ids[t - 1]) return -1;
+    }
+    /* new id of every old row (-1: removed) */
+    int32_t *nid = (int32_t *)xmalloc((size_t)m * sizeof(int32_t));
+    int64_t t = 0, next = 0;
+    for (int64_t i = 0; i < m; i++) {
+        if (t < k && ids[t] == i) { nid[i] = -1; t++; }
+        else nid[i] = (int32_t)next++;
+    }
+    int64_t *np = (int64_t *)xmalloc((size_t)(m2 - k + 1) * sizeof(int64_t));
+    int32_t *ni = (int32_t *)xmalloc((size_t)(f->L2p[m2] + 1) * sizeof(int32_t));
+    double *nv = (double *)xmalloc((size_t)(f->L2p[m2] + 1) * sizeof(double));
+    int32_t *na2 = (int32_t *)xmalloc((size_t)(m2 - k > 0 ? m2 - k : 1) * sizeof(int32_t));
+    np[0] = 0;
+    int64_t r = 0, w = 0;
+    for (int64_t c = 0; c < m2; c++) {
+        int32_t orig = f->a2rows[c];
+        if (nid[orig] < 0) continue;
+        for (int64_t e = f->L2p[c]; e < f->L2p[c + 1]; e++) { ni[w] = f->L2i[e]; nv[w] = f->L2v[e]; w++; }
+        na2[r] = nid[orig];
+        np[++r] = w;
+    }
+    for (int64_t q = 0; q < n; q++) f->prow[q] = nid[f->prow[q]];
+    free(f->L2p); free(f->L2i); free(f->L2v); free(f->a2rows);
+    f->L2p = np; f->L2i = ni; f->L2v = nv; f->a2rows = na2;
+    free(f->L2tp); free(f->L2ti); free(f->L2tv);
+    csr_transpose(m2 - k, n, f->L2p, f->L2i, f->L2v, &f->L2tp, &f->L2ti, &f->L2tv);
+    int32_t *pp = (int32_t *)xmalloc((size_t)(m - k > 0 ? m - k : 1) * sizeof(int32_t));
+    int32_t *ai = (int32_t *)xmalloc((size_t)(m - k > 0 ? m - k : 1) * sizeof(int32_t));
+    for (int64_t i = 0; i < m - k; i++) { pp[i] = -1; ai[i] = -1; }
+    for (int64_t q = 0; q < n; q++) pp[f->prow[q]] = (int32_t)q;
+    for (int64_t c = 0; c < m2 - k; c++) ai[f->a2rows[c]] = (int32_t)c;
+    free(f->pivpos); free(f->a2idx); free(nid);
+    f->pivpos = pp; f->a2idx = ai;
+    f->m = m - k;
+    if (f->mode == 3) return orc_correction(f, 3, f->cg_steps);
+    return 0;
 }

@@ -103,7 +103,7 @@ EXPORTS = [
     "rlsq_server_poll", "rlsq_server_get_stats", "rlsq_server_destroy", "rlsq_last_error",
     "rlsq_setup_create", "rlsq_setup_sizes", "rlsq_setup_split", "rlsq_setup_factor",
     "rlsq_setup_levels", "rlsq_setup_destroy", "rlsq_profile", "rlsq_trsv_noalloc",
-    "rlsq_setup_fuse", "rlsq_setup_fused",
+    "rlsq_setup_fuse", "rlsq_setup_fused", "rlsq_setup_add_rows", "rlsq_setup_remove_rows",
 ]
 
 KCLASS = ["spmv", "spmvt", "trsv_L1", "trsv_L1t", "trsv_U", "trsv_Ut", "l2", "l2t", "vec",
@@ -161,6 +161,8 @@ def load(build_if_missing: bool = True):
             "rlsq_trsv_noalloc": (C.c_int, [P, i32, P, P, P]),
             "rlsq_setup_fuse": (C.c_int, [P, i32, i32, P]),
             "rlsq_setup_fused": (C.c_int, [P, i32, P, P, P]),
+            "rlsq_setup_add_rows": (C.c_int, [P, i64, P, P, P]),
+            "rlsq_setup_remove_rows": (C.c_int, [P, i64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -486,6 +488,22 @@ class HostSetup:
         lev = np.zeros(self.n, dtype=np.int32)
         _check(load().rlsq_setup_levels(self._h, int(which), _ptr(lev)[0]))
         return lev
+
+    def add_rows(self, rowptr, colidx, vals):
+        """Sec. 3.4: append rows (host CSR over the n columns) to A2."""
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(colidx, dtype=np.int32)
+        va = np.ascontiguousarray(vals, dtype=np.float64)
+        k = len(rp) - 1
+        _check(load().rlsq_setup_add_rows(self._h, k, _ptr(rp)[0], _ptr(ci if len(ci) else np.zeros(1, np.int32))[0],
+                                          _ptr(va if len(va) else np.zeros(1))[0]))
+        self.m += k
+
+    def remove_rows(self, ids):
+        """Sec. 3.4: remove rows of A2 (ascending ids); raises for a pivot row."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        _check(load().rlsq_setup_remove_rows(self._h, len(ids), _ptr(ids if len(ids) else np.zeros(1, np.int32))[0]))
+        self.m -= len(ids)
 
     def fuse(self, which: int, k: int):
         """Level fusion of one system (k >= 1 fixed groups, 0 chosen level by

@@ -5,6 +5,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "host_setup.h"
 #include "rlsq.h"
@@ -15,6 +16,7 @@ void set_last_error(const std::string& msg);
 
 struct rlsq_setup_s {
     rlsq::IlupResult F;
+    rlsq::IlupParams prm;   // the drop rule, reused when rows are added
     rlsq::MergedTri fused;  // the last rlsq_setup_fuse result
 };
 
@@ -92,6 +94,7 @@ int rlsq_setup_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t
         prm.small = o.small;
         prm.scale = o.scale_columns != 0;
         std::unique_ptr<rlsq_setup_s> s(new rlsq_setup_s());
+        s->prm = prm;
         try {
             s->F = rlsq::ilup_factor(A, prm);
         } catch (const std::runtime_error& e) {
@@ -191,6 +194,47 @@ int rlsq_setup_fused(rlsq_setup s, int32_t part, int64_t* ptr, int32_t* idx, dou
         std::memcpy(ptr, M.ptr.data(), M.ptr.size() * sizeof(int64_t));
         std::memcpy(idx, M.idx.data(), M.idx.size() * sizeof(int32_t));
         std::memcpy(val, M.val.data(), M.val.size() * sizeof(double));
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_setup_add_rows(rlsq_setup s, int64_t k, const int64_t* rowptr, const int32_t* colidx,
+                        const double* vals) {
+    return run([&]() -> int {
+        if (!s || !rowptr || (k > 0 && (!colidx || !vals))) throw SetupError(RLSQ_ERR_ARG, "null argument");
+        if (k < 0) throw SetupError(RLSQ_ERR_ARG, "k must be >= 0");
+        if (rowptr[0] != 0) throw SetupError(RLSQ_ERR_CSR, "rowptr[0] must be 0");
+        const int64_t n = s->F.n;
+        for (int64_t i = 0; i < k; ++i) {
+            if (rowptr[i + 1] < rowptr[i]) throw SetupError(RLSQ_ERR_CSR, "rowptr must be nondecreasing");
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                if (colidx[e] < 0 || colidx[e] >= n) throw SetupError(RLSQ_ERR_CSR, "column index out of range");
+                if (e > rowptr[i] && colidx[e] <= colidx[e - 1])
+                    throw SetupError(RLSQ_ERR_CSR, "column indices must be strictly increasing within a row");
+                if (!std::isfinite(vals[e])) throw SetupError(RLSQ_ERR_CSR, "non-finite value");
+            }
+        }
+        if (s->F.m + k >= (int64_t(1) << 31)) throw SetupError(RLSQ_ERR_SHAPE, "m must stay < 2^31");
+        rlsq::HostCSR rows;
+        rows.rows = k;
+        rows.cols = n;
+        rows.ptr.assign(rowptr, rowptr + k + 1);
+        rows.idx.assign(colidx, colidx + rowptr[k]);
+        rows.val.assign(vals, vals + rowptr[k]);
+        rlsq::add_rows(s->F, rows, s->prm);
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t* ids) {
+    return run([&]() -> int {
+        if (!s || (k > 0 && !ids) || k < 0) throw SetupError(RLSQ_ERR_ARG, "bad argument");
+        std::vector<int32_t> v(ids, ids + k);
+        try {
+            rlsq::remove_rows(s->F, v);
+        } catch (const std::invalid_argument& e) {
+            throw SetupError(RLSQ_ERR_ARG, e.what());
+        }
         return RLSQ_OK;
     });
 }

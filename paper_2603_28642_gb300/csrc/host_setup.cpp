@@ -556,6 +556,79 @@ MergedTri merge_levels_adaptive(const HostCSR& strict, const double* diag, const
     return M;
 }
 
+void add_rows(IlupResult& F, const HostCSR& rows, const IlupParams& prm) {
+    const int64_t n = F.n, k = rows.rows;
+    if (rows.cols != n) throw std::invalid_argument("added rows must have n columns");
+    std::vector<double> rhs(static_cast<size_t>(n)), l(static_cast<size_t>(n));
+    std::vector<Entry> cand;
+    HostCSR& L2 = F.L2;
+    for (int64_t t = 0; t < k; ++t) {
+        std::fill(rhs.begin(), rhs.end(), 0.0);
+        for (int64_t e = rows.ptr[t]; e < rows.ptr[t + 1]; ++e) {
+            const int32_t j = rows.idx[e];
+            if (j < 0 || j >= n) throw std::invalid_argument("column index out of range");
+            rhs[j] = rows.val[e] * F.d[j];
+        }
+        // U^T l = rhs: rows of Ut are positions, entries ascending, then the pivot
+        for (int64_t i = 0; i < n; ++i) {
+            double s = rhs[i];
+            for (int64_t e = F.Ut.ptr[i]; e < F.Ut.ptr[i + 1]; ++e) s = s - F.Ut.val[e] * l[F.Ut.idx[e]];
+            l[i] = s / F.Udiag[i];
+        }
+        cand.clear();
+        for (int64_t q = 0; q < n; ++q)
+            if (l[q] != 0.0) cand.push_back({std::fabs(l[q]), static_cast<int32_t>(q), l[q]});
+        dual_drop(cand, prm.p, prm.tau);
+        for (const Entry& c : cand) {
+            L2.idx.push_back(c.key);
+            L2.val.push_back(c.val);
+        }
+        L2.ptr.push_back(static_cast<int64_t>(L2.idx.size()));
+        F.a2rows.push_back(static_cast<int32_t>(F.m + t));
+    }
+    L2.rows += k;
+    F.m += k;
+    F.L2t = transpose(L2);
+}
+
+void remove_rows(IlupResult& F, const std::vector<int32_t>& ids) {
+    const int64_t m = F.m;
+    std::vector<char> gone(static_cast<size_t>(m), 0);
+    std::vector<char> pivot(static_cast<size_t>(m), 0);
+    for (const int32_t r : F.prow) pivot[static_cast<size_t>(r)] = 1;
+    for (size_t t = 0; t < ids.size(); ++t) {
+        const int32_t r = ids[t];
+        if (r < 0 || r >= m || (t > 0 && r <= ids[t - 1]))
+            throw std::invalid_argument("row ids must be ascending, distinct and in range");
+        if (pivot[static_cast<size_t>(r)]) throw std::invalid_argument("a pivot row cannot be removed without refactorising");
+        gone[static_cast<size_t>(r)] = 1;
+    }
+    std::vector<int32_t> newid(static_cast<size_t>(m), -1);
+    int32_t next = 0;
+    for (int64_t i = 0; i < m; ++i)
+        if (!gone[static_cast<size_t>(i)]) newid[static_cast<size_t>(i)] = next++;
+    HostCSR L2;
+    L2.cols = F.L2.cols;
+    L2.ptr.push_back(0);
+    std::vector<int32_t> a2;
+    for (size_t c = 0; c < F.a2rows.size(); ++c) {
+        const int32_t orig = F.a2rows[c];
+        if (gone[static_cast<size_t>(orig)]) continue;
+        for (int64_t e = F.L2.ptr[c]; e < F.L2.ptr[c + 1]; ++e) {
+            L2.idx.push_back(F.L2.idx[e]);
+            L2.val.push_back(F.L2.val[e]);
+        }
+        L2.ptr.push_back(static_cast<int64_t>(L2.idx.size()));
+        a2.push_back(newid[static_cast<size_t>(orig)]);
+    }
+    L2.rows = static_cast<int64_t>(a2.size());
+    for (auto& r : F.prow) r = newid[static_cast<size_t>(r)];
+    F.L2 = std::move(L2);
+    F.L2t = transpose(F.L2);
+    F.a2rows = std::move(a2);
+    F.m = m - static_cast<int64_t>(ids.size());
+}
+
 bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads) {
     const int64_t n = f.n, m2 = f.m - f.n;
     if (m2 <= 0) {

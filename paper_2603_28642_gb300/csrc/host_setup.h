@@ -58,6 +58,18 @@ struct IlupResult {
     Levels lev_L1, lev_L1t, lev_U, lev_Ut;
 };
 
+// Sec. 3.4, adding rows: every row of `rows` (n columns, the user's values)
+// joins A2 with the ids m, m+1, ...; its L2 row l solves l U = a D (a lower
+// solve with U^T in position order), dropped like an L column of Algorithm 4
+// (|l| >= tau, then at most p of the largest).  L1, U, D and the pivots are
+// unchanged; L2^T is rebuilt.
+void add_rows(IlupResult& F, const HostCSR& rows, const IlupParams& prm);
+// Sec. 3.4, removing rows of A2 (ids ascending and distinct): their L2 rows
+// go and the remaining rows are renumbered in order.  Throws
+// std::invalid_argument for a pivot row or a bad id (a refactorisation is
+// needed then).
+void remove_rows(IlupResult& F, const std::vector<int32_t>& ids);
+
 // Column scaling d_j = 1 / ||A_:,j||_2.  Returns false if a column is empty.
 bool column_scaling(const HostCSR& a, std::vector<double>& d);
 
