@@ -240,6 +240,17 @@ int rlsq_get_factor(rlsq_problem h, int32_t part, int64_t *ptr, int32_t *idx, do
 /* Level of every row of system RLSQ_SYS_* (length n). */
 int rlsq_get_levels(rlsq_problem h, int32_t which, int32_t *level);
 
+/* Sec. 3.4 on a factored handle (no counterpart in the paper beyond that
+   section): add k rows (host CSR over the n columns; they join A2 with ids
+   m .. m+k-1 and get L2 rows l with l U = a D, dropped by the factor's rule),
+   or remove rows of A2 (ids ascending and distinct; the rest are renumbered in
+   order).  L1 and U are kept; A's device copy, the m-sized vectors and the
+   device factor are rebuilt with the handle's factor options (autotuning
+   again if it was on).  b of later solves has the new m.  Not while the
+   handle is registered with a server.  Errors: ARG (a pivot row cannot be
+   removed: refactorise), CSR, SHAPE, NOT_FACTORED, OOM, CUDA. */
+int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t *rowptr, const int32_t *colidx, const double *vals);
+int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t *ids);
 void rlsq_destroy(rlsq_problem h);
 
 /* ---- continuous-batching server ------------------------------------------ */

@@ -104,6 +104,7 @@ EXPORTS = [
     "rlsq_setup_create", "rlsq_setup_sizes", "rlsq_setup_split", "rlsq_setup_factor",
     "rlsq_setup_levels", "rlsq_setup_destroy", "rlsq_profile", "rlsq_trsv_noalloc",
     "rlsq_setup_fuse", "rlsq_setup_fused", "rlsq_setup_add_rows", "rlsq_setup_remove_rows",
+    "rlsq_add_rows", "rlsq_remove_rows",
 ]
 
 KCLASS = ["spmv", "spmvt", "trsv_L1", "trsv_L1t", "trsv_U", "trsv_Ut", "l2", "l2t", "vec",
@@ -163,6 +164,8 @@ def load(build_if_missing: bool = True):
             "rlsq_setup_fused": (C.c_int, [P, i32, P, P, P]),
             "rlsq_setup_add_rows": (C.c_int, [P, i64, P, P, P]),
             "rlsq_setup_remove_rows": (C.c_int, [P, i64, P]),
+            "rlsq_add_rows": (C.c_int, [P, i64, P, P, P]),
+            "rlsq_remove_rows": (C.c_int, [P, i64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -263,6 +266,24 @@ class Problem:
     def factor(self, **kw):
         o = factor_opts(**kw)
         _check(load().rlsq_factor(self._h, C.byref(o)))
+        return self.info()
+
+    def add_rows(self, rowptr, colidx, vals):
+        """Sec. 3.4: append rows (host CSR over the n columns) without refactorising."""
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(colidx, dtype=np.int32)
+        va = np.ascontiguousarray(vals, dtype=np.float64)
+        k = len(rp) - 1
+        _check(load().rlsq_add_rows(self._h, k, _ptr(rp)[0], _ptr(ci if len(ci) else np.zeros(1, np.int32))[0],
+                                    _ptr(va if len(va) else np.zeros(1))[0]))
+        self.m += k
+        return self.info()
+
+    def remove_rows(self, ids):
+        """Sec. 3.4: remove rows of A2 (ascending ids) without refactorising."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        _check(load().rlsq_remove_rows(self._h, len(ids), _ptr(ids if len(ids) else np.zeros(1, np.int32))[0]))
+        self.m -= len(ids)
         return self.info()
 
     def info(self) -> dict:

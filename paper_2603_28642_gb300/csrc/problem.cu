@@ -1208,6 +1208,96 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
     });
 }
 
+// Sec. 3.4 on a GPU handle: the host factor is updated (rows join A2 / A2
+// rows leave, L1 and U kept), then A's device layout, the m-sized vectors and
+// the device factor are rebuilt with the handle's own options (rlsq_factor
+// finds the ILUP parameters unchanged and keeps the updated host factor).
+static void refresh_after_rows(rlsq_problem_s* h) {
+    cudaStream_t st = h->stream;
+    h->m = h->A.rows;
+    h->nnz = h->A.nnz();
+    const int64_t thr = h->opts.dense_row_min != 0 ? h->opts.dense_row_min : auto_dense_threshold(h->A);
+    layout_A(h, thr);
+    h->qr.alloc(static_cast<size_t>(h->m));
+    h->b.alloc(static_cast<size_t>(h->m));
+    RLSQ_CUDA(cudaStreamSynchronize(st));
+    h->anorm = power_norm(h, 50);
+    const rlsq_factor_opts o = h->opts;
+    const int code = rlsq_factor(h, &o);
+    if (code != RLSQ_OK) throw ApiError(code, "refactor after the row update failed");
+}
+
+int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t* rowptr, const int32_t* colidx, const double* vals) {
+    return guarded([&]() -> int {
+        if (!h || !rowptr || (k > 0 && (!colidx || !vals)) || k < 0) throw ApiError(RLSQ_ERR_ARG, "bad argument");
+        if (!h->factored || !h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        if (rowptr[0] != 0) throw ApiError(RLSQ_ERR_CSR, "rowptr[0] must be 0");
+        const int64_t n = h->n;
+        for (int64_t i = 0; i < k; ++i) {
+            if (rowptr[i + 1] < rowptr[i]) throw ApiError(RLSQ_ERR_CSR, "rowptr must be nondecreasing");
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                if (colidx[e] < 0 || colidx[e] >= n) throw ApiError(RLSQ_ERR_CSR, "column index out of range");
+                if (e > rowptr[i] && colidx[e] <= colidx[e - 1])
+                    throw ApiError(RLSQ_ERR_CSR, "column indices must be strictly increasing within a row");
+                if (!std::isfinite(vals[e])) throw ApiError(RLSQ_ERR_CSR, "non-finite value");
+            }
+        }
+        if (h->m + k >= (int64_t(1) << 31) || h->A.nnz() + rowptr[k] >= (int64_t(1) << 31))
+            throw ApiError(RLSQ_ERR_SHAPE, "sizes must stay < 2^31");
+        HostCSR rows;
+        rows.rows = k;
+        rows.cols = n;
+        rows.ptr.assign(rowptr, rowptr + k + 1);
+        rows.idx.assign(colidx, colidx + rowptr[k]);
+        rows.val.assign(vals, vals + rowptr[k]);
+        IlupParams prm;
+        prm.p = h->opts.p;
+        prm.tau = h->opts.tau;
+        prm.mu = h->opts.mu;
+        prm.small = h->opts.small;
+        prm.scale = h->opts.scale_columns != 0;
+        add_rows(*h->F, rows, prm);
+        HostCSR& A = h->A;
+        const int64_t base = A.nnz();
+        for (int64_t i = 0; i < k; ++i) A.ptr.push_back(base + rowptr[i + 1]);
+        A.idx.insert(A.idx.end(), rows.idx.begin(), rows.idx.end());
+        A.val.insert(A.val.end(), rows.val.begin(), rows.val.end());
+        A.rows += k;
+        refresh_after_rows(h);
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t* ids) {
+    return guarded([&]() -> int {
+        if (!h || (k > 0 && !ids) || k < 0) throw ApiError(RLSQ_ERR_ARG, "bad argument");
+        if (!h->factored || !h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        std::vector<int32_t> v(ids, ids + k);
+        try {
+            remove_rows(*h->F, v);
+        } catch (const std::invalid_argument& e) {
+            throw ApiError(RLSQ_ERR_ARG, e.what());
+        }
+        HostCSR& A = h->A;
+        HostCSR B;
+        B.cols = A.cols;
+        B.ptr.push_back(0);
+        size_t t = 0;
+        for (int64_t i = 0; i < A.rows; ++i) {
+            if (t < v.size() && v[t] == i) { ++t; continue; }
+            for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+                B.idx.push_back(A.idx[e]);
+                B.val.push_back(A.val[e]);
+            }
+            B.ptr.push_back(static_cast<int64_t>(B.idx.size()));
+        }
+        B.rows = A.rows - static_cast<int64_t>(v.size());
+        h->A = std::move(B);
+        refresh_after_rows(h);
+        return RLSQ_OK;
+    });
+}
+
 int rlsq_solve(rlsq_problem h, const double* b, double* x, const rlsq_solve_opts* opts, rlsq_info* info) {
     return guarded([&]() -> int {
         if (!h) throw ApiError(RLSQ_ERR_ARG, "null handle");
