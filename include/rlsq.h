@@ -115,7 +115,11 @@ typedef struct {
     int64_t dense_row_min; /* rows of A with at least this many nonzeros are kept as dense
                               rows and multiplied by a dense-row GEMV block; 0 = automatic,
                               < 0 = never */
-    int32_t host_threads;  /* threads for the dense S set-up (0 = hardware concurrency) */
+    int32_t host_threads;  /* host threads of the set-up: the ILUP column loop (pipelined over
+                              columns, the same factor bit for bit for any count) and the dense
+                              S; <= 0 = hardware concurrency (the ILUP takes at most 8, and
+                              fewer where its per-thread arrays, 16 bytes per row of A, would
+                              pass 2 GiB) */
     int32_t level_merge;   /* levels fused per group in the triangular solves: 1 = none,
                               k > 1 = groups of k levels (same-group dependencies are
                               substituted on the host), 0 = chosen per system by a
@@ -340,11 +344,15 @@ int rlsq_trsv_noalloc(rlsq_problem h, int32_t which, const double *b, double *x,
  * its own: column scaling (Sec. 5.1), ILUP(p, tau) with threshold pivoting
  * (Algorithms 4-6), the split P A D ~ [L1; L2] U (eq. 3.8) and the level
  * sets of L1, L1^T, U, U^T.  Inputs are host CSR arrays (copied); only
- * opts->p, tau, mu, small and scale_columns are used.  Errors: ARG, SHAPE,
- * CSR, RANK. */
+ * opts->p, tau, mu, small, scale_columns and host_threads are used.  Errors:
+ * ARG, SHAPE, CSR, RANK. */
 typedef struct rlsq_setup_s *rlsq_setup;
 int rlsq_setup_create(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
                       const double *vals, const rlsq_factor_opts *opts, rlsq_setup *out);
+/* Host threads the ILUP column loop of an m x n set-up takes when
+   host_threads = requested (the rule of rlsq_factor_opts.host_threads; the
+   factor does not depend on it).  Never fails; returns >= 1. */
+int32_t rlsq_setup_threads(int32_t requested, int64_t m, int64_t n);
 /* sizes[0..7] = nnz(L1 strict), nnz(L2), nnz(U strict), nmod,
    levels of L1, L1^T, U, U^T */
 int rlsq_setup_sizes(rlsq_setup s, int64_t *sizes);

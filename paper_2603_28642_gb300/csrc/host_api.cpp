@@ -93,6 +93,7 @@ int rlsq_setup_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t
         prm.mu = o.mu;
         prm.small = o.small;
         prm.scale = o.scale_columns != 0;
+        prm.threads = rlsq::ilup_threads(o.host_threads, m, n);
         std::unique_ptr<rlsq_setup_s> s(new rlsq_setup_s());
         s->prm = prm;
         try {
@@ -103,6 +104,10 @@ int rlsq_setup_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t
         *out = s.release();
         return RLSQ_OK;
     });
+}
+
+int32_t rlsq_setup_threads(int32_t requested, int64_t m, int64_t n) {
+    return rlsq::ilup_threads(requested, m, n);
 }
 
 int rlsq_setup_sizes(rlsq_setup s, int64_t* sizes) {

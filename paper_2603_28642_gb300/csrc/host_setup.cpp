@@ -8,7 +8,9 @@
 // nonzeros of A(:, j) (the pattern of U(1:j-1, j)), the positions are sorted
 // ascending (a topological order because L is unit lower triangular in pivot
 // order), and the sparse triangular solve then updates the not-yet-pivoted
-// rows at the same time, which yields the L part of step 7.
+// rows at the same time, which yields the L part of step 7.  With more than
+// one thread the column loop is pipelined over consecutive columns
+// (columns_pipelined below); the factor is the same bit for bit.
 //
 // Readings of points the paper leaves open:
 //  * rc(i) at step j counts the nonzeros of the original scaled matrix in row
@@ -23,8 +25,11 @@
 #include "host_setup.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <exception>
+#include <functional>
+#include <memory>
 #include <stdexcept>
 #include <thread>
 
@@ -118,25 +123,29 @@ Levels analyse_levels(const HostCSR& s, bool lower) {
     return L;
 }
 
-IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
+namespace {
+
+// Columns of L (original row ids, multipliers) and of U (pivot positions,
+// values) in the order Algorithm 4 produces them, and the pivot position of
+// every row (-1: a row of A2).
+struct ColumnFactor {
+    std::vector<int64_t> Lp, Up;
+    std::vector<int32_t> Li, Ui;
+    std::vector<double> Lv, Uv;
+    std::vector<int32_t> pivpos;
+};
+
+// Algorithm 6: the magnitude a modified pivot of column j (0-based) gets.
+double modified_pivot(double colinf, int64_t j, int64_t n, double small) {
+    const double beta = std::pow(10.0, -2.0 * (1.0 - static_cast<double>(j + 1) / static_cast<double>(n)));
+    double modval = beta * colinf;
+    if (modval < small) modval = small;
+    return modval;
+}
+
+// Column by column on one thread.
+void columns_serial(const HostCSR& a, const HostCSR& ac, const IlupParams& prm, IlupResult& R, ColumnFactor& C) {
     const int64_t m = a.rows, n = a.cols;
-    if (!(m > n && n > 0)) throw std::runtime_error("need m > n > 0");
-    IlupResult R;
-    R.m = m;
-    R.n = n;
-    if (prm.scale) {
-        if (!column_scaling(a, R.d)) throw std::runtime_error("A has an empty column");
-    } else {
-        R.d.assign(static_cast<size_t>(n), 1.0);
-    }
-
-    // scaled matrix by columns, rows ascending in each column
-    HostCSR ac = transpose(a);
-    for (int64_t j = 0; j < n; ++j) {
-        if (ac.ptr[j + 1] == ac.ptr[j]) throw std::runtime_error("A has an empty column");
-        for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) ac.val[e] = ac.val[e] * R.d[j];
-    }
-
     std::vector<int32_t> rc(static_cast<size_t>(m));
     for (int64_t i = 0; i < m; ++i) rc[i] = static_cast<int32_t>(a.ptr[i + 1] - a.ptr[i]);
 
@@ -149,13 +158,15 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         int32_t piv;
     };
     std::vector<RowState> rows(static_cast<size_t>(m), RowState{0.0, -1, -1});
-    R.prow.assign(static_cast<size_t>(n), -1);
-    R.Udiag.assign(static_cast<size_t>(n), 0.0);
 
-    // columns of L (original row id, multiplier) and of U (pivot position, value)
-    std::vector<int64_t> Lp(static_cast<size_t>(n) + 1, 0), Up(static_cast<size_t>(n) + 1, 0);
-    std::vector<int32_t> Li, Ui;
-    std::vector<double> Lv, Uv;
+    std::vector<int64_t>& Lp = C.Lp;
+    std::vector<int64_t>& Up = C.Up;
+    std::vector<int32_t>& Li = C.Li;
+    std::vector<int32_t>& Ui = C.Ui;
+    std::vector<double>& Lv = C.Lv;
+    std::vector<double>& Uv = C.Uv;
+    Lp.assign(static_cast<size_t>(n) + 1, 0);
+    Up.assign(static_cast<size_t>(n) + 1, 0);
     const size_t guess = static_cast<size_t>(n) * static_cast<size_t>(prm.p >= 0 ? prm.p : 16);
     Li.reserve(guess);
     Lv.reserve(guess);
@@ -307,12 +318,356 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) rc[ac.idx[e]]--;
     }
 
-    // split: pivot rows in pivot order form L1, the rest (ascending id) L2
+    C.pivpos.resize(static_cast<size_t>(m));
+    for (int64_t i = 0; i < m; ++i) C.pivpos[i] = rows[i].piv;
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined columns.  Column c's triangular solve over the pivot positions
+// k < c - W + 1 uses only columns that are final once column c - W is, so W
+// threads each take every W-th column and run that part of W consecutive
+// columns at the same time, in working arrays of their own.  Each then waits
+// for column c - 1 to be final and finishes column c itself: the remaining
+// positions c - W + 1 .. c - 1 (in ascending order, after all smaller ones,
+// as the serial solve takes them), the U drop, the pivot choice and the L
+// part.  Every floating-point operation happens on the same operands in the
+// same order as in the serial loop, so the factor is the same bit for bit.
+
+struct Touched {
+    double x;     // value of the row in this column
+    int32_t row;  // original row id
+    int32_t out;  // 1: pivoted (at a position above the horizon, or here)
+};
+
+// A worker's view of one row, one 16-byte record so a random row access
+// costs one cache line.  During the worker's solve `x` is the row's working
+// value; afterwards, for a row listed in `act`, it holds the row's index
+// there.  `piv` is the row's pivot position if it is below the worker's
+// horizon, else -1.
+struct WorkerRow {
+    double x;
+    int32_t mark;  // column that last touched the row
+    int32_t piv;
+};
+
+// The p + 1 largest magnitudes seen, largest first (a multiset).
+struct TopMags {
+    std::vector<double> v;
+    size_t cap = 0;
+    void reset(size_t k) {
+        v.clear();
+        cap = k;
+    }
+    void add(double g) {
+        if (cap == 0) return;
+        if (v.size() == cap) {
+            if (!(g > v.back())) return;
+            v.pop_back();
+        }
+        size_t i = v.size();
+        v.push_back(g);
+        for (; i > 0 && v[i - 1] < g; --i) v[i] = v[i - 1];
+        v[i] = g;
+    }
+    void remove_one(double g) {
+        for (size_t i = 0; i < v.size(); ++i)
+            if (v[i] == g) {
+                v.erase(v.begin() + static_cast<std::ptrdiff_t>(i));
+                return;
+            }
+    }
+};
+
+struct Worker {
+    std::vector<WorkerRow> rows;
+    std::vector<int32_t> vmark;  // column that queued the pivot position
+    std::vector<int32_t> heap;
+    std::vector<Touched> act;    // touched rows not pivoted below the horizon
+    std::vector<Entry> cand;     // U part, ascending position
+    std::vector<Entry> lc;       // L part
+    TopMags top;
+    int64_t applied = 0;         // pivot positions copied into rows[].piv
+};
+
+struct alignas(64) PaddedCounter {
+    std::atomic<int64_t> v{0};
+};
+
+class Aborted {};
+
+template <class Ready>
+void wait_for(Ready ready, const std::atomic<bool>& abort) {
+    for (int spin = 0; !ready(); ++spin) {
+        if (abort.load(std::memory_order_relaxed)) throw Aborted();
+        if (spin > 64) std::this_thread::yield();
+    }
+}
+
+// Keep the entries of `c` (those not out and nonzero) that dual_drop keeps
+// when each becomes {|x / pv|, row, x / pv}, dividing only the candidates
+// that can be kept.  `xp` is the p-th largest |x| among them (0 if there are
+// at most p).  x -> fl(x / pv) is monotone in |x|, so an entry clearly
+// smaller in |x| than the p-th largest is clearly smaller after the division.
+void drop_scaled(const std::vector<Touched>& c, double pv, double xp, int p, double tau, std::vector<Entry>& out) {
+    out.clear();
+    if (p == 0 || c.empty()) return;
+    double lo = 0.0;
+    // the margin is far above the quotients' rounding; it is not used where a
+    // quotient could be subnormal
+    if (xp > 0.0 && xp / std::fabs(pv) > 1e-290) lo = xp * (1.0 - 0x1p-40);
+    for (const Touched& t : c)
+        if (!t.out && t.x != 0.0 && std::fabs(t.x) >= lo) {
+            const double l = t.x / pv;
+            out.push_back({std::fabs(l), t.row, l});
+        }
+    dual_drop(out, p, tau);
+}
+
+void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& prm, int nthreads, IlupResult& R,
+                       ColumnFactor& C) {
+    const int64_t m = a.rows, n = a.cols;
+    const int64_t W = nthreads;
+    const size_t cap = static_cast<size_t>(n) * static_cast<size_t>(prm.p);
+    // L storage is appended to while other threads read finished columns,
+    // so it never moves: each column keeps at most p entries.
+    std::unique_ptr<int32_t[]> Li(new int32_t[cap > 0 ? cap : 1]);
+    std::unique_ptr<double[]> Lv(new double[cap > 0 ? cap : 1]);
+    std::vector<int64_t>& Lp = C.Lp;
+    std::vector<int64_t>& Up = C.Up;
+    Lp.assign(static_cast<size_t>(n) + 1, 0);
+    Up.assign(static_cast<size_t>(n) + 1, 0);
+    C.Ui.reserve(cap);
+    C.Uv.reserve(cap);
+    std::vector<int32_t>& piv = C.pivpos;  // touched only while finishing a column
+    piv.assign(static_cast<size_t>(m), -1);
+    std::vector<int32_t> rc(static_cast<size_t>(m));
+    for (int64_t i = 0; i < m; ++i) rc[i] = static_cast<int32_t>(a.ptr[i + 1] - a.ptr[i]);
+
+    std::vector<std::unique_ptr<Worker>> ws;
+    for (int64_t w = 0; w < W; ++w) {
+        std::unique_ptr<Worker> k(new Worker());
+        k->rows.assign(static_cast<size_t>(m), WorkerRow{0.0, -1, -1});
+        k->vmark.assign(static_cast<size_t>(n), -1);
+        ws.push_back(std::move(k));
+    }
+    PaddedCounter done;  // columns final
+    std::atomic<bool> abort{false};
+    const int32_t* prow = R.prow.data();
+    const auto heap_after = std::greater<int32_t>();
+
+    // column c's solve over the positions k < c - W + 1, ascending
+    auto solve_below_horizon = [&](Worker& K, int64_t cc) {
+        const int32_t c = static_cast<int32_t>(cc);
+        const int64_t horizon = cc - W + 1;
+        WorkerRow* rw = K.rows.data();
+        for (; K.applied < horizon; ++K.applied) rw[prow[K.applied]].piv = static_cast<int32_t>(K.applied);
+        K.act.clear();
+        K.cand.clear();
+        K.heap.clear();
+        for (int64_t e = ac.ptr[c]; e < ac.ptr[c + 1]; ++e) {
+            const int32_t i = ac.idx[e];
+            WorkerRow& r = rw[i];
+            r.x = ac.val[e];
+            r.mark = c;
+            if (r.piv >= 0) {
+                if (K.vmark[r.piv] != c) {
+                    K.vmark[r.piv] = c;
+                    K.heap.push_back(r.piv);
+                }
+            } else {
+                K.act.push_back({0.0, i, 0});
+            }
+        }
+        std::make_heap(K.heap.begin(), K.heap.end(), heap_after);
+        while (!K.heap.empty()) {
+            std::pop_heap(K.heap.begin(), K.heap.end(), heap_after);
+            const int32_t k = K.heap.back();
+            K.heap.pop_back();
+            const double ukj = rw[prow[k]].x;
+            if (ukj == 0.0) continue;
+            K.cand.push_back({std::fabs(ukj), k, ukj});
+            const int64_t e1 = Lp[k + 1];
+            for (int64_t e = Lp[k]; e < e1; ++e) {
+                const int32_t i = Li[e];
+                WorkerRow& r = rw[i];
+                if (r.mark != c) {
+                    r.mark = c;
+                    r.x = 0.0;
+                    const int32_t q = r.piv;
+                    if (q >= 0) {
+                        if (K.vmark[q] != c) {
+                            K.vmark[q] = c;
+                            K.heap.push_back(q);
+                            std::push_heap(K.heap.begin(), K.heap.end(), heap_after);
+                            __builtin_prefetch(&Li[Lp[q]]);
+                            __builtin_prefetch(&Lv[Lp[q]]);
+                        }
+                    } else {
+                        K.act.push_back({0.0, i, 0});
+                    }
+                }
+                r.x = r.x - Lv[e] * ukj;
+            }
+        }
+        for (size_t s = 0; s < K.act.size(); ++s) {
+            WorkerRow& r = rw[K.act[s].row];
+            K.act[s].x = r.x;
+            r.x = static_cast<double>(s);
+        }
+    };
+
+    // the rest of column j, once columns 0 .. j-1 are final
+    auto finish_column = [&](Worker& K, int64_t jj) {
+        const int32_t j = static_cast<int32_t>(jj);
+        WorkerRow* rw = K.rows.data();
+        // the positions above the horizon, ascending
+        for (int64_t k = std::max<int64_t>(jj - W + 1, 0); k < jj; ++k) {
+            const WorkerRow& pr = rw[prow[k]];
+            if (pr.mark != j) continue;
+            Touched& tr = K.act[static_cast<size_t>(pr.x)];
+            tr.out = 1;
+            const double ukj = tr.x;
+            if (ukj == 0.0) continue;
+            K.cand.push_back({std::fabs(ukj), static_cast<int32_t>(k), ukj});
+            for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
+                const int32_t i = Li[e];
+                WorkerRow& r = rw[i];
+                if (r.mark != j) {
+                    r.mark = j;
+                    r.x = static_cast<double>(K.act.size());
+                    K.act.push_back({0.0, i, 0});
+                }
+                Touched& t = K.act[static_cast<size_t>(r.x)];
+                t.x = t.x - Lv[e] * ukj;
+            }
+        }
+        dual_drop(K.cand, prm.p, prm.tau);
+        for (const Entry& c : K.cand) {
+            C.Ui.push_back(c.key);
+            C.Uv.push_back(c.val);
+        }
+        Up[j + 1] = static_cast<int64_t>(C.Ui.size());
+
+        // pivot choice (Algorithms 5 and 6) among the unpivoted nonzeros
+        K.top.reset(static_cast<size_t>(prm.p) + 1);
+        double maxabs = 0.0, gate = -1.0;
+        size_t neligible = 0;
+        for (const Touched& t : K.act)
+            if (!t.out && t.x != 0.0) {
+                ++neligible;
+                const double g = std::fabs(t.x);
+                maxabs = std::max(maxabs, g);
+                if (g > gate) {
+                    K.top.add(g);
+                    if (K.top.v.size() == K.top.cap) gate = K.top.v.back();
+                }
+            }
+        double colinf = 0.0;
+        for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) colinf = std::max(colinf, std::fabs(ac.val[e]));
+        const double modval = modified_pivot(colinf, jj, n, prm.small);
+        int32_t r = -1;
+        double pv;
+        if (neligible == 0) {
+            for (int64_t i = 0; i < m; ++i)
+                if (piv[i] < 0 && (r < 0 || rc[i] < rc[r])) r = static_cast<int32_t>(i);
+            pv = modval;
+            R.nmod++;
+        } else {
+            const double thr = prm.mu * maxabs;
+            double rmag = 0.0;
+            size_t rslot = 0;
+            for (size_t s = 0; s < K.act.size(); ++s) {
+                const Touched& t = K.act[s];
+                const double mag = std::fabs(t.x);
+                if (t.out || t.x == 0.0 || !(mag >= thr)) continue;
+                const int32_t i = t.row;
+                bool take = r < 0;
+                if (!take) {
+                    if (rc[i] != rc[r]) take = rc[i] < rc[r];
+                    else if (mag != rmag) take = mag > rmag;
+                    else take = i < r;
+                }
+                if (take) {
+                    r = i;
+                    rmag = mag;
+                    rslot = s;
+                }
+            }
+            pv = K.act[rslot].x;
+            if (std::fabs(pv) < prm.small) {
+                pv = (pv < 0.0) ? -modval : modval;
+                R.nmod++;
+            }
+            K.act[rslot].out = 1;
+            --neligible;
+            if (K.top.v.size() == K.top.cap && rmag < K.top.v.back()) K.top.v.pop_back();
+            else K.top.remove_one(rmag);
+        }
+        R.Udiag[j] = pv;
+        R.prow[j] = r;
+        piv[r] = j;
+
+        // L part: scale by the pivot, then drop
+        const double xp = (prm.p > 0 && neligible > static_cast<size_t>(prm.p))
+                              ? K.top.v[static_cast<size_t>(prm.p) - 1] : 0.0;
+        drop_scaled(K.act, pv, xp, prm.p, prm.tau, K.lc);
+        int64_t at = Lp[j];
+        for (const Entry& c : K.lc) {
+            Li[at] = c.key;
+            Lv[at] = c.val;
+            ++at;
+        }
+        Lp[j + 1] = at;
+
+        for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) rc[ac.idx[e]]--;
+    };
+
+    std::vector<std::exception_ptr> errs(static_cast<size_t>(W));
+    auto run = [&](int64_t w) {
+        Worker& K = *ws[static_cast<size_t>(w)];
+        try {
+            for (int64_t c = w; c < n; c += W) {
+                wait_for([&]() { return done.v.load(std::memory_order_acquire) >= c - W + 1; }, abort);
+                solve_below_horizon(K, c);
+                wait_for([&]() { return done.v.load(std::memory_order_acquire) >= c; }, abort);
+                finish_column(K, c);
+                done.v.store(c + 1, std::memory_order_release);
+            }
+        } catch (const Aborted&) {
+        } catch (...) {
+            errs[static_cast<size_t>(w)] = std::current_exception();
+            abort.store(true);
+        }
+    };
+    std::vector<std::thread> threads;
+    try {
+        for (int64_t w = 1; w < W; ++w) threads.emplace_back(run, w);
+    } catch (...) {
+        abort.store(true);
+        for (auto& t : threads) t.join();
+        throw;
+    }
+    run(0);
+    for (auto& t : threads) t.join();
+    for (const auto& e : errs)
+        if (e) std::rethrow_exception(e);
+
+    C.Li.assign(Li.get(), Li.get() + Lp[n]);
+    C.Lv.assign(Lv.get(), Lv.get() + Lp[n]);
+}
+
+// The split (pivot rows in pivot order form L1, the rest in ascending id L2),
+// U by rows, the transposes and the level sets.
+void split_and_analyse(IlupResult& R, const ColumnFactor& C) {
+    const int64_t m = R.m, n = R.n;
     const int64_t m2 = m - n;
-    std::vector<int32_t> pivpos(static_cast<size_t>(m));
-    for (int64_t i = 0; i < m; ++i) pivpos[i] = rows[i].piv;
-    rows.clear();
-    rows.shrink_to_fit();
+    const std::vector<int32_t>& pivpos = C.pivpos;
+    const std::vector<int64_t>& Lp = C.Lp;
+    const std::vector<int64_t>& Up = C.Up;
+    const std::vector<int32_t>& Li = C.Li;
+    const std::vector<int32_t>& Ui = C.Ui;
+    const std::vector<double>& Lv = C.Lv;
+    const std::vector<double>& Uv = C.Uv;
     std::vector<int32_t> a2idx(static_cast<size_t>(m), -1);
     R.a2rows.reserve(static_cast<size_t>(m2));
     for (int64_t i = 0; i < m; ++i)
@@ -400,6 +755,46 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         for (const auto& e : {e0, e1, e2})
             if (e) std::rethrow_exception(e);
     }
+}
+
+}  // namespace
+
+int ilup_threads(int requested, int64_t m, int64_t n) {
+    int64_t t = requested > 0 ? std::min(requested, 64)
+                              : std::min<int64_t>(8, std::max(1u, std::thread::hardware_concurrency()));
+    const int64_t per = 16 * std::max<int64_t>(m, 1) + 4 * std::max<int64_t>(n, 1);
+    t = std::min<int64_t>(t, std::max<int64_t>(1, (int64_t(1) << 31) / per));
+    return static_cast<int>(t);
+}
+
+IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
+    const int64_t m = a.rows, n = a.cols;
+    if (!(m > n && n > 0)) throw std::runtime_error("need m > n > 0");
+    IlupResult R;
+    R.m = m;
+    R.n = n;
+    if (prm.scale) {
+        if (!column_scaling(a, R.d)) throw std::runtime_error("A has an empty column");
+    } else {
+        R.d.assign(static_cast<size_t>(n), 1.0);
+    }
+
+    // scaled matrix by columns, rows ascending in each column
+    HostCSR ac = transpose(a);
+    for (int64_t j = 0; j < n; ++j) {
+        if (ac.ptr[j + 1] == ac.ptr[j]) throw std::runtime_error("A has an empty column");
+        for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) ac.val[e] = ac.val[e] * R.d[j];
+    }
+    R.prow.assign(static_cast<size_t>(n), -1);
+    R.Udiag.assign(static_cast<size_t>(n), 0.0);
+
+    ColumnFactor C;
+    // The pipeline needs a bound on the entries of an L column (p >= 0).
+    if (prm.p >= 0 && prm.threads > 1)
+        columns_pipelined(a, ac, prm, prm.threads, R, C);
+    else
+        columns_serial(a, ac, prm, R, C);
+    split_and_analyse(R, C);
     return R;
 }
 

@@ -33,6 +33,7 @@ struct IlupParams {
     double mu = 0.1;     // threshold pivoting parameter (Algorithm 5)
     double small = 1e-10;// smallest admissible |U_jj| (Algorithm 6)
     bool scale = true;   // prescale columns to unit 2-norm
+    int threads = 1;     // threads of the column loop; > 1 pipelines it (same factor bit for bit)
 };
 
 // Level structure of one triangular system: level of every row, rows sorted
@@ -75,6 +76,11 @@ bool column_scaling(const HostCSR& a, std::vector<double>& d);
 
 // Full set-up.  Throws std::runtime_error with a message on bad input.
 IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm);
+
+// Threads for the column loop of an m x n factorisation: `requested` if > 0
+// (at most 64), else the hardware concurrency (at most 8); fewer where the
+// per-thread row arrays (16 bytes per row of A, 4 per column) would pass 2 GiB.
+int ilup_threads(int requested, int64_t m, int64_t n);
 
 // lower = true: row i depends on k < i; otherwise on k > i.
 Levels analyse_levels(const HostCSR& strict, bool lower);

@@ -1101,6 +1101,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         prm.mu = opts.mu;
         prm.small = opts.small;
         prm.scale = opts.scale_columns != 0;
+        prm.threads = ilup_threads(opts.host_threads, h->m, h->n);
         // The host factor depends only on (p, tau, mu, small, scaling): a call
         // that changes the correction, precision or schedule re-uses it.
         std::unique_ptr<IlupResult> F;
