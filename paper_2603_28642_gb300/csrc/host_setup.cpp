@@ -31,6 +31,7 @@
 #include <functional>
 #include <memory>
 #include <stdexcept>
+#include <system_error>
 #include <thread>
 
 namespace rlsq {
@@ -789,11 +790,21 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     R.Udiag.assign(static_cast<size_t>(n), 0.0);
 
     ColumnFactor C;
-    // The pipeline needs a bound on the entries of an L column (p >= 0).
-    if (prm.p >= 0 && prm.threads > 1)
-        columns_pipelined(a, ac, prm, prm.threads, R, C);
-    else
-        columns_serial(a, ac, prm, R, C);
+    // The pipeline needs a bound on the entries of an L column (p >= 0).  If
+    // the system refuses a thread, the serial loop does the work instead.
+    bool serial = !(prm.p >= 0 && prm.threads > 1);
+    if (!serial) {
+        try {
+            columns_pipelined(a, ac, prm, prm.threads, R, C);
+        } catch (const std::system_error&) {
+            R.prow.assign(static_cast<size_t>(n), -1);
+            R.Udiag.assign(static_cast<size_t>(n), 0.0);
+            R.nmod = 0;
+            C = ColumnFactor();
+            serial = true;
+        }
+    }
+    if (serial) columns_serial(a, ac, prm, R, C);
     split_and_analyse(R, C);
     return R;
 }
