@@ -325,14 +325,18 @@ void columns_serial(const HostCSR& a, const HostCSR& ac, const IlupParams& prm, 
 
 // ---------------------------------------------------------------------------
 // Pipelined columns.  Column c's triangular solve over the pivot positions
-// k < c - W + 1 uses only columns that are final once column c - W is, so W
-// threads each take every W-th column and run that part of W consecutive
-// columns at the same time, in working arrays of their own.  Each then waits
-// for column c - 1 to be final and finishes column c itself: the remaining
-// positions c - W + 1 .. c - 1 (in ascending order, after all smaller ones,
-// as the serial solve takes them), the U drop, the pivot choice and the L
-// part.  Every floating-point operation happens on the same operands in the
-// same order as in the serial loop, so the factor is the same bit for bit.
+// k < h uses only columns 0 .. h-1 and their pivots, so once h columns are
+// final that part can run while columns h .. c-1 are still being finished.
+// W threads take every W-th column each and keep up to D of their columns in
+// flight, each in working arrays (a slot) of its own: a thread starts a
+// column's solve with h = the number of final columns, and finishes its
+// oldest column once column c - 1 is final (checking for that between steps
+// of a long solve): the positions h .. c-1 (in ascending order, after all
+// smaller ones, as the serial solve takes them), the U drop, the pivot
+// choice and the L part.  Every floating-point operation happens on the same
+// operands in the same order as in the serial loop, so the factor is the same
+// bit for bit.  Solve times are very uneven (a few columns reach thousands of
+// pivot positions), which is what the D columns of look-ahead absorb.
 
 struct Touched {
     double x;     // value of the row in this column
@@ -379,15 +383,16 @@ struct TopMags {
     }
 };
 
-struct Worker {
+// Working state of one column in flight.
+struct Slot {
     std::vector<WorkerRow> rows;
-    std::vector<int32_t> vmark;  // column that queued the pivot position
     std::vector<int32_t> heap;
     std::vector<Touched> act;    // touched rows not pivoted below the horizon
     std::vector<Entry> cand;     // U part, ascending position
     std::vector<Entry> lc;       // L part
     TopMags top;
     int64_t applied = 0;         // pivot positions copied into rows[].piv
+    int64_t horizon = 0;         // columns final when the column's solve began
 };
 
 struct alignas(64) PaddedCounter {
@@ -424,10 +429,10 @@ void drop_scaled(const std::vector<Touched>& c, double pv, double xp, int p, dou
     dual_drop(out, p, tau);
 }
 
-void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& prm, int nthreads, IlupResult& R,
-                       ColumnFactor& C) {
+void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& prm, int nthreads, int depth,
+                       IlupResult& R, ColumnFactor& C) {
     const int64_t m = a.rows, n = a.cols;
-    const int64_t W = nthreads;
+    const int64_t W = nthreads, D = depth;
     const size_t cap = static_cast<size_t>(n) * static_cast<size_t>(prm.p);
     // L storage is appended to while other threads read finished columns,
     // so it never moves: each column keeps at most p entries.
@@ -444,22 +449,17 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
     std::vector<int32_t> rc(static_cast<size_t>(m));
     for (int64_t i = 0; i < m; ++i) rc[i] = static_cast<int32_t>(a.ptr[i + 1] - a.ptr[i]);
 
-    std::vector<std::unique_ptr<Worker>> ws;
-    for (int64_t w = 0; w < W; ++w) {
-        std::unique_ptr<Worker> k(new Worker());
-        k->rows.assign(static_cast<size_t>(m), WorkerRow{0.0, -1, -1});
-        k->vmark.assign(static_cast<size_t>(n), -1);
-        ws.push_back(std::move(k));
-    }
     PaddedCounter done;  // columns final
     std::atomic<bool> abort{false};
     const int32_t* prow = R.prow.data();
     const auto heap_after = std::greater<int32_t>();
 
-    // column c's solve over the positions k < c - W + 1, ascending
-    auto solve_below_horizon = [&](Worker& K, int64_t cc) {
+    // column c's solve over the positions below the horizon, ascending;
+    // poll() is called now and then to finish an older column
+    auto solve_below_horizon = [&](Slot& K, int64_t cc, auto&& poll) {
         const int32_t c = static_cast<int32_t>(cc);
-        const int64_t horizon = cc - W + 1;
+        const int64_t horizon = done.v.load(std::memory_order_acquire);
+        K.horizon = horizon;
         WorkerRow* rw = K.rows.data();
         for (; K.applied < horizon; ++K.applied) rw[prow[K.applied]].piv = static_cast<int32_t>(K.applied);
         K.act.clear();
@@ -470,17 +470,17 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
             WorkerRow& r = rw[i];
             r.x = ac.val[e];
             r.mark = c;
+            // a pivot position is queued when its pivot row is first touched
+            // in this column, so at most once
             if (r.piv >= 0) {
-                if (K.vmark[r.piv] != c) {
-                    K.vmark[r.piv] = c;
-                    K.heap.push_back(r.piv);
-                }
+                K.heap.push_back(r.piv);
             } else {
                 K.act.push_back({0.0, i, 0});
             }
         }
         std::make_heap(K.heap.begin(), K.heap.end(), heap_after);
-        while (!K.heap.empty()) {
+        for (uint32_t step = 1; !K.heap.empty(); ++step) {
+            if ((step & 31u) == 0) poll();
             std::pop_heap(K.heap.begin(), K.heap.end(), heap_after);
             const int32_t k = K.heap.back();
             K.heap.pop_back();
@@ -496,13 +496,10 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
                     r.x = 0.0;
                     const int32_t q = r.piv;
                     if (q >= 0) {
-                        if (K.vmark[q] != c) {
-                            K.vmark[q] = c;
-                            K.heap.push_back(q);
-                            std::push_heap(K.heap.begin(), K.heap.end(), heap_after);
-                            __builtin_prefetch(&Li[Lp[q]]);
-                            __builtin_prefetch(&Lv[Lp[q]]);
-                        }
+                        K.heap.push_back(q);
+                        std::push_heap(K.heap.begin(), K.heap.end(), heap_after);
+                        __builtin_prefetch(&Li[Lp[q]]);
+                        __builtin_prefetch(&Lv[Lp[q]]);
                     } else {
                         K.act.push_back({0.0, i, 0});
                     }
@@ -518,11 +515,12 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
     };
 
     // the rest of column j, once columns 0 .. j-1 are final
-    auto finish_column = [&](Worker& K, int64_t jj) {
+    auto finish_column = [&](Slot& K, int64_t jj) {
         const int32_t j = static_cast<int32_t>(jj);
         WorkerRow* rw = K.rows.data();
-        // the positions above the horizon, ascending
-        for (int64_t k = std::max<int64_t>(jj - W + 1, 0); k < jj; ++k) {
+        // the positions from the horizon on, ascending
+        for (int64_t k = K.horizon; k < jj; ++k) __builtin_prefetch(&rw[prow[k]]);
+        for (int64_t k = K.horizon; k < jj; ++k) {
             const WorkerRow& pr = rw[prow[k]];
             if (pr.mark != j) continue;
             Touched& tr = K.act[static_cast<size_t>(pr.x)];
@@ -625,14 +623,35 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
 
     std::vector<std::exception_ptr> errs(static_cast<size_t>(W));
     auto run = [&](int64_t w) {
-        Worker& K = *ws[static_cast<size_t>(w)];
         try {
-            for (int64_t c = w; c < n; c += W) {
-                wait_for([&]() { return done.v.load(std::memory_order_acquire) >= c - W + 1; }, abort);
-                solve_below_horizon(K, c);
-                wait_for([&]() { return done.v.load(std::memory_order_acquire) >= c; }, abort);
-                finish_column(K, c);
-                done.v.store(c + 1, std::memory_order_release);
+            // this thread's slots, allocated (and first touched) here
+            std::vector<std::unique_ptr<Slot>> slots;
+            for (int64_t d = 0; d < D && w + d * W < n; ++d) {
+                std::unique_ptr<Slot> k(new Slot());
+                k->rows.assign(static_cast<size_t>(m), WorkerRow{0.0, -1, -1});
+                slots.push_back(std::move(k));
+            }
+            auto slot_of = [&](int64_t c) -> Slot& { return *slots[static_cast<size_t>((c / W) % D)]; };
+            // this thread's columns whose solve is done, oldest first
+            std::vector<int64_t> pending;
+            size_t head = 0;
+            auto finish_ready = [&]() {
+                while (head < pending.size() && done.v.load(std::memory_order_acquire) == pending[head]) {
+                    const int64_t c = pending[head++];
+                    finish_column(slot_of(c), c);
+                    done.v.store(c + 1, std::memory_order_release);
+                }
+            };
+            for (int64_t next = w; next < n || head < pending.size();) {
+                if (next < n && pending.size() - head < static_cast<size_t>(D)) {
+                    solve_below_horizon(slot_of(next), next, finish_ready);
+                    pending.push_back(next);
+                    next += W;
+                } else {
+                    const int64_t c = pending[head];
+                    wait_for([&]() { return done.v.load(std::memory_order_acquire) >= c; }, abort);
+                }
+                finish_ready();
             }
         } catch (const Aborted&) {
         } catch (...) {
@@ -760,11 +779,26 @@ void split_and_analyse(IlupResult& R, const ColumnFactor& C) {
 
 }  // namespace
 
+namespace {
+
+// Working arrays of one column in flight: 16 bytes per row of A.
+int64_t slot_bytes(int64_t m) {
+    return 16 * std::max<int64_t>(m, 1);
+}
+
+// Columns in flight per thread: up to 8 while all slots fit in 2 GiB.
+int ilup_depth(int threads, int64_t m) {
+    const int64_t fit = (int64_t(1) << 31) / (slot_bytes(m) * std::max(threads, 1));
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, fit)));
+}
+
+}  // namespace
+
 int ilup_threads(int requested, int64_t m, int64_t n) {
+    (void)n;
     int64_t t = requested > 0 ? std::min(requested, 64)
                               : std::min<int64_t>(8, std::max(1u, std::thread::hardware_concurrency()));
-    const int64_t per = 16 * std::max<int64_t>(m, 1) + 4 * std::max<int64_t>(n, 1);
-    t = std::min<int64_t>(t, std::max<int64_t>(1, (int64_t(1) << 31) / per));
+    t = std::min<int64_t>(t, std::max<int64_t>(1, (int64_t(1) << 31) / slot_bytes(m)));
     return static_cast<int>(t);
 }
 
@@ -795,7 +829,7 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     bool serial = !(prm.p >= 0 && prm.threads > 1);
     if (!serial) {
         try {
-            columns_pipelined(a, ac, prm, prm.threads, R, C);
+            columns_pipelined(a, ac, prm, prm.threads, ilup_depth(prm.threads, m), R, C);
         } catch (const std::system_error&) {
             R.prow.assign(static_cast<size_t>(n), -1);
             R.Udiag.assign(static_cast<size_t>(n), 0.0);
