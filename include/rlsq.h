@@ -250,11 +250,13 @@ int rlsq_get_levels(rlsq_problem h, int32_t which, int32_t *level);
    or remove rows of A2 (ids ascending and distinct; the rest are renumbered in
    order).  L1 and U are kept; A's device copy, the m-sized vectors and the
    device factor are rebuilt with the handle's factor options (autotuning
-   again if it was on).  b of later solves has the new m.  Not while the
-   handle is registered with a server.  Errors: ARG (a pivot row cannot be
-   removed: refactorise), CSR, SHAPE, NOT_FACTORED, OOM, CUDA. */
+   again if it was on).  b of later solves has the new m.  Errors: ARG (a
+   pivot row cannot be removed: refactorise; the handle is registered with a
+   live server), CSR, SHAPE, NOT_FACTORED, OOM, CUDA. */
 int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t *rowptr, const int32_t *colidx, const double *vals);
 int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t *ids);
+/* Free the handle and its device memory.  A handle registered with a live
+   server is left in place and the last error set (rlsq_server_register). */
 void rlsq_destroy(rlsq_problem h);
 
 /* ---- continuous-batching server ------------------------------------------ */
@@ -262,8 +264,10 @@ void rlsq_destroy(rlsq_problem h);
 /* Create a server with its own scheduler thread and CUDA stream. */
 int rlsq_server_create(const rlsq_server_opts *opts, rlsq_server *out);
 /* Make a factored problem available to requests; the problem must outlive
-   the server.  Errors: ARG, NOT_FACTORED, ADMISSION (state larger than the
-   whole budget). */
+   the server.  Until the server is destroyed, rlsq_factor, rlsq_add_rows and
+   rlsq_remove_rows on the problem fail with ARG and rlsq_destroy leaves it in
+   place (setting the last error).  Errors: ARG, NOT_FACTORED, ADMISSION (state
+   larger than the whole budget). */
 int rlsq_server_register(rlsq_server s, rlsq_problem h, int32_t *matrix_id);
 /* Queue a solve with right-hand side b (host memory, length m of the matrix;
    copied before return, never blocks on the device).  ticket identifies the

@@ -1044,6 +1044,7 @@ struct rlsq_server_s {
         }
         cv.notify_all();
         if (worker.joinable()) worker.join();
+        for (rlsq_problem_s* p : matrices) p->served.fetch_sub(1);
         e64.reset();
         e32.reset();
         b64.clear();
@@ -1258,6 +1259,7 @@ int rlsq_server_register(rlsq_server s, rlsq_problem h, int32_t* matrix_id) {
             throw ApiError(RLSQ_ERR_ARG, "all served matrices need the same precision");
         s->precision = h->precision;
         s->matrices.push_back(h);
+        h->served.fetch_add(1);
         s->dirty = true;
         *matrix_id = static_cast<int32_t>(s->matrices.size() - 1);
         s->cv.notify_all();

@@ -2,6 +2,8 @@
 // C ABI, owning device arrays and the problem handle.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -162,6 +164,9 @@ void copy_half(double* dst, const double2* pairs, int64_t n, int half, bool dev,
 
 struct rlsq_problem_s {
     int64_t m = 0, n = 0, nnz = 0;
+    // servers this problem is registered with: while > 0 its device data must
+    // not change (refactor, row updates) or go (destroy)
+    std::atomic<int32_t> served{0};
     rlsq::HostCSR A;                 // host copy (the set-up runs on the host)
     rlsq::DevCsr<double> dA, dAt;    // CSR and CSC (= CSR of A^T) of the sparse rows, internal row order
     // Dense rows (sparse-dense problems): rows with many nonzeros sit at the end

@@ -1084,6 +1084,7 @@ int rlsq_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* coli
 int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
     return guarded([&]() -> int {
         if (!h) throw ApiError(RLSQ_ERR_ARG, "null handle");
+        if (h->served.load() > 0) throw ApiError(RLSQ_ERR_ARG, "the problem is registered with a server");
         rlsq_factor_opts opts;
         rlsq_factor_opts_default(&opts);
         if (o) opts = *o;
@@ -1231,6 +1232,7 @@ static void refresh_after_rows(rlsq_problem_s* h) {
 int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t* rowptr, const int32_t* colidx, const double* vals) {
     return guarded([&]() -> int {
         if (!h || !rowptr || (k > 0 && (!colidx || !vals)) || k < 0) throw ApiError(RLSQ_ERR_ARG, "bad argument");
+        if (h->served.load() > 0) throw ApiError(RLSQ_ERR_ARG, "the problem is registered with a server");
         if (!h->factored || !h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
         if (rowptr[0] != 0) throw ApiError(RLSQ_ERR_CSR, "rowptr[0] must be 0");
         const int64_t n = h->n;
@@ -1272,6 +1274,7 @@ int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t* rowptr, const int32_
 int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t* ids) {
     return guarded([&]() -> int {
         if (!h || (k > 0 && !ids) || k < 0) throw ApiError(RLSQ_ERR_ARG, "bad argument");
+        if (h->served.load() > 0) throw ApiError(RLSQ_ERR_ARG, "the problem is registered with a server");
         if (!h->factored || !h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
         std::vector<int32_t> v(ids, ids + k);
         try {
@@ -1572,6 +1575,13 @@ int rlsq_get_levels(rlsq_problem h, int32_t which, int32_t* level) {
     });
 }
 
-void rlsq_destroy(rlsq_problem h) { delete h; }
+void rlsq_destroy(rlsq_problem h) {
+    // a live server still reads the problem's device data: keep it (and say so)
+    if (h && h->served.load() > 0) {
+        (void)guarded([&]() -> int { throw ApiError(RLSQ_ERR_ARG, "the problem is registered with a server"); });
+        return;
+    }
+    delete h;
+}
 
 }  // extern "C"

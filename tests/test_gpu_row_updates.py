@@ -69,3 +69,21 @@ def test_remove_pivot_row_refused():
     with pytest.raises(B.RlsqError) as e:
         P.remove_rows(np.array([prow[0]], dtype=np.int32))
     assert e.value.code == -1
+
+
+def test_registered_problem_refuses_changes():
+    """While a server holds the problem, its device data must stay: refactoring
+    and row updates are refused (ARG) until the server is destroyed."""
+    p = synth.config_problem(0)
+    P = B.Problem.from_problem(p)
+    P.factor(mu=1.0, correction=B.CORR_CG)
+    srv = B.Server(hbm_budget_bytes=1 << 30, max_slots=2)
+    srv.register(P)
+    ptr, idx, val = new_rows(p.n, 2, 4, seed=3)
+    for call in (lambda: P.add_rows(ptr, idx, val), lambda: P.factor(mu=1.0, correction=B.CORR_CG)):
+        with pytest.raises(B.RlsqError) as e:
+            call()
+        assert e.value.code == -1
+    assert P.m == p.m
+    srv.close()
+    assert P.add_rows(ptr, idx, val)["m"] == p.m + 2
