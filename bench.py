@@ -312,6 +312,7 @@ def run_ours(args):
                           "x_rel_diff_vs_lsmr": float(np.linalg.norm(cgls.x - tol64.x) / np.linalg.norm(tol64.x))},
         },
         "factor_seconds": finfo["factor_seconds"],
+        "ilup_seconds": finfo["ilup_seconds"], "ilup_threads": finfo["ilup_threads"],
         "roofline": roof,
         "kernel_classes": {k: {"ms": v["ms"], "launches": v["launches"],
                                "GBps": v["bytes"] / (v["ms"] / 1000.0) / 1e9} for k, v in cls.items()},

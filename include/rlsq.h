@@ -158,6 +158,9 @@ typedef struct {
     int32_t level_merge[4];  /* fused levels per group, per system (groups chosen level by level:
                                 the largest group) */
     int32_t trsv_schedule[4]; /* RLSQ_TRSV_* each system runs with (after autotuning) */
+    double ilup_seconds;   /* host ILUP (Algorithms 4-6), split, transposes and level sets of the
+                              factorisation in use (part of factor_seconds) */
+    int32_t ilup_threads;  /* threads of its column loop */
 } rlsq_info;
 
 /* Server options and statistics (continuous batching of right-hand sides). */

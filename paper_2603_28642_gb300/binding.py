@@ -66,7 +66,7 @@ class Info(C.Structure):
         ("levels_L1", C.c_int32), ("levels_L1t", C.c_int32), ("levels_U", C.c_int32),
         ("levels_Ut", C.c_int32), ("correction", C.c_int32), ("precision", C.c_int32),
         ("bytes_per_iter", C.c_double), ("solve_levels", C.c_int32 * 4), ("level_merge", C.c_int32 * 4),
-        ("trsv_schedule", C.c_int32 * 4),
+        ("trsv_schedule", C.c_int32 * 4), ("ilup_seconds", C.c_double), ("ilup_threads", C.c_int32),
     ]
 
     def as_dict(self):

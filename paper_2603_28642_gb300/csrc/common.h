@@ -187,6 +187,8 @@ struct rlsq_problem_s {
     int correction = RLSQ_CORR_NONE;
     int precision = RLSQ_PREC_FP64;
     double factor_seconds = 0.0;
+    double ilup_seconds = 0.0;       // the host set-up of the factor in use
+    int32_t ilup_threads = 0;
     std::unique_ptr<rlsq::IlupResult> F;
     std::vector<rlsq::MergedTri> merged;  // the four systems as the GPU solves them
     rlsq::DevFactor<double> f64;

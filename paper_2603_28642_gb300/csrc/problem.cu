@@ -634,6 +634,8 @@ static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
     info->correction = P->correction;
     info->precision = P->precision;
     info->factor_seconds = P->factor_seconds;
+    info->ilup_seconds = P->ilup_seconds;
+    info->ilup_threads = P->ilup_threads;
     if (P->F) {
         const IlupResult& F = *P->F;
         info->nnz_L1 = F.L1.nnz();
@@ -1114,7 +1116,11 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         } else {
             h->F.reset();
             try {
+                const auto t_ilup = std::chrono::steady_clock::now();
                 F.reset(new IlupResult(ilup_factor(h->A, prm)));
+                h->ilup_seconds =
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t_ilup).count();
+                h->ilup_threads = prm.threads;
             } catch (const std::runtime_error& e) {
                 throw ApiError(RLSQ_ERR_RANK, e.what());
             }
