@@ -168,7 +168,8 @@ void columns_serial(const HostCSR& a, const HostCSR& ac, const IlupParams& prm, 
     std::vector<double>& Uv = C.Uv;
     Lp.assign(static_cast<size_t>(n) + 1, 0);
     Up.assign(static_cast<size_t>(n) + 1, 0);
-    const size_t guess = static_cast<size_t>(n) * static_cast<size_t>(prm.p >= 0 ? prm.p : 16);
+    const size_t guess = std::min<size_t>(size_t(1) << 27,
+                                          static_cast<size_t>(n) * static_cast<size_t>(prm.p >= 0 ? prm.p : 16));
     Li.reserve(guess);
     Lv.reserve(guess);
     Ui.reserve(guess);
@@ -824,9 +825,11 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     R.Udiag.assign(static_cast<size_t>(n), 0.0);
 
     ColumnFactor C;
-    // The pipeline needs a bound on the entries of an L column (p >= 0).  If
+    // The pipeline stores L in place, so it needs a bound on the entries of an
+    // L column (p >= 0) that keeps n p entries to a sensible size (2^27).  If
     // the system refuses a thread, the serial loop does the work instead.
-    bool serial = !(prm.p >= 0 && prm.threads > 1);
+    bool serial = !(prm.p >= 0 && prm.threads > 1 &&
+                    static_cast<double>(n) * static_cast<double>(prm.p) <= static_cast<double>(int64_t(1) << 27));
     if (!serial) {
         try {
             columns_pipelined(a, ac, prm, prm.threads, ilup_depth(prm.threads, m), R, C);
