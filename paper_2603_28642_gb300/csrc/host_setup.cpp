@@ -485,6 +485,11 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
             std::pop_heap(K.heap.begin(), K.heap.end(), heap_after);
             const int32_t k = K.heap.back();
             K.heap.pop_back();
+            // the rows the next position will update, while this one's are updated
+            if (!K.heap.empty()) {
+                const int32_t nk = K.heap.front();
+                for (int64_t e = Lp[nk]; e < Lp[nk + 1]; ++e) __builtin_prefetch(&rw[Li[e]]);
+            }
             const double ukj = rw[prow[k]].x;
             if (ukj == 0.0) continue;
             K.cand.push_back({std::fabs(ukj), k, ukj});
