@@ -117,7 +117,7 @@ typedef struct {
                               < 0 = never */
     int32_t host_threads;  /* host threads of the set-up: the ILUP column loop (pipelined over
                               columns, the same factor bit for bit for any count) and the dense
-                              S; <= 0 = hardware concurrency (the ILUP takes at most 8, and
+                              S; <= 0 = the CPUs the process may run on (the ILUP takes at most 16, and
                               fewer where its per-thread arrays, 16 bytes per row of A, would
                               pass 2 GiB) */
     int32_t level_merge;   /* levels fused per group in the triangular solves: 1 = none,

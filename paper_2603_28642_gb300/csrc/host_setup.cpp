@@ -26,6 +26,9 @@
 
 #include <algorithm>
 #include <atomic>
+#if defined(__linux__)
+#include <sched.h>
+#endif
 #include <cmath>
 #include <exception>
 #include <functional>
@@ -340,9 +343,10 @@ void columns_serial(const HostCSR& a, const HostCSR& ac, const IlupParams& prm, 
 // pivot positions), which is what the D columns of look-ahead absorb.
 
 struct Touched {
-    double x;     // value of the row in this column
-    int32_t row;  // original row id
-    int32_t out;  // 1: pivoted (at a position above the horizon, or here)
+    double x;         // value of the row in this column
+    int32_t row;      // original row id
+    uint8_t out;      // pivoted (at a position above the horizon, or here)
+    uint8_t changed;  // flagged, updated or added while the column is finished
 };
 
 // A worker's view of one row, one 16-byte record so a random row access
@@ -375,13 +379,6 @@ struct TopMags {
         for (; i > 0 && v[i - 1] < g; --i) v[i] = v[i - 1];
         v[i] = g;
     }
-    void remove_one(double g) {
-        for (size_t i = 0; i < v.size(); ++i)
-            if (v[i] == g) {
-                v.erase(v.begin() + static_cast<std::ptrdiff_t>(i));
-                return;
-            }
-    }
 };
 
 // Working state of one column in flight.
@@ -394,6 +391,14 @@ struct Slot {
     TopMags top;
     int64_t applied = 0;         // pivot positions copied into rows[].piv
     int64_t horizon = 0;         // columns final when the column's solve began
+    // The rows the finish is likely to need, listed by the solve: every
+    // nonzero with |x| >= big_lo; big_hi (>= big_lo) is at most the
+    // (p + 9)-th largest |x| and mu times the largest (0 with fewer than
+    // p + 9 nonzeros).  Rows left out are below big_lo.
+    std::vector<int32_t> big;
+    double big_lo = 0.0, big_hi = 0.0;
+    std::vector<int32_t> chg;    // rows changed while finishing
+    std::vector<int32_t> sel;    // rows the finish examines
 };
 
 struct alignas(64) PaddedCounter {
@@ -415,18 +420,26 @@ void wait_for(Ready ready, const std::atomic<bool>& abort) {
 // that can be kept.  `xp` is the p-th largest |x| among them (0 if there are
 // at most p).  x -> fl(x / pv) is monotone in |x|, so an entry clearly
 // smaller in |x| than the p-th largest is clearly smaller after the division.
-void drop_scaled(const std::vector<Touched>& c, double pv, double xp, int p, double tau, std::vector<Entry>& out) {
+// `sel` (if not null) names the entries of `c` to consider; the others are
+// known to be out, zero or below the p-th largest by more than the margin.
+void drop_scaled(const std::vector<Touched>& c, const std::vector<int32_t>* sel, double pv, double xp, int p,
+                 double tau, std::vector<Entry>& out) {
     out.clear();
     if (p == 0 || c.empty()) return;
     double lo = 0.0;
     // the margin is far above the quotients' rounding; it is not used where a
     // quotient could be subnormal
     if (xp > 0.0 && xp / std::fabs(pv) > 1e-290) lo = xp * (1.0 - 0x1p-40);
-    for (const Touched& t : c)
+    auto take = [&](const Touched& t) {
         if (!t.out && t.x != 0.0 && std::fabs(t.x) >= lo) {
             const double l = t.x / pv;
             out.push_back({std::fabs(l), t.row, l});
         }
+    };
+    if (sel)
+        for (const int32_t s : *sel) take(c[static_cast<size_t>(s)]);
+    else
+        for (const Touched& t : c) take(t);
     dual_drop(out, p, tau);
 }
 
@@ -476,7 +489,7 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
             if (r.piv >= 0) {
                 K.heap.push_back(r.piv);
             } else {
-                K.act.push_back({0.0, i, 0});
+                K.act.push_back({0.0, i, 0, 0});
             }
         }
         std::make_heap(K.heap.begin(), K.heap.end(), heap_after);
@@ -507,7 +520,7 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
                         __builtin_prefetch(&Li[Lp[q]]);
                         __builtin_prefetch(&Lv[Lp[q]]);
                     } else {
-                        K.act.push_back({0.0, i, 0});
+                        K.act.push_back({0.0, i, 0, 0});
                     }
                 }
                 r.x = r.x - Lv[e] * ukj;
@@ -518,6 +531,27 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
             K.act[s].x = r.x;
             r.x = static_cast<double>(s);
         }
+        // the rows the finish is likely to need (off the ordered chain)
+        K.big.clear();
+        const size_t want = static_cast<size_t>(prm.p) + 9;
+        K.top.reset(want);
+        double mw = 0.0, gate = -1.0;
+        for (const Touched& t : K.act)
+            if (t.x != 0.0) {
+                const double g = std::fabs(t.x);
+                mw = std::max(mw, g);
+                if (g > gate) {
+                    K.top.add(g);
+                    if (K.top.v.size() == want) gate = K.top.v.back();
+                }
+            }
+        K.big_hi = K.big_lo = 0.0;
+        if (K.top.v.size() == want) {
+            K.big_hi = std::min(K.top.v.back(), prm.mu * mw * (1.0 - 0x1p-30));
+            K.big_lo = K.big_hi * (1.0 - 0x1p-30);
+        }
+        for (size_t s = 0; s < K.act.size(); ++s)
+            if (K.act[s].x != 0.0 && std::fabs(K.act[s].x) >= K.big_lo) K.big.push_back(static_cast<int32_t>(s));
     };
 
     // the rest of column j, once columns 0 .. j-1 are final
@@ -526,12 +560,20 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
         WorkerRow* rw = K.rows.data();
         // the positions from the horizon on, ascending
         for (int64_t k = K.horizon; k < jj; ++k) __builtin_prefetch(&rw[prow[k]]);
+        K.chg.clear();
+        auto changed = [&](size_t s) {
+            if (!K.act[s].changed) {
+                K.act[s].changed = 1;
+                K.chg.push_back(static_cast<int32_t>(s));
+            }
+        };
         for (int64_t k = K.horizon; k < jj; ++k) {
             const WorkerRow& pr = rw[prow[k]];
             if (pr.mark != j) continue;
-            Touched& tr = K.act[static_cast<size_t>(pr.x)];
-            tr.out = 1;
-            const double ukj = tr.x;
+            const size_t ps = static_cast<size_t>(pr.x);
+            K.act[ps].out = 1;
+            changed(ps);
+            const double ukj = K.act[ps].x;
             if (ukj == 0.0) continue;
             K.cand.push_back({std::fabs(ukj), static_cast<int32_t>(k), ukj});
             for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
@@ -540,9 +582,11 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
                 if (r.mark != j) {
                     r.mark = j;
                     r.x = static_cast<double>(K.act.size());
-                    K.act.push_back({0.0, i, 0});
+                    K.act.push_back({0.0, i, 0, 0});
                 }
-                Touched& t = K.act[static_cast<size_t>(r.x)];
+                const size_t ts = static_cast<size_t>(r.x);
+                changed(ts);
+                Touched& t = K.act[ts];
                 t.x = t.x - Lv[e] * ukj;
             }
         }
@@ -553,20 +597,34 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
         }
         Up[j + 1] = static_cast<int64_t>(C.Ui.size());
 
-        // pivot choice (Algorithms 5 and 6) among the unpivoted nonzeros
-        K.top.reset(static_cast<size_t>(prm.p) + 1);
-        double maxabs = 0.0, gate = -1.0;
+        // Pivot choice (Algorithms 5 and 6) among the unpivoted nonzeros.  The
+        // rows examined first are the solve's list (unchanged ones) and the
+        // changed ones; every other row is below big_lo, so they decide alone
+        // when the largest and the threshold are at least big_lo.  Otherwise
+        // all rows are examined.
+        K.sel.clear();
+        for (const int32_t s : K.big)
+            if (!K.act[static_cast<size_t>(s)].changed) K.sel.push_back(s);
+        for (const int32_t s : K.chg) K.sel.push_back(s);
+        double maxabs = 0.0;
         size_t neligible = 0;
-        for (const Touched& t : K.act)
+        for (const int32_t s : K.sel) {
+            const Touched& t = K.act[static_cast<size_t>(s)];
             if (!t.out && t.x != 0.0) {
                 ++neligible;
-                const double g = std::fabs(t.x);
-                maxabs = std::max(maxabs, g);
-                if (g > gate) {
-                    K.top.add(g);
-                    if (K.top.v.size() == K.top.cap) gate = K.top.v.back();
-                }
+                maxabs = std::max(maxabs, std::fabs(t.x));
             }
+        }
+        bool listed = neligible > 0 && maxabs >= K.big_lo && prm.mu * maxabs >= K.big_lo;
+        if (!listed) {
+            maxabs = 0.0;
+            neligible = 0;
+            for (const Touched& t : K.act)
+                if (!t.out && t.x != 0.0) {
+                    ++neligible;
+                    maxabs = std::max(maxabs, std::fabs(t.x));
+                }
+        }
         double colinf = 0.0;
         for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) colinf = std::max(colinf, std::fabs(ac.val[e]));
         const double modval = modified_pivot(colinf, jj, n, prm.small);
@@ -581,10 +639,10 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
             const double thr = prm.mu * maxabs;
             double rmag = 0.0;
             size_t rslot = 0;
-            for (size_t s = 0; s < K.act.size(); ++s) {
+            auto consider = [&](size_t s) {
                 const Touched& t = K.act[s];
                 const double mag = std::fabs(t.x);
-                if (t.out || t.x == 0.0 || !(mag >= thr)) continue;
+                if (t.out || t.x == 0.0 || !(mag >= thr)) return;
                 const int32_t i = t.row;
                 bool take = r < 0;
                 if (!take) {
@@ -597,25 +655,56 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
                     rmag = mag;
                     rslot = s;
                 }
-            }
+            };
+            if (listed)
+                for (const int32_t s : K.sel) consider(static_cast<size_t>(s));
+            else
+                for (size_t s = 0; s < K.act.size(); ++s) consider(s);
             pv = K.act[rslot].x;
             if (std::fabs(pv) < prm.small) {
                 pv = (pv < 0.0) ? -modval : modval;
                 R.nmod++;
             }
             K.act[rslot].out = 1;
-            --neligible;
-            if (K.top.v.size() == K.top.cap && rmag < K.top.v.back()) K.top.v.pop_back();
-            else K.top.remove_one(rmag);
         }
         R.Udiag[j] = pv;
         R.prow[j] = r;
         piv[r] = j;
 
-        // L part: scale by the pivot, then drop
-        const double xp = (prm.p > 0 && neligible > static_cast<size_t>(prm.p))
-                              ? K.top.v[static_cast<size_t>(prm.p) - 1] : 0.0;
-        drop_scaled(K.act, pv, xp, prm.p, prm.tau, K.lc);
+        // L part: scale by the pivot, then drop.  The p-th largest |x| among
+        // the remaining rows comes from the examined rows when at least p of
+        // them reach big_hi (every other row is then below it by more than
+        // the margin drop_scaled uses); otherwise from all rows.
+        const size_t pp = static_cast<size_t>(prm.p);
+        K.top.reset(pp + 1);
+        size_t nhi = 0;
+        if (listed && pp > 0) {
+            for (const int32_t s : K.sel) {
+                const Touched& t = K.act[static_cast<size_t>(s)];
+                if (t.out || t.x == 0.0) continue;
+                const double g = std::fabs(t.x);
+                if (g >= K.big_hi) ++nhi;
+                K.top.add(g);
+            }
+        }
+        if (pp > 0 && listed && nhi >= pp) {
+            drop_scaled(K.act, &K.sel, pv, K.top.v[pp - 1], prm.p, prm.tau, K.lc);
+        } else {
+            K.top.reset(pp + 1);
+            double gate = -1.0;
+            size_t nrest = 0;
+            for (const Touched& t : K.act)
+                if (!t.out && t.x != 0.0) {
+                    ++nrest;
+                    const double g = std::fabs(t.x);
+                    if (g > gate) {
+                        K.top.add(g);
+                        if (K.top.v.size() == K.top.cap) gate = K.top.v.back();
+                    }
+                }
+            const double xp = (pp > 0 && nrest > pp) ? K.top.v[pp - 1] : 0.0;
+            drop_scaled(K.act, nullptr, pv, xp, prm.p, prm.tau, K.lc);
+        }
         int64_t at = Lp[j];
         for (const Entry& c : K.lc) {
             Li[at] = c.key;
@@ -800,10 +889,20 @@ int ilup_depth(int threads, int64_t m) {
 
 }  // namespace
 
+// CPUs this process may run on (its affinity mask; the whole machine where
+// that cannot be read).
+int usable_cpus() {
+#if defined(__linux__)
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    if (sched_getaffinity(0, sizeof(set), &set) == 0) return std::max(1, CPU_COUNT(&set));
+#endif
+    return static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+}
+
 int ilup_threads(int requested, int64_t m, int64_t n) {
     (void)n;
-    int64_t t = requested > 0 ? std::min(requested, 64)
-                              : std::min<int64_t>(8, std::max(1u, std::thread::hardware_concurrency()));
+    int64_t t = requested > 0 ? std::min(requested, 64) : std::min(16, usable_cpus());
     t = std::min<int64_t>(t, std::max<int64_t>(1, (int64_t(1) << 31) / slot_bytes(m)));
     return static_cast<int>(t);
 }

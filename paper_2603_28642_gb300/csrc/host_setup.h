@@ -78,7 +78,7 @@ bool column_scaling(const HostCSR& a, std::vector<double>& d);
 IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm);
 
 // Threads for the column loop of an m x n factorisation: `requested` if > 0
-// (at most 64), else the hardware concurrency (at most 8); fewer where one
+// (at most 64), else the CPUs the process may run on (at most 16); fewer where one
 // working array per thread (16 bytes per row of A) would pass 2 GiB.  Each
 // thread keeps up to 8 columns in flight, as many as such arrays fit in 2 GiB.
 int ilup_threads(int requested, int64_t m, int64_t n);

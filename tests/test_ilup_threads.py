@@ -130,7 +130,7 @@ def test_thread_count_rule():
     lib = B.load()
     assert lib.rlsq_setup_threads(3, 1000, 500) == 3
     assert lib.rlsq_setup_threads(1000, 1000, 500) == 64
-    assert 1 <= lib.rlsq_setup_threads(0, 1000, 500) <= 8
+    assert 1 <= lib.rlsq_setup_threads(0, 1000, 500) <= 16
     # working arrays of 16 bytes per row: 2 GiB holds one thread's at 2^27 rows
     assert lib.rlsq_setup_threads(8, 1 << 27, 1 << 20) == 1
     assert lib.rlsq_setup_threads(8, 1 << 25, 1 << 20) == 4
