@@ -59,6 +59,74 @@ HostCSR transpose(const HostCSR& a) {
     return t;
 }
 
+namespace {
+
+// The transpose of a CSR structure (rows x cols) on up to `threads` threads:
+// output row relabel[c] (c itself without a relabelling, which must then be a
+// permutation onto 0..cols-1) holds the entries of column c in ascending
+// source row, exactly as transpose() orders them.  Each thread counts and
+// then scatters one block of source rows; per-block offsets keep the order.
+void transpose_into(int64_t rows, int64_t cols, const int64_t* ptr, const int32_t* idx, const double* val,
+                    const int32_t* relabel, int threads, HostCSR& out) {
+    const int64_t nnz = ptr[rows];
+    const int64_t T = std::max<int64_t>(1, std::min<int64_t>(threads, nnz / (int64_t(1) << 18) + 1));
+    out.rows = cols;
+    out.cols = rows;
+    out.ptr.assign(static_cast<size_t>(cols) + 1, 0);
+    out.idx.resize(static_cast<size_t>(nnz));
+    out.val.resize(static_cast<size_t>(nnz));
+    // blocks of source rows with about nnz / T entries each
+    std::vector<int64_t> start(static_cast<size_t>(T) + 1, rows);
+    start[0] = 0;
+    for (int64_t b = 1; b < T; ++b)
+        start[b] = std::lower_bound(ptr, ptr + rows + 1, b * nnz / T) - ptr;
+    for (int64_t b = 1; b <= T; ++b) start[b] = std::max(start[b], start[b - 1]);
+    std::vector<std::vector<int64_t>> off(static_cast<size_t>(T));
+    auto parallel = [&](auto&& body) {
+        std::vector<std::thread> ts;
+        std::vector<std::exception_ptr> errs(static_cast<size_t>(T));
+        auto guarded_body = [&](int64_t b) {
+            try {
+                body(b);
+            } catch (...) {
+                errs[static_cast<size_t>(b)] = std::current_exception();
+            }
+        };
+        for (int64_t b = 1; b < T; ++b) ts.emplace_back(guarded_body, b);
+        guarded_body(0);
+        for (auto& t : ts) t.join();
+        for (const auto& e : errs)
+            if (e) std::rethrow_exception(e);
+    };
+    auto row_of = [&](int32_t c) -> int64_t { return relabel ? relabel[c] : c; };
+    parallel([&](int64_t b) {
+        std::vector<int64_t>& cnt = off[static_cast<size_t>(b)];
+        cnt.assign(static_cast<size_t>(cols), 0);
+        for (int64_t e = ptr[start[b]]; e < ptr[start[b + 1]]; ++e) cnt[row_of(idx[e])]++;
+    });
+    // output row r starts after all earlier rows; block b after blocks < b
+    for (int64_t r = 0; r < cols; ++r) {
+        int64_t run = out.ptr[r];
+        for (int64_t b = 0; b < T; ++b) {
+            const int64_t c = off[static_cast<size_t>(b)][r];
+            off[static_cast<size_t>(b)][r] = run;
+            run += c;
+        }
+        out.ptr[r + 1] = run;
+    }
+    parallel([&](int64_t b) {
+        std::vector<int64_t>& at = off[static_cast<size_t>(b)];
+        for (int64_t r = start[b]; r < start[b + 1]; ++r)
+            for (int64_t e = ptr[r]; e < ptr[r + 1]; ++e) {
+                const int64_t dst = at[row_of(idx[e])]++;
+                out.idx[dst] = static_cast<int32_t>(r);
+                out.val[dst] = val[e];
+            }
+    });
+}
+
+}  // namespace
+
 bool column_scaling(const HostCSR& a, std::vector<double>& d) {
     std::vector<double> ss(static_cast<size_t>(a.cols), 0.0);
     for (int64_t r = 0; r < a.rows; ++r)
@@ -773,7 +841,7 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
 
 // The split (pivot rows in pivot order form L1, the rest in ascending id L2),
 // U by rows, the transposes and the level sets.
-void split_and_analyse(IlupResult& R, const ColumnFactor& C) {
+void split_and_analyse(IlupResult& R, const ColumnFactor& C, int threads) {
     const int64_t m = R.m, n = R.n;
     const int64_t m2 = m - n;
     const std::vector<int32_t>& pivpos = C.pivpos;
@@ -790,53 +858,27 @@ void split_and_analyse(IlupResult& R, const ColumnFactor& C) {
             a2idx[i] = static_cast<int32_t>(R.a2rows.size());
             R.a2rows.push_back(static_cast<int32_t>(i));
         }
-    R.L1.rows = n; R.L1.cols = n;
-    R.L2.rows = m2; R.L2.cols = n;
-    R.L1.ptr.assign(static_cast<size_t>(n) + 1, 0);
-    R.L2.ptr.assign(static_cast<size_t>(m2) + 1, 0);
-    for (size_t e = 0; e < Li.size(); ++e) {
-        const int32_t i = Li[e];
-        if (pivpos[i] >= 0) R.L1.ptr[pivpos[i] + 1]++;
-        else R.L2.ptr[a2idx[i] + 1]++;
-    }
-    for (int64_t k = 0; k < n; ++k) R.L1.ptr[k + 1] += R.L1.ptr[k];
-    for (int64_t k = 0; k < m2; ++k) R.L2.ptr[k + 1] += R.L2.ptr[k];
-    R.L1.idx.resize(static_cast<size_t>(R.L1.ptr[n]));
-    R.L1.val.resize(static_cast<size_t>(R.L1.ptr[n]));
-    R.L2.idx.resize(static_cast<size_t>(R.L2.ptr[m2]));
-    R.L2.val.resize(static_cast<size_t>(R.L2.ptr[m2]));
+    // L by rows: row label(i) holds original row i's multipliers in ascending
+    // position, with the pivot rows first (in pivot order) and the rows of A2
+    // after them (ascending id)
     {
-        std::vector<int64_t> f1(R.L1.ptr.begin(), R.L1.ptr.end() - 1);
-        std::vector<int64_t> f2(R.L2.ptr.begin(), R.L2.ptr.end() - 1);
-        for (int64_t k = 0; k < n; ++k)
-            for (int64_t e = Lp[k]; e < Lp[k + 1]; ++e) {
-                const int32_t i = Li[e];
-                if (pivpos[i] >= 0) {
-                    const int64_t dst = f1[pivpos[i]]++;
-                    R.L1.idx[dst] = static_cast<int32_t>(k);
-                    R.L1.val[dst] = Lv[e];
-                } else {
-                    const int64_t dst = f2[a2idx[i]]++;
-                    R.L2.idx[dst] = static_cast<int32_t>(k);
-                    R.L2.val[dst] = Lv[e];
-                }
-            }
+        std::vector<int32_t> label(static_cast<size_t>(m));
+        for (int64_t i = 0; i < m; ++i)
+            label[i] = pivpos[i] >= 0 ? pivpos[i] : static_cast<int32_t>(n + a2idx[i]);
+        HostCSR LL;
+        transpose_into(n, m, Lp.data(), Li.data(), Lv.data(), label.data(), threads, LL);
+        const int64_t cut = LL.ptr[n];
+        R.L1.rows = n; R.L1.cols = n;
+        R.L1.ptr.assign(LL.ptr.begin(), LL.ptr.begin() + n + 1);
+        R.L1.idx.assign(LL.idx.begin(), LL.idx.begin() + cut);
+        R.L1.val.assign(LL.val.begin(), LL.val.begin() + cut);
+        R.L2.rows = m2; R.L2.cols = n;
+        R.L2.ptr.resize(static_cast<size_t>(m2) + 1);
+        for (int64_t r = 0; r <= m2; ++r) R.L2.ptr[r] = LL.ptr[n + r] - cut;
+        R.L2.idx.assign(LL.idx.begin() + cut, LL.idx.end());
+        R.L2.val.assign(LL.val.begin() + cut, LL.val.end());
     }
-    R.U.rows = n; R.U.cols = n;
-    R.U.ptr.assign(static_cast<size_t>(n) + 1, 0);
-    for (const int32_t k : Ui) R.U.ptr[k + 1]++;
-    for (int64_t k = 0; k < n; ++k) R.U.ptr[k + 1] += R.U.ptr[k];
-    R.U.idx.resize(Ui.size());
-    R.U.val.resize(Ui.size());
-    {
-        std::vector<int64_t> fu(R.U.ptr.begin(), R.U.ptr.end() - 1);
-        for (int64_t jj = 0; jj < n; ++jj)
-            for (int64_t e = Up[jj]; e < Up[jj + 1]; ++e) {
-                const int64_t dst = fu[Ui[e]]++;
-                R.U.idx[dst] = static_cast<int32_t>(jj);
-                R.U.val[dst] = Uv[e];
-            }
-    }
+    transpose_into(n, n, Up.data(), Ui.data(), Uv.data(), nullptr, threads, R.U);
     // transposes and level sets: independent of each other, built on three
     // threads (each result is deterministic)
     {
@@ -920,7 +962,8 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     }
 
     // scaled matrix by columns, rows ascending in each column
-    HostCSR ac = transpose(a);
+    HostCSR ac;
+    transpose_into(a.rows, a.cols, a.ptr.data(), a.idx.data(), a.val.data(), nullptr, prm.threads, ac);
     for (int64_t j = 0; j < n; ++j) {
         if (ac.ptr[j + 1] == ac.ptr[j]) throw std::runtime_error("A has an empty column");
         for (int64_t e = ac.ptr[j]; e < ac.ptr[j + 1]; ++e) ac.val[e] = ac.val[e] * R.d[j];
@@ -946,7 +989,7 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
         }
     }
     if (serial) columns_serial(a, ac, prm, R, C);
-    split_and_analyse(R, C);
+    split_and_analyse(R, C, prm.threads);
     return R;
 }
 
