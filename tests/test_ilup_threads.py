@@ -134,3 +134,12 @@ def test_thread_count_rule():
     # working arrays of 16 bytes per row: 2 GiB holds one thread's at 2^27 rows
     assert lib.rlsq_setup_threads(8, 1 << 27, 1 << 20) == 1
     assert lib.rlsq_setup_threads(8, 1 << 25, 1 << 20) == 4
+
+
+def test_threads_bitexact_blocked_transposes():
+    """Large enough (about 800k entries in A) that the set-up's transposes
+    split into several blocks of rows on several threads."""
+    prob = synth.config_problem(1, scale=0.05)
+    assert prob.rowptr[-1] > 4 * (1 << 18)
+    ref = setup_arrays(prob, 1, p=10, tau=1e-2, mu=1.0)
+    assert_same(setup_arrays(prob, 8, p=10, tau=1e-2, mu=1.0), ref)
