@@ -140,6 +140,6 @@ def test_threads_bitexact_blocked_transposes():
     """Large enough (about 800k entries in A) that the set-up's transposes
     split into several blocks of rows on several threads."""
     prob = synth.config_problem(1, scale=0.05)
-    assert prob.rowptr[-1] > 4 * (1 << 18)
+    assert prob.rowptr[-1] > 2 * (1 << 18)  # at least 3 blocks
     ref = setup_arrays(prob, 1, p=10, tau=1e-2, mu=1.0)
     assert_same(setup_arrays(prob, 8, p=10, tau=1e-2, mu=1.0), ref)
