@@ -143,3 +143,18 @@ def test_threads_bitexact_blocked_transposes():
     assert prob.rowptr[-1] > 2 * (1 << 18)  # at least 3 blocks
     ref = setup_arrays(prob, 1, p=10, tau=1e-2, mu=1.0)
     assert_same(setup_arrays(prob, 8, p=10, tau=1e-2, mu=1.0), ref)
+
+
+@pytest.mark.parametrize("case", ["sparse_dense", "tall", "long_columns"])
+def test_threads_bitexact_stress(case):
+    """Heavy columns (dense rows in A), tall matrices (m = 40 n) and long L
+    columns (no drop tolerance, p = 60)."""
+    if case == "sparse_dense":
+        prob, kw = synth.sparse_dense_problem(6000, 3000, 6, 20, seed=2), dict(p=10, tau=1e-2, mu=1.0)
+    elif case == "tall":
+        prob, kw = synth.sparse_problem(40 * 400, 400, 5, seed=31), dict(p=10, tau=1e-3, mu=0.1)
+    else:
+        prob, kw = synth.sparse_problem(3000, 1500, 7, seed=32), dict(p=60, tau=0.0, mu=0.5)
+    ref = setup_arrays(prob, 1, **kw)
+    for t in (3, 8):
+        assert_same(setup_arrays(prob, t, **kw), ref)
