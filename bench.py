@@ -32,7 +32,17 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FACTOR = dict(p=10, tau=1e-2, mu=1.0, small=1e-10, correction=2, cg_steps=2)
+def host_threads():
+    """Host threads for one rank's set-up: this process's CPUs shared among
+    the ranks on the node."""
+    try:
+        cpus = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cpus = os.cpu_count() or 1
+    return max(1, cpus // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", "1"))))
+
+
+FACTOR = dict(p=10, tau=1e-2, mu=1.0, small=1e-10, correction=2, cg_steps=2, host_threads=host_threads())
 WORKLOAD = ("sparse LS m=2,000,000 n=1,000,000, 8 N(0,1) nnz/row + hidden +-4 diagonal (seed 1); "
             "ILUP(p=10, tau=1e-2, mu=1) row split, CG(2) correction; LSMR, atol 1e-8")
 
@@ -349,7 +359,8 @@ def factor_all(problems, threads=None, **kw):
 
     def one(p):
         P = B.Problem.from_problem(p)
-        P.factor(**kw)
+        # the pool already runs one set-up per CPU
+        P.factor(**{"host_threads": 1, **kw})
         return P
 
     with ThreadPoolExecutor(threads or os.cpu_count() or 4) as ex:
