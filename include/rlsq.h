@@ -119,7 +119,8 @@ typedef struct {
                               columns, the same factor bit for bit for any count) and the dense
                               S; <= 0 = the CPUs the process may run on (the ILUP takes at most 16, and
                               fewer where its per-thread arrays, 16 bytes per row of A, would
-                              pass 2 GiB) */
+                              pass 2 GiB); set-ups running at the same time should each get a
+                              share of the CPUs */
     int32_t level_merge;   /* levels fused per group in the triangular solves: 1 = none,
                               k > 1 = groups of k levels (same-group dependencies are
                               substituted on the host), 0 = chosen per system by a
