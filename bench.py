@@ -152,42 +152,54 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(cpu_scale: float, full_nnz: int, iters_target_s: float = 12.0):
+class OracleSample:
     """The oracle as it stands (single thread) on the same recipe at a smaller
-    size; iterations/s scaled to the full workload by the nonzero ratio."""
-    import numpy as np
+    size, factored once; run(its) times `its` LSMR+CG(2) iterations from x = 0
+    and gives iterations/s scaled to the full workload by the nonzero ratio."""
 
-    import oracle
-    from paper_2603_28642_gb300 import synth
+    def __init__(self, cpu_scale: float, full_nnz: int):
+        import oracle
+        from paper_2603_28642_gb300 import synth
 
-    prob = synth.config_problem(1, scale=cpu_scale)
-    f = oracle.Factor(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, p=FACTOR["p"],
-                      tau=FACTOR["tau"], mu=FACTOR["mu"], small=FACTOR["small"])
-    f.set_correction(oracle.CG, FACTOR["cg_steps"])
-    anorm = oracle.norm2(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals)
-    # calibrate, then time a run of ~iters_target_s seconds
-    t0 = time.perf_counter()
-    oracle.lsmr(f, prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, prob.b, anorm=anorm,
-                atol=0.0, maxit=2)
-    per = (time.perf_counter() - t0) / 3.0
-    its = max(3, int(iters_target_s / max(per, 1e-6)))
-    t0 = time.perf_counter()
-    r = oracle.lsmr(f, prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, prob.b, anorm=anorm,
-                    atol=0.0, maxit=its)
-    dt = time.perf_counter() - t0
-    # r.its iterations plus one stopping check per iterate
-    its_per_s_sample = r.its / dt
-    factor = prob.nnz / full_nnz
-    del np
-    return {
-        "value": its_per_s_sample * factor,
-        "unit": "iter/s",
-        "cores": 1,
-        "kind": "oracle",
-        "sample": (f"config-1 recipe at scale {cpu_scale} (m={prob.m:,}, n={prob.n:,}, "
-                   f"nnz={prob.nnz:,}); {r.its} LSMR+CG(2) iterations in {dt:.1f}s on 1 of "
-                   f"{os.cpu_count()} host cores; iter/s scaled by nnz ratio {factor:.4f}"),
-    }
+        self.oracle = oracle
+        self.scale = cpu_scale
+        self.prob = synth.config_problem(1, scale=cpu_scale)
+        p = self.prob
+        self.f = oracle.Factor(p.m, p.n, p.rowptr, p.colidx, p.vals, p=FACTOR["p"], tau=FACTOR["tau"],
+                               mu=FACTOR["mu"], small=FACTOR["small"])
+        self.f.set_correction(oracle.CG, FACTOR["cg_steps"])
+        self.anorm = oracle.norm2(p.m, p.n, p.rowptr, p.colidx, p.vals)
+        self.factor = p.nnz / full_nnz
+
+    def run(self, its: int):
+        p = self.prob
+        t0 = time.perf_counter()
+        r = self.oracle.lsmr(self.f, p.m, p.n, p.rowptr, p.colidx, p.vals, p.b, anorm=self.anorm, atol=0.0,
+                             maxit=its)
+        return r.its, time.perf_counter() - t0
+
+    def seconds_per_iteration(self):
+        its, dt = self.run(2)
+        return dt / max(its, 1)
+
+    def describe(self, its: int, dt: float, runs: int = 1):
+        p = self.prob
+        what = f"{its} LSMR+CG(2) iterations in {dt:.1f}s" if runs == 1 else \
+            f"{runs} runs of {its // runs} LSMR+CG(2) iterations in {dt:.1f}s"
+        return (f"config-1 recipe at scale {self.scale} (m={p.m:,}, n={p.n:,}, nnz={p.nnz:,}); {what} on 1 of "
+                f"{os.cpu_count()} host cores; iter/s scaled by nnz ratio {self.factor:.4f}")
+
+    def baseline(self, its: int, dt: float, runs: int = 1):
+        return {"value": its / dt * self.factor, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                "sample": self.describe(its, dt, runs)}
+
+
+def cpu_oracle_sample(cpu_scale: float, full_nnz: int, iters_target_s: float = 12.0):
+    """One bounded run of the oracle on the scaled recipe (about iters_target_s)."""
+    o = OracleSample(cpu_scale, full_nnz)
+    its = max(3, int(iters_target_s / max(o.seconds_per_iteration(), 1e-6)))
+    done, dt = o.run(its)
+    return o.baseline(done, dt)
 
 
 def full_nnz_estimate(scale):
@@ -199,21 +211,30 @@ def full_nnz_estimate(scale):
 
 # ---------------------------------------------------------------------------
 def run_reference(args):
+    """The oracle arm: the same metric on the host cores.  The sample is factored
+    once (untimed, as the GPU arm's set-up is), then `warmup` untimed and
+    `steps` timed steps of a fixed iteration count, sized so that all of them
+    take about two minutes (at most 3 s a step)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    full = full_nnz_estimate(args.scale)
-    steps = []
-    for _ in range(max(1, args.steps)):
-        steps.append(cpu_oracle_sample(args.cpu_scale, full, iters_target_s=3.0))
-        if len(steps) >= 3:
-            break
-    v = statistics.median(s["value"] for s in steps)
-    cb = dict(steps[0])
-    cb["value"] = v
+    o = OracleSample(args.cpu_scale, full_nnz_estimate(args.scale))
+    per = o.seconds_per_iteration()
+    k, w = max(1, args.steps), max(0, args.warmup)
+    step_s = min(3.0, 120.0 / (k + w))
+    its = max(2, int(step_s / max(per, 1e-6)))
+    for _ in range(w):
+        o.run(its)
+    total_its, total_s = 0, 0.0
+    for _ in range(k):
+        done, dt = o.run(its)
+        total_its += done
+        total_s += dt
+    cb = o.baseline(total_its, total_s, runs=k)
+    v = cb["value"]
     out = {
         "impl": "reference", "metric": "preconditioned LSMR iterations/s", "value": v,
-        "unit": "iter/s", "n_gpus": args.gpus, "steps": len(steps), "warmup": 0,
+        "unit": "iter/s", "n_gpus": args.gpus, "steps": k, "warmup": w,
         "ms_per_step": 1000.0 / v if v else None, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "scale": args.scale},
