@@ -39,3 +39,14 @@ def test_reference_arm_contract():
 def test_reference_arm_other_ranks_print_nothing():
     assert run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"],
                      env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_gpu_arm_cpu_baseline_helper():
+    """The GPU arm's cpu_baseline object comes from the same oracle sample."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    cb = bench.cpu_oracle_sample(0.02, bench.full_nnz_estimate(1.0), iters_target_s=1.0)
+    assert set(cb) == {"value", "unit", "cores", "kind", "sample"}
+    assert cb["value"] > 0 and cb["unit"] == "iter/s" and cb["cores"] == 1 and cb["kind"] == "oracle"
+    assert "scale 0.02" in cb["sample"]
