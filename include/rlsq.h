@@ -392,6 +392,14 @@ int rlsq_setup_add_rows(rlsq_setup s, int64_t k, const int64_t *rowptr, const in
    and the remaining rows are renumbered in order (ids above a removed row move
    down).  A pivot row cannot be removed this way: ARG (refactorise). */
 int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t *ids);
+/* S^{-1} of the dense correction (S = I + Z^T Z, Z = L1^{-T} L2^T, eq. 3.9;
+   Lemma 3.1), row-major (m-n) x (m-n) into out.  Formed (through the Cholesky
+   factor of S) on the first call or when recompute != 0; after that the
+   handle keeps it and rlsq_setup_add_rows / rlsq_setup_remove_rows update it
+   by block inversion through the Schur complement (Sec. 3.4), O((m-n)^2) per
+   row, instead of forming it again.  Errors: ARG, NUMERIC (S not positive
+   definite). */
+int rlsq_setup_schur_inverse(rlsq_setup s, int32_t recompute, double *out);
 void rlsq_setup_destroy(rlsq_setup s);
 
 /* Message of the last error on this thread ("" if none). */

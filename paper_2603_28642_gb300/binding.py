@@ -101,7 +101,7 @@ EXPORTS = [
     "rlsq_trsv", "rlsq_get_info", "rlsq_get_split", "rlsq_get_factor", "rlsq_get_levels",
     "rlsq_destroy", "rlsq_server_create", "rlsq_server_register", "rlsq_server_submit",
     "rlsq_server_poll", "rlsq_server_get_stats", "rlsq_server_destroy", "rlsq_last_error",
-    "rlsq_setup_create", "rlsq_setup_threads", "rlsq_setup_sizes", "rlsq_setup_split", "rlsq_setup_factor",
+    "rlsq_setup_create", "rlsq_setup_threads", "rlsq_setup_schur_inverse", "rlsq_setup_sizes", "rlsq_setup_split", "rlsq_setup_factor",
     "rlsq_setup_levels", "rlsq_setup_destroy", "rlsq_profile", "rlsq_trsv_noalloc",
     "rlsq_setup_fuse", "rlsq_setup_fused", "rlsq_setup_add_rows", "rlsq_setup_remove_rows",
     "rlsq_add_rows", "rlsq_remove_rows",
@@ -154,6 +154,7 @@ def load(build_if_missing: bool = True):
             "rlsq_last_error": (C.c_char_p, []),
             "rlsq_setup_create": (C.c_int, [i64, i64, P, P, P, P, P]),
             "rlsq_setup_threads": (C.c_int32, [C.c_int32, C.c_int64, C.c_int64]),
+            "rlsq_setup_schur_inverse": (C.c_int, [P, C.c_int32, P]),
             "rlsq_setup_sizes": (C.c_int, [P, P]),
             "rlsq_setup_split": (C.c_int, [P, P, P, P, P]),
             "rlsq_setup_factor": (C.c_int, [P, i32, P, P, P]),
@@ -520,6 +521,13 @@ class HostSetup:
         _check(load().rlsq_setup_add_rows(self._h, k, _ptr(rp)[0], _ptr(ci if len(ci) else np.zeros(1, np.int32))[0],
                                           _ptr(va if len(va) else np.zeros(1))[0]))
         self.m += k
+
+    def schur_inverse(self, recompute: bool = False):
+        """S^{-1} of the dense correction ((m-n) x (m-n)); kept and updated by row changes."""
+        m2 = self.m - self.n
+        out = np.zeros((m2, m2))
+        _check(load().rlsq_setup_schur_inverse(self._h, int(bool(recompute)), _ptr(out if m2 else np.zeros(1))[0]))
+        return out
 
     def remove_rows(self, ids):
         """Sec. 3.4: remove rows of A2 (ascending ids); raises for a pivot row."""

@@ -190,6 +190,10 @@ struct rlsq_problem_s {
     double ilup_seconds = 0.0;       // the host set-up of the factor in use
     int32_t ilup_threads = 0;
     std::unique_ptr<rlsq::IlupResult> F;
+    // S^{-1} of the dense correction for F, kept on the host once formed so
+    // that row updates can update it (valid only while it belongs to F)
+    std::vector<double> sinv_host;
+    bool sinv_valid = false;
     std::vector<rlsq::MergedTri> merged;  // the four systems as the GPU solves them
     rlsq::DevFactor<double> f64;
     rlsq::DevFactor<float> f32;

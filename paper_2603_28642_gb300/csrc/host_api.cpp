@@ -8,6 +8,8 @@
 #include <vector>
 
 #include "host_setup.h"
+
+#include <algorithm>
 #include "rlsq.h"
 
 namespace rlsq {
@@ -18,6 +20,8 @@ struct rlsq_setup_s {
     rlsq::IlupResult F;
     rlsq::IlupParams prm;   // the drop rule, reused when rows are added
     rlsq::MergedTri fused;  // the last rlsq_setup_fuse result
+    std::vector<double> sinv;  // S^{-1} of the dense correction, once asked for (kept current by row updates)
+    bool has_sinv = false;
 };
 
 namespace {
@@ -227,6 +231,13 @@ int rlsq_setup_add_rows(rlsq_setup s, int64_t k, const int64_t* rowptr, const in
         rows.idx.assign(colidx, colidx + rowptr[k]);
         rows.val.assign(vals, vals + rowptr[k]);
         rlsq::add_rows(s->F, rows, s->prm);
+        if (s->has_sinv) {
+            try {
+                rlsq::schur_inverse_add(s->F, k, s->sinv);
+            } catch (const std::runtime_error&) {
+                s->has_sinv = false;  // formed again when next asked for
+            }
+        }
         return RLSQ_OK;
     });
 }
@@ -235,11 +246,37 @@ int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t* ids) {
     return run([&]() -> int {
         if (!s || (k > 0 && !ids) || k < 0) throw SetupError(RLSQ_ERR_ARG, "bad argument");
         std::vector<int32_t> v(ids, ids + k);
+        const int64_t m2 = s->F.m - s->F.n;
+        std::vector<int64_t> pos;
+        for (const int32_t r : v) {
+            const auto it = std::lower_bound(s->F.a2rows.begin(), s->F.a2rows.end(), r);
+            pos.push_back(it - s->F.a2rows.begin());
+        }
         try {
             rlsq::remove_rows(s->F, v);
         } catch (const std::invalid_argument& e) {
             throw SetupError(RLSQ_ERR_ARG, e.what());
         }
+        if (s->has_sinv) {
+            try {
+                rlsq::schur_inverse_remove(pos, m2, s->sinv);
+            } catch (const std::exception&) {
+                s->has_sinv = false;
+            }
+        }
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_setup_schur_inverse(rlsq_setup s, int32_t recompute, double* out) {
+    return run([&]() -> int {
+        if (!s || !out) throw SetupError(RLSQ_ERR_ARG, "null argument");
+        if (recompute || !s->has_sinv) {
+            if (!rlsq::dense_schur_inverse(s->F, s->sinv, std::max(1, s->prm.threads)))
+                throw SetupError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
+            s->has_sinv = true;
+        }
+        std::copy(s->sinv.begin(), s->sinv.end(), out);
         return RLSQ_OK;
     });
 }

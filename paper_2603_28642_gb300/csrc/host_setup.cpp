@@ -1302,4 +1302,88 @@ bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int thr
     return true;
 }
 
+void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv) {
+    const int64_t n = F.n, m2 = F.m - F.n, s0 = m2 - k;
+    if (k < 0 || s0 < 0 || static_cast<int64_t>(sinv.size()) != s0 * s0)
+        throw std::invalid_argument("the inverse does not match the rows of A2");
+    std::vector<double> X(sinv), z(static_cast<size_t>(n)), w(static_cast<size_t>(n)), b, u, Y;
+    for (int64_t r = s0; r < m2; ++r) {
+        const int64_t sz = r;  // the inverse held is sz x sz
+        // z = L1^{-T} l_r^T: unit upper solve with L1^T, i descending
+        std::fill(z.begin(), z.end(), 0.0);
+        for (int64_t e = F.L2.ptr[r]; e < F.L2.ptr[r + 1]; ++e) z[F.L2.idx[e]] = F.L2.val[e];
+        for (int64_t i = n - 1; i >= 0; --i) {
+            double t = z[i];
+            for (int64_t e = F.L1t.ptr[i]; e < F.L1t.ptr[i + 1]; ++e) t -= F.L1t.val[e] * z[F.L1t.idx[e]];
+            z[i] = t;
+        }
+        // the border b_a = z_a . z = l_a L1^{-1} z for the rows a < r, and the corner 1 + z . z
+        for (int64_t i = 0; i < n; ++i) {
+            double t = z[i];
+            for (int64_t e = F.L1.ptr[i]; e < F.L1.ptr[i + 1]; ++e) t -= F.L1.val[e] * w[F.L1.idx[e]];
+            w[i] = t;
+        }
+        b.assign(static_cast<size_t>(sz), 0.0);
+        for (int64_t a = 0; a < sz; ++a) {
+            double t = 0.0;
+            for (int64_t e = F.L2.ptr[a]; e < F.L2.ptr[a + 1]; ++e) t += F.L2.val[e] * w[F.L2.idx[e]];
+            b[a] = t;
+        }
+        double c = 1.0;
+        for (int64_t i = 0; i < n; ++i) c += z[i] * z[i];
+        // u = S^{-1} b, sigma = c - b . u; the new inverse is
+        // [X + u u^T / sigma, -u / sigma; -u^T / sigma, 1 / sigma]
+        u.assign(static_cast<size_t>(sz), 0.0);
+        for (int64_t a = 0; a < sz; ++a) {
+            double t = 0.0;
+            for (int64_t q = 0; q < sz; ++q) t += X[a * sz + q] * b[q];
+            u[a] = t;
+        }
+        double sigma = c;
+        for (int64_t a = 0; a < sz; ++a) sigma -= b[a] * u[a];
+        if (!(sigma > 0.0)) throw std::runtime_error("the bordered S is not positive definite");
+        const int64_t nz = sz + 1;
+        Y.assign(static_cast<size_t>(nz * nz), 0.0);
+        for (int64_t a = 0; a < sz; ++a) {
+            for (int64_t q = 0; q < sz; ++q) Y[a * nz + q] = X[a * sz + q] + u[a] * u[q] / sigma;
+            Y[a * nz + sz] = -u[a] / sigma;
+            Y[sz * nz + a] = -u[a] / sigma;
+        }
+        Y[sz * nz + sz] = 1.0 / sigma;
+        X.swap(Y);
+    }
+    sinv.swap(X);
+}
+
+void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vector<double>& sinv) {
+    if (static_cast<int64_t>(sinv.size()) != m2 * m2) throw std::invalid_argument("the inverse does not match");
+    for (size_t t = 0; t < pos.size(); ++t)
+        if (pos[t] < 0 || pos[t] >= m2 || (t > 0 && pos[t] <= pos[t - 1]))
+            throw std::invalid_argument("positions must be ascending, distinct and in range");
+    std::vector<double> X(sinv), Y;
+    int64_t sz = m2;
+    // the inverse of S without row and column i is X - X(:, i) X(i, :) / X(i, i)
+    // with row and column i dropped; the last position first keeps the others
+    for (size_t t = pos.size(); t-- > 0;) {
+        const int64_t i = pos[t];
+        const double g = X[i * sz + i];
+        if (!(g > 0.0)) throw std::runtime_error("the inverse of S is not positive definite");
+        const int64_t nz = sz - 1;
+        Y.assign(static_cast<size_t>(nz * nz), 0.0);
+        for (int64_t a = 0, ya = 0; a < sz; ++a) {
+            if (a == i) continue;
+            const double f = X[a * sz + i] / g;
+            for (int64_t q = 0, yq = 0; q < sz; ++q) {
+                if (q == i) continue;
+                Y[ya * nz + yq] = X[a * sz + q] - f * X[i * sz + q];
+                ++yq;
+            }
+            ++ya;
+        }
+        X.swap(Y);
+        sz = nz;
+    }
+    sinv.swap(X);
+}
+
 }  // namespace rlsq

@@ -121,4 +121,17 @@ MergedTri merge_levels_adaptive(const HostCSR& strict, const double* diag, const
 // factor; row-major (m-n)^2.  Returns false if S is not numerically SPD.
 bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads);
 
+// Sec. 3.4 for the dense correction: a row joining A2 borders S with one row
+// and column, and a row leaving A2 takes its row and column away, so S^{-1}
+// follows by block inversion through the Schur complement in O((m-n)^2) per
+// row instead of being formed again.  S's eigenvalues are >= 1, so every
+// Schur complement is >= 1.
+// schur_inverse_add: F already holds the k added rows as the last rows of L2;
+// sinv is the inverse for the first m-n-k rows on entry.  Throws
+// std::runtime_error if a Schur complement is not positive.
+void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv);
+// schur_inverse_remove: `pos` are the removed rows' positions in A2 (before the
+// removal, ascending), sinv the inverse for all m2 rows on entry.
+void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vector<double>& sinv);
+
 }  // namespace rlsq

@@ -1115,6 +1115,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
             F = std::move(h->F);
         } else {
             h->F.reset();
+            h->sinv_valid = false;
             try {
                 const auto t_ilup = std::chrono::steady_clock::now();
                 F.reset(new IlupResult(ilup_factor(h->A, prm)));
@@ -1130,10 +1131,16 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         if (corr == RLSQ_CORR_AUTO) corr = (m2 <= opts.dense_cap) ? RLSQ_CORR_DENSE : RLSQ_CORR_CG;
         std::vector<double> sinv;
         if (corr == RLSQ_CORR_DENSE) {
-            int th = opts.host_threads > 0 ? opts.host_threads
-                                           : static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
-            if (!dense_schur_inverse(*F, sinv, th))
-                throw ApiError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
+            if (h->sinv_valid) {
+                sinv = h->sinv_host;  // formed for this factor, or updated with its rows
+            } else {
+                int th = opts.host_threads > 0 ? opts.host_threads
+                                               : static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+                if (!dense_schur_inverse(*F, sinv, th))
+                    throw ApiError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
+                h->sinv_host = sinv;
+                h->sinv_valid = true;
+            }
         }
         cudaStream_t st = h->stream;
         // fused levels per system (0: the grouping of least modelled time
@@ -1266,6 +1273,13 @@ int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t* rowptr, const int32_
         prm.small = h->opts.small;
         prm.scale = h->opts.scale_columns != 0;
         add_rows(*h->F, rows, prm);
+        if (h->sinv_valid) {
+            try {
+                schur_inverse_add(*h->F, k, h->sinv_host);
+            } catch (const std::runtime_error&) {
+                h->sinv_valid = false;  // formed again by the refresh if needed
+            }
+        }
         HostCSR& A = h->A;
         const int64_t base = A.nnz();
         for (int64_t i = 0; i < k; ++i) A.ptr.push_back(base + rowptr[i + 1]);
@@ -1283,10 +1297,22 @@ int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t* ids) {
         if (h->served.load() > 0) throw ApiError(RLSQ_ERR_ARG, "the problem is registered with a server");
         if (!h->factored || !h->F) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
         std::vector<int32_t> v(ids, ids + k);
+        // positions of the rows in A2 before the removal (for S^{-1})
+        const int64_t m2_before = h->F->m - h->F->n;
+        std::vector<int64_t> pos;
+        for (const int32_t r : v)
+            pos.push_back(std::lower_bound(h->F->a2rows.begin(), h->F->a2rows.end(), r) - h->F->a2rows.begin());
         try {
             remove_rows(*h->F, v);
         } catch (const std::invalid_argument& e) {
             throw ApiError(RLSQ_ERR_ARG, e.what());
+        }
+        if (h->sinv_valid) {
+            try {
+                schur_inverse_remove(pos, m2_before, h->sinv_host);
+            } catch (const std::exception&) {
+                h->sinv_valid = false;
+            }
         }
         HostCSR& A = h->A;
         HostCSR B;

@@ -87,3 +87,27 @@ def test_registered_problem_refuses_changes():
     assert P.m == p.m
     srv.close()
     assert P.add_rows(ptr, idx, val)["m"] == p.m + 2
+
+
+def test_dense_correction_follows_row_updates():
+    """With the dense correction the handle updates S^{-1} with the rows (block
+    inversion, Sec. 3.4) instead of forming it again; its solves match the
+    oracle, which forms S for the updated factor."""
+    p = synth.config_problem(0)
+    P = B.Problem.from_problem(p)
+    P.factor(mu=1.0, correction=B.CORR_DENSE)
+    f = oracle.Factor(p.m, p.n, p.rowptr, p.colidx, p.vals, mu=1.0)
+    ptr, idx, val = new_rows(p.n, 12, 6, seed=21)
+    P.add_rows(ptr, idx, val)
+    assert f.add_rows(ptr, idx, val) == 0
+    f.set_correction(oracle.DENSE)
+    A = sp.vstack([p.to_scipy(), sp.csr_matrix((val, idx, ptr), shape=(12, p.n))]).tocsr()
+    b = np.concatenate([p.b, np.random.default_rng(22).standard_normal(12)])
+    check_against_oracle(P, f, A, b)
+    _, a2 = f.perm()
+    ids = np.sort(np.concatenate([a2[:4], a2[-2:]])).astype(np.int32)
+    P.remove_rows(ids)
+    assert f.remove_rows(ids) == 0
+    f.set_correction(oracle.DENSE)
+    keep = np.setdiff1d(np.arange(A.shape[0]), ids)
+    check_against_oracle(P, f, A[keep].tocsr(), b[keep])
