@@ -256,7 +256,8 @@ int rlsq_get_levels(rlsq_problem h, int32_t which, int32_t *level);
    device factor are rebuilt with the handle's factor options (autotuning
    again if it was on).  b of later solves has the new m.  Errors: ARG (a
    pivot row cannot be removed: refactorise; the handle is registered with a
-   live server), CSR, SHAPE, NOT_FACTORED, OOM, CUDA. */
+   live server), CSR, SHAPE (sizes past 2^31; a removal that would leave no
+   row of A2, i.e. m <= n), NOT_FACTORED, OOM, CUDA. */
 int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t *rowptr, const int32_t *colidx, const double *vals);
 int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t *ids);
 /* Free the handle and its device memory.  A handle registered with a live
@@ -390,7 +391,8 @@ int rlsq_setup_add_rows(rlsq_setup s, int64_t k, const int64_t *rowptr, const in
                         const double *vals);
 /* Sec. 3.4, removing rows of A2: ids ascending and distinct; their L2 rows go
    and the remaining rows are renumbered in order (ids above a removed row move
-   down).  A pivot row cannot be removed this way: ARG (refactorise). */
+   down).  A pivot row cannot be removed this way: ARG (refactorise).  At
+   least one row of A2 must remain (m > n): SHAPE otherwise. */
 int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t *ids);
 /* S^{-1} of the dense correction (S = I + Z^T Z, Z = L1^{-T} L2^T, eq. 3.9;
    Lemma 3.1), row-major (m-n) x (m-n) into out.  Formed (through the Cholesky

@@ -256,6 +256,8 @@ int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t* ids) {
             rlsq::remove_rows(s->F, v);
         } catch (const std::invalid_argument& e) {
             throw SetupError(RLSQ_ERR_ARG, e.what());
+        } catch (const std::length_error& e) {
+            throw SetupError(RLSQ_ERR_SHAPE, e.what());
         }
         if (s->has_sinv) {
             try {

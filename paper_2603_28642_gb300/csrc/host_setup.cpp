@@ -1183,6 +1183,8 @@ void add_rows(IlupResult& F, const HostCSR& rows, const IlupParams& prm) {
 
 void remove_rows(IlupResult& F, const std::vector<int32_t>& ids) {
     const int64_t m = F.m;
+    if (static_cast<int64_t>(ids.size()) >= m - F.n)
+        throw std::length_error("at least one row of A2 must remain (m > n)");
     std::vector<char> gone(static_cast<size_t>(m), 0);
     std::vector<char> pivot(static_cast<size_t>(m), 0);
     for (const int32_t r : F.prow) pivot[static_cast<size_t>(r)] = 1;

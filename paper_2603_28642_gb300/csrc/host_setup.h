@@ -68,7 +68,7 @@ void add_rows(IlupResult& F, const HostCSR& rows, const IlupParams& prm);
 // Sec. 3.4, removing rows of A2 (ids ascending and distinct): their L2 rows
 // go and the remaining rows are renumbered in order.  Throws
 // std::invalid_argument for a pivot row or a bad id (a refactorisation is
-// needed then).
+// needed then) and std::length_error if no row of A2 would remain (m > n).
 void remove_rows(IlupResult& F, const std::vector<int32_t>& ids);
 
 // Column scaling d_j = 1 / ||A_:,j||_2.  Returns false if a column is empty.

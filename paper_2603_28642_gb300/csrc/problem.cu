@@ -1306,6 +1306,8 @@ int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t* ids) {
             remove_rows(*h->F, v);
         } catch (const std::invalid_argument& e) {
             throw ApiError(RLSQ_ERR_ARG, e.what());
+        } catch (const std::length_error& e) {
+            throw ApiError(RLSQ_ERR_SHAPE, e.what());
         }
         if (h->sinv_valid) {
             try {

@@ -129,3 +129,15 @@ def test_ilu_update_still_preconditions(cfg0):
     res = oracle.lsmr(f, A2.shape[0], p.n, A2.indptr, A2.indices, A2.data, b2, atol=1e-8, maxit=2000)
     assert res.status == 0 and res.its < 100
     np.testing.assert_allclose(res.x, np.linalg.lstsq(A2.toarray(), b2, rcond=None)[0], rtol=1e-6)
+
+
+def test_removing_every_row_of_A2_is_refused():
+    """The problem needs m > n (eq. 1.1): at least one row of A2 stays."""
+    prob = synth.sparse_problem(60, 40, 4, seed=3)
+    s = B.HostSetup(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, mu=1.0)
+    _, a2, _, _ = s.split()
+    with pytest.raises(B.RlsqError) as e:
+        s.remove_rows(a2.astype(np.int32))
+    assert e.value.code == -2  # RLSQ_ERR_SHAPE
+    s.remove_rows(a2[1:].astype(np.int32))  # all but one
+    assert s.m == prob.n + 1
