@@ -108,7 +108,8 @@ typedef struct {
     int32_t scale_columns; /* 1: prescale A to unit 2-norm columns (Sec. 5.1) */
     int32_t correction;    /* RLSQ_CORR_* */
     int32_t cg_steps;      /* CG iterations for RLSQ_CORR_CG, >= 1 */
-    int64_t dense_cap;     /* RLSQ_CORR_AUTO uses DENSE when m - n <= dense_cap */
+    int64_t dense_cap;     /* RLSQ_CORR_AUTO uses DENSE when m - n <= dense_cap and the n x (m - n)
+                              float64 buffer that forms S fits in 2 GiB, else CG */
     int32_t precision;     /* RLSQ_PREC_* */
     int32_t trsv_schedule; /* RLSQ_TRSV_* */
     int32_t autotune;      /* 1: time candidate kernel mappings on this matrix */

@@ -1252,19 +1252,52 @@ bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int thr
         for (auto& x : th) x.join();
     };
     par(m2, zcols);
-    // S = I + Z^T Z (lower triangle, row-major)
+    // S = I + Z^T Z (lower triangle, row-major).  Each entry is one running
+    // sum over the rows in ascending order, kept in S between chunks of rows
+    // so that a chunk of every column stays in cache while all pairs use it;
+    // 4 x 4 tiles of column pairs (each owned by one thread) keep 16
+    // independent sums going.
     std::vector<double> S(static_cast<size_t>(m2 * m2), 0.0);
-    par(m2, [&](int64_t a0, int64_t a1) {
-        for (int64_t a = a0; a < a1; ++a) {
-            const double* za = Z.data() + a * n;
-            for (int64_t b = 0; b <= a; ++b) {
-                const double* zb = Z.data() + b * n;
-                double s = 0.0;
-                for (int64_t i = 0; i < n; ++i) s += za[i] * zb[i];
-                S[a * m2 + b] = (a == b) ? 1.0 + s : s;
-            }
+    const int64_t nt = (m2 + 3) / 4;
+    constexpr int64_t kChunk = 512;
+    par(threads, [&](int64_t t0, int64_t t1) {
+        for (int64_t i0 = 0; i0 < n; i0 += kChunk) {
+            const int64_t i1 = std::min(n, i0 + kChunk);
+            int64_t tile = 0;
+            for (int64_t ta = 0; ta < nt; ++ta)
+                for (int64_t tb = 0; tb <= ta; ++tb, ++tile) {
+                    if (tile % threads < t0 || tile % threads >= t1) continue;
+                    const int64_t a0 = 4 * ta, b0 = 4 * tb;
+                    if (a0 + 4 <= m2 && b0 + 4 <= m2) {
+                        double acc[4][4];
+                        for (int x = 0; x < 4; ++x)
+                            for (int y = 0; y < 4; ++y) acc[x][y] = S[(a0 + x) * m2 + b0 + y];
+                        const double* za = Z.data() + a0 * n;
+                        const double* zb = Z.data() + b0 * n;
+                        for (int64_t i = i0; i < i1; ++i) {
+                            const double u0 = za[i], u1 = za[n + i], u2 = za[2 * n + i], u3 = za[3 * n + i];
+                            const double v0 = zb[i], v1 = zb[n + i], v2 = zb[2 * n + i], v3 = zb[3 * n + i];
+                            acc[0][0] += u0 * v0; acc[0][1] += u0 * v1; acc[0][2] += u0 * v2; acc[0][3] += u0 * v3;
+                            acc[1][0] += u1 * v0; acc[1][1] += u1 * v1; acc[1][2] += u1 * v2; acc[1][3] += u1 * v3;
+                            acc[2][0] += u2 * v0; acc[2][1] += u2 * v1; acc[2][2] += u2 * v2; acc[2][3] += u2 * v3;
+                            acc[3][0] += u3 * v0; acc[3][1] += u3 * v1; acc[3][2] += u3 * v2; acc[3][3] += u3 * v3;
+                        }
+                        for (int x = 0; x < 4; ++x)
+                            for (int y = 0; y < 4; ++y) S[(a0 + x) * m2 + b0 + y] = acc[x][y];
+                    } else {
+                        for (int64_t a = a0; a < std::min(m2, a0 + 4); ++a)
+                            for (int64_t b = b0; b < std::min(m2, b0 + 4); ++b) {
+                                const double* za = Z.data() + a * n;
+                                const double* zb = Z.data() + b * n;
+                                double acc = S[a * m2 + b];
+                                for (int64_t i = i0; i < i1; ++i) acc += za[i] * zb[i];
+                                S[a * m2 + b] = acc;
+                            }
+                    }
+                }
         }
     });
+    for (int64_t a = 0; a < m2; ++a) S[a * m2 + a] = 1.0 + S[a * m2 + a];
     Z.clear();
     Z.shrink_to_fit();
     // Cholesky S = G G^T in place (lower)

@@ -1128,7 +1128,12 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         }
         int corr = opts.correction;
         const int64_t m2 = h->m - h->n;
-        if (corr == RLSQ_CORR_AUTO) corr = (m2 <= opts.dense_cap) ? RLSQ_CORR_DENSE : RLSQ_CORR_CG;
+        // the dense S is formed through Z = L1^{-T} L2^T (n x (m-n) float64), so the
+        // automatic choice also keeps that within 2 GiB
+        if (corr == RLSQ_CORR_AUTO)
+            corr = (m2 <= opts.dense_cap && static_cast<double>(h->n) * static_cast<double>(m2) * 8.0 <= 2147483648.0)
+                       ? RLSQ_CORR_DENSE
+                       : RLSQ_CORR_CG;
         std::vector<double> sinv;
         if (corr == RLSQ_CORR_DENSE) {
             if (h->sinv_valid) {
