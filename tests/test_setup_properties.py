@@ -1,0 +1,49 @@
+"""Property-based checks of the host set-up on random small problems (any
+shape with m > n, any p, tau, mu and thread count): the pipelined column loop
+gives the serial loop's factor bit for bit, and the serial loop gives the
+oracle's.  No GPU is used."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_2603_28642_gb300 import binding as B  # noqa: E402
+from paper_2603_28642_gb300 import synth  # noqa: E402
+
+from test_ilup_threads import assert_oracle, assert_same, setup_arrays  # noqa: E402
+
+
+@st.composite
+def problems(draw):
+    n = draw(st.integers(1, 40))
+    m = n + draw(st.integers(1, 30))
+    density = draw(st.floats(0.02, 0.6))
+    seed = draw(st.integers(0, 2**31 - 1))
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) * (rng.random((m, n)) < density)
+    # a repeated row (ties, cancellation); then every column needs an entry
+    if draw(st.booleans()) and m > 1:
+        A[m - 1] = A[0]
+    for j in range(n):
+        if not A[:, j].any():
+            A[rng.integers(0, m), j] = rng.choice([-1.0, 1.0]) * (1 + rng.random())
+    S = sp.csr_matrix(A)
+    prob = synth.Problem(m, n, S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data,
+                         np.zeros(m), np.zeros(n), np.zeros(0, dtype=np.int64))
+    kw = dict(p=draw(st.sampled_from([0, 1, 2, 3, 5, 10, 50])),
+              tau=draw(st.sampled_from([0.0, 1e-3, 1e-2, 0.2])),
+              mu=draw(st.sampled_from([0.05, 0.1, 0.5, 1.0])),
+              scale_columns=draw(st.sampled_from([0, 1])))
+    return prob, kw, draw(st.sampled_from([2, 3, 4, 7, 16]))
+
+
+@settings(max_examples=120, deadline=None, derandomize=True)
+@given(problems())
+def test_pipelined_equals_serial_equals_oracle(case):
+    prob, kw, threads = case
+    ref = setup_arrays(prob, 1, **kw)
+    assert_same(setup_arrays(prob, threads, **kw), ref)
+    assert_oracle(prob, ref, **kw)
