@@ -398,10 +398,12 @@ int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t *ids);
 /* S^{-1} of the dense correction (S = I + Z^T Z, Z = L1^{-T} L2^T, eq. 3.9;
    Lemma 3.1), row-major (m-n) x (m-n) into out.  Formed (through the Cholesky
    factor of S) on the first call or when recompute != 0; after that the
-   handle keeps it and rlsq_setup_add_rows / rlsq_setup_remove_rows update it
-   by block inversion through the Schur complement (Sec. 3.4), O((m-n)^2) per
-   row, instead of forming it again.  Errors: ARG, NUMERIC (S not positive
-   definite). */
+   handle keeps it, with Z while Z (n x (m-n) float64) fits in 2 GiB, and
+   rlsq_setup_add_rows / rlsq_setup_remove_rows update it by block inversion
+   through the Schur complement (Sec. 3.4): O(n (m-n) + (m-n)^2) per added row,
+   O((m-n)^2) per removed row, instead of forming it again (which they do
+   where the update would lose more than 4 digits, or without Z).  Errors:
+   ARG, NUMERIC (S not positive definite). */
 int rlsq_setup_schur_inverse(rlsq_setup s, int32_t recompute, double *out);
 void rlsq_setup_destroy(rlsq_setup s);
 

@@ -193,6 +193,7 @@ struct rlsq_problem_s {
     // S^{-1} of the dense correction for F, kept on the host once formed so
     // that row updates can update it (valid only while it belongs to F)
     std::vector<double> sinv_host;
+    std::vector<double> sinv_z;  // Z = L1^{-T} L2^T beside it (empty: updates form S^{-1} again)
     bool sinv_valid = false;
     std::vector<rlsq::MergedTri> merged;  // the four systems as the GPU solves them
     rlsq::DevFactor<double> f64;

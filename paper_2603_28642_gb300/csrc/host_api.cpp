@@ -21,6 +21,7 @@ struct rlsq_setup_s {
     rlsq::IlupParams prm;   // the drop rule, reused when rows are added
     rlsq::MergedTri fused;  // the last rlsq_setup_fuse result
     std::vector<double> sinv;  // S^{-1} of the dense correction, once asked for (kept current by row updates)
+    std::vector<double> Z;     // Z = L1^{-T} L2^T beside it (empty: row updates form S^{-1} again)
     bool has_sinv = false;
 };
 
@@ -233,8 +234,9 @@ int rlsq_setup_add_rows(rlsq_setup s, int64_t k, const int64_t* rowptr, const in
         rlsq::add_rows(s->F, rows, s->prm);
         if (s->has_sinv) {
             try {
-                rlsq::schur_inverse_add(s->F, k, s->sinv);
-            } catch (const std::runtime_error&) {
+                if (s->Z.empty()) throw std::runtime_error("Z is not kept");
+                rlsq::schur_inverse_add(s->F, k, s->sinv, s->Z);
+            } catch (const std::exception&) {
                 s->has_sinv = false;  // formed again when next asked for
             }
         }
@@ -261,7 +263,8 @@ int rlsq_setup_remove_rows(rlsq_setup s, int64_t k, const int32_t* ids) {
         }
         if (s->has_sinv) {
             try {
-                rlsq::schur_inverse_remove(pos, m2, s->sinv);
+                if (s->Z.empty()) throw std::runtime_error("Z is not kept");
+                rlsq::schur_inverse_remove(pos, m2, s->sinv, s->Z);
             } catch (const std::exception&) {
                 s->has_sinv = false;
             }
@@ -274,7 +277,11 @@ int rlsq_setup_schur_inverse(rlsq_setup s, int32_t recompute, double* out) {
     return run([&]() -> int {
         if (!s || !out) throw SetupError(RLSQ_ERR_ARG, "null argument");
         if (recompute || !s->has_sinv) {
-            if (!rlsq::dense_schur_inverse(s->F, s->sinv, std::max(1, s->prm.threads)))
+            s->has_sinv = false;
+            // Z is kept for later row updates while it fits in 2 GiB
+            const bool keep = static_cast<double>(s->F.n) * static_cast<double>(s->F.m - s->F.n) * 8.0 <= 2147483648.0;
+            s->Z.clear();
+            if (!rlsq::dense_schur_inverse(s->F, s->sinv, std::max(1, s->prm.threads), keep ? &s->Z : nullptr))
                 throw SetupError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
             s->has_sinv = true;
         }

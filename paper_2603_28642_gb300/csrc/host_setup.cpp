@@ -1221,7 +1221,7 @@ void remove_rows(IlupResult& F, const std::vector<int32_t>& ids) {
     F.m = m - static_cast<int64_t>(ids.size());
 }
 
-bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads) {
+bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads, std::vector<double>* keep_z) {
     const int64_t n = f.n, m2 = f.m - f.n;
     if (m2 <= 0) {
         sinv.clear();
@@ -1298,6 +1298,8 @@ bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int thr
         }
     });
     for (int64_t a = 0; a < m2; ++a) S[a * m2 + a] = 1.0 + S[a * m2 + a];
+    if (keep_z)
+        keep_z->swap(Z);
     Z.clear();
     Z.shrink_to_fit();
     // Cholesky S = G G^T in place (lower)
@@ -1337,35 +1339,35 @@ bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int thr
     return true;
 }
 
-void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv) {
+void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv, std::vector<double>& Z) {
     const int64_t n = F.n, m2 = F.m - F.n, s0 = m2 - k;
-    if (k < 0 || s0 < 0 || static_cast<int64_t>(sinv.size()) != s0 * s0)
+    if (k < 0 || s0 < 0 || static_cast<int64_t>(sinv.size()) != s0 * s0 ||
+        static_cast<int64_t>(Z.size()) != s0 * n)
         throw std::invalid_argument("the inverse does not match the rows of A2");
-    std::vector<double> X(sinv), z(static_cast<size_t>(n)), w(static_cast<size_t>(n)), b, u, Y;
+    std::vector<double> X(sinv), ZZ(Z), b, u, Y;
+    ZZ.resize(static_cast<size_t>(m2 * n), 0.0);
     for (int64_t r = s0; r < m2; ++r) {
         const int64_t sz = r;  // the inverse held is sz x sz
-        // z = L1^{-T} l_r^T: unit upper solve with L1^T, i descending
-        std::fill(z.begin(), z.end(), 0.0);
+        // z = L1^{-T} l_r^T (column r of Z): unit upper solve with L1^T, i descending
+        double* z = ZZ.data() + r * n;
         for (int64_t e = F.L2.ptr[r]; e < F.L2.ptr[r + 1]; ++e) z[F.L2.idx[e]] = F.L2.val[e];
         for (int64_t i = n - 1; i >= 0; --i) {
             double t = z[i];
             for (int64_t e = F.L1t.ptr[i]; e < F.L1t.ptr[i + 1]; ++e) t -= F.L1t.val[e] * z[F.L1t.idx[e]];
             z[i] = t;
         }
-        // the border b_a = z_a . z = l_a L1^{-1} z for the rows a < r, and the corner 1 + z . z
-        for (int64_t i = 0; i < n; ++i) {
-            double t = z[i];
-            for (int64_t e = F.L1.ptr[i]; e < F.L1.ptr[i + 1]; ++e) t -= F.L1.val[e] * w[F.L1.idx[e]];
-            w[i] = t;
-        }
+        // the border b_a = z_a . z and the corner 1 + z . z: the entries the
+        // formation of S would compute, summed in the same order
         b.assign(static_cast<size_t>(sz), 0.0);
         for (int64_t a = 0; a < sz; ++a) {
+            const double* za = ZZ.data() + a * n;
             double t = 0.0;
-            for (int64_t e = F.L2.ptr[a]; e < F.L2.ptr[a + 1]; ++e) t += F.L2.val[e] * w[F.L2.idx[e]];
+            for (int64_t i = 0; i < n; ++i) t += z[i] * za[i];
             b[a] = t;
         }
-        double c = 1.0;
-        for (int64_t i = 0; i < n; ++i) c += z[i] * z[i];
+        double zz = 0.0;
+        for (int64_t i = 0; i < n; ++i) zz += z[i] * z[i];
+        const double c = 1.0 + zz;
         // u = S^{-1} b, sigma = c - b . u; the new inverse is
         // [X + u u^T / sigma, -u / sigma; -u^T / sigma, 1 / sigma]
         u.assign(static_cast<size_t>(sz), 0.0);
@@ -1376,7 +1378,9 @@ void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv
         }
         double sigma = c;
         for (int64_t a = 0; a < sz; ++a) sigma -= b[a] * u[a];
-        if (!(sigma > 0.0)) throw std::runtime_error("the bordered S is not positive definite");
+        // sigma >= 1 in exact arithmetic; computed as c - b.u it keeps about
+        // log10(c / sigma) fewer digits, so past 4 the inverse is formed again
+        if (!(sigma > 0.0) || c > 1e4 * sigma) throw std::runtime_error("the bordered S loses too many digits");
         const int64_t nz = sz + 1;
         Y.assign(static_cast<size_t>(nz * nz), 0.0);
         for (int64_t a = 0; a < sz; ++a) {
@@ -1388,10 +1392,14 @@ void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv
         X.swap(Y);
     }
     sinv.swap(X);
+    Z.swap(ZZ);
 }
 
-void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vector<double>& sinv) {
-    if (static_cast<int64_t>(sinv.size()) != m2 * m2) throw std::invalid_argument("the inverse does not match");
+void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vector<double>& sinv,
+                          std::vector<double>& Z) {
+    if (static_cast<int64_t>(sinv.size()) != m2 * m2 || (m2 > 0 && Z.size() % static_cast<size_t>(m2) != 0))
+        throw std::invalid_argument("the inverse does not match");
+    const int64_t n = m2 > 0 ? static_cast<int64_t>(Z.size()) / m2 : 0;
     for (size_t t = 0; t < pos.size(); ++t)
         if (pos[t] < 0 || pos[t] >= m2 || (t > 0 && pos[t] <= pos[t - 1]))
             throw std::invalid_argument("positions must be ascending, distinct and in range");
@@ -1403,6 +1411,13 @@ void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vect
         const int64_t i = pos[t];
         const double g = X[i * sz + i];
         if (!(g > 0.0)) throw std::runtime_error("the inverse of S is not positive definite");
+        // a diagonal entry that shrinks by more than 10^4 has lost that many
+        // digits: the inverse is formed again instead
+        for (int64_t a = 0; a < sz; ++a) {
+            if (a == i) continue;
+            const double keep = X[a * sz + a] - X[a * sz + i] * X[a * sz + i] / g;
+            if (!(keep > 1e-4 * X[a * sz + a])) throw std::runtime_error("the reduced S loses too many digits");
+        }
         const int64_t nz = sz - 1;
         Y.assign(static_cast<size_t>(nz * nz), 0.0);
         for (int64_t a = 0, ya = 0; a < sz; ++a) {
@@ -1418,7 +1433,18 @@ void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vect
         X.swap(Y);
         sz = nz;
     }
+    // Z loses the same columns
+    std::vector<double> ZZ;
+    ZZ.reserve(static_cast<size_t>(sz * n));
+    for (int64_t c = 0, t = 0; c < m2; ++c) {
+        if (t < static_cast<int64_t>(pos.size()) && pos[static_cast<size_t>(t)] == c) {
+            ++t;
+            continue;
+        }
+        ZZ.insert(ZZ.end(), Z.begin() + c * n, Z.begin() + (c + 1) * n);
+    }
     sinv.swap(X);
+    Z.swap(ZZ);
 }
 
 }  // namespace rlsq

@@ -119,19 +119,25 @@ MergedTri merge_levels_adaptive(const HostCSR& strict, const double* diag, const
 
 // Dense inverse of S = I + Z^T Z, Z = L1^{-T} L2^T, through its Cholesky
 // factor; row-major (m-n)^2.  Returns false if S is not numerically SPD.
-bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads);
+// keep_z (if not null) receives Z, column-major n x (m-n).
+bool dense_schur_inverse(const IlupResult& f, std::vector<double>& sinv, int threads,
+                         std::vector<double>* keep_z = nullptr);
 
 // Sec. 3.4 for the dense correction: a row joining A2 borders S with one row
 // and column, and a row leaving A2 takes its row and column away, so S^{-1}
-// follows by block inversion through the Schur complement in O((m-n)^2) per
-// row instead of being formed again.  S's eigenvalues are >= 1, so every
-// Schur complement is >= 1.
+// follows by block inversion through the Schur complement instead of being
+// formed again: O(n (m-n) + (m-n)^2) per added row (the border is z_a . z
+// with the columns of Z, which the caller keeps beside S^{-1}, and z
+// = L1^{-T} l^T; exactly the entries a new formation would compute), O((m-n)^2)
+// per removed row.  S's eigenvalues are >= 1, so every Schur complement is
+// >= 1; both updates throw std::runtime_error (the caller then forms the
+// inverse again) where their subtractions would cancel more than 4 digits.
 // schur_inverse_add: F already holds the k added rows as the last rows of L2;
-// sinv is the inverse for the first m-n-k rows on entry.  Throws
-// std::runtime_error if a Schur complement is not positive.
-void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv);
+// sinv and Z belong to the first m-n-k rows on entry, to all rows on return.
+void schur_inverse_add(const IlupResult& F, int64_t k, std::vector<double>& sinv, std::vector<double>& Z);
 // schur_inverse_remove: `pos` are the removed rows' positions in A2 (before the
-// removal, ascending), sinv the inverse for all m2 rows on entry.
-void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vector<double>& sinv);
+// removal, ascending); sinv and Z belong to all m2 rows on entry.
+void schur_inverse_remove(const std::vector<int64_t>& pos, int64_t m2, std::vector<double>& sinv,
+                          std::vector<double>& Z);
 
 }  // namespace rlsq

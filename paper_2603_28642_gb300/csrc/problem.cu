@@ -1141,7 +1141,9 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
             } else {
                 int th = opts.host_threads > 0 ? opts.host_threads
                                                : static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
-                if (!dense_schur_inverse(*F, sinv, th))
+                const bool keep = static_cast<double>(F->n) * static_cast<double>(F->m - F->n) * 8.0 <= 2147483648.0;
+                h->sinv_z.clear();
+                if (!dense_schur_inverse(*F, sinv, th, keep ? &h->sinv_z : nullptr))
                     throw ApiError(RLSQ_ERR_NUMERIC, "dense S is not positive definite");
                 h->sinv_host = sinv;
                 h->sinv_valid = true;
@@ -1280,8 +1282,9 @@ int rlsq_add_rows(rlsq_problem h, int64_t k, const int64_t* rowptr, const int32_
         add_rows(*h->F, rows, prm);
         if (h->sinv_valid) {
             try {
-                schur_inverse_add(*h->F, k, h->sinv_host);
-            } catch (const std::runtime_error&) {
+                if (h->sinv_z.empty()) throw std::runtime_error("Z is not kept");
+                schur_inverse_add(*h->F, k, h->sinv_host, h->sinv_z);
+            } catch (const std::exception&) {
                 h->sinv_valid = false;  // formed again by the refresh if needed
             }
         }
@@ -1316,7 +1319,8 @@ int rlsq_remove_rows(rlsq_problem h, int64_t k, const int32_t* ids) {
         }
         if (h->sinv_valid) {
             try {
-                schur_inverse_remove(pos, m2_before, h->sinv_host);
+                if (h->sinv_z.empty()) throw std::runtime_error("Z is not kept");
+                schur_inverse_remove(pos, m2_before, h->sinv_host, h->sinv_z);
             } catch (const std::exception&) {
                 h->sinv_valid = false;
             }

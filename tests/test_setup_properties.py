@@ -47,3 +47,43 @@ def test_pipelined_equals_serial_equals_oracle(case):
     ref = setup_arrays(prob, 1, **kw)
     assert_same(setup_arrays(prob, threads, **kw), ref)
     assert_oracle(prob, ref, **kw)
+
+
+def _same_split_and_l2(s, f):
+    prow, a2, _, _ = s.split()
+    oprow, oa2 = f.perm()
+    assert np.array_equal(prow, oprow) and np.array_equal(a2, oa2)
+    ptr, idx, val = s.factor_csr(B.PART_L2)
+    L2 = f.L2()
+    assert np.array_equal(ptr, L2.ptr) and np.array_equal(idx, L2.idx) and np.array_equal(val, L2.val)
+
+
+@settings(max_examples=60, deadline=None, derandomize=True)
+@given(problems(), st.integers(0, 6), st.integers(0, 2**31 - 1), st.floats(0.0, 1.0))
+def test_row_updates_match_oracle_and_keep_schur_inverse(case, k, seed, frac):
+    """Rows added (Sec. 3.4) and then some rows of A2 removed: the library's
+    updated factor equals the oracle's bit for bit, and the S^{-1} it keeps
+    through the updates equals S^{-1} formed again for the updated factor."""
+    prob, kw, threads = case
+    okw = {x: kw[x] for x in ("p", "tau", "mu")}
+    s = B.HostSetup(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, host_threads=threads, **kw)
+    f = oracle.Factor(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, scale=kw["scale_columns"], **okw)
+    s.schur_inverse()  # held from here on
+    rng = np.random.default_rng(seed)
+    rows = [np.sort(rng.choice(prob.n, size=int(rng.integers(1, min(prob.n, 5) + 1)), replace=False))
+            for _ in range(k)]
+    ptr = np.zeros(k + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum([len(r) for r in rows])
+    idx = np.concatenate(rows).astype(np.int32) if k else np.zeros(0, np.int32)
+    val = rng.standard_normal(int(ptr[-1]))
+    s.add_rows(ptr, idx, val)
+    assert f.add_rows(ptr, idx, val, p=kw["p"], tau=kw["tau"]) == 0
+    _same_split_and_l2(s, f)
+    _, a2, _, _ = s.split()
+    drop = np.sort(rng.choice(a2, size=int(frac * (len(a2) - 1)), replace=False)).astype(np.int32)
+    s.remove_rows(drop)
+    assert f.remove_rows(drop) == 0
+    _same_split_and_l2(s, f)
+    held = s.schur_inverse()
+    fresh = s.schur_inverse(recompute=True)
+    assert np.linalg.norm(held - fresh) <= 1e-9 * np.linalg.norm(fresh)
