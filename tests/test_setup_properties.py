@@ -87,3 +87,36 @@ def test_row_updates_match_oracle_and_keep_schur_inverse(case, k, seed, frac):
     held = s.schur_inverse()
     fresh = s.schur_inverse(recompute=True)
     assert np.linalg.norm(held - fresh) <= 1e-9 * np.linalg.norm(fresh)
+
+
+@settings(max_examples=80, deadline=None, derandomize=True)
+@given(problems(), st.sampled_from([0, 2, 3, 5]))
+def test_fused_systems_solve_the_original(case, k):
+    """Level fusion on random factors: the fused rows, taken in level order,
+    solve the original triangular system (small backward error), every
+    remaining dependency lies in an earlier group, and no levels are added."""
+    from test_level_fusion import fused_solve
+
+    prob, kw, threads = case
+    s = B.HostSetup(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, host_threads=threads, **kw)
+    n = prob.n
+    Lp, Li, Lv = s.factor_csr(B.PART_L1)
+    Up, Ui, Uv = s.factor_csr(B.PART_U)
+    L = sp.csr_matrix((Lv, Li, Lp), shape=(n, n))
+    U = sp.csr_matrix((Uv, Ui, Up), shape=(n, n))
+    _, _, _, ud = s.split()
+    rng = np.random.default_rng(n)
+    for which, S, d in ((B.SYS_L1, L, np.ones(n)), (B.SYS_L1T, L.T.tocsr(), np.ones(n)),
+                        (B.SYS_U, U, ud), (B.SYS_UT, U.T.tocsr(), ud)):
+        lev = s.levels(which)
+        sizes, T, R = s.fuse(which, k)
+        assert sizes["levels"] <= int(lev.max()) + 1
+        Tp, Ti, _ = T
+        rows = np.repeat(np.arange(n), np.diff(Tp))
+        assert np.all((lev[Ti] // k < lev[rows] // k) if k > 0 else (lev[Ti] < lev[rows]))
+        b = rng.standard_normal(n)
+        x = fused_solve(n, T, R, d, lev, b)
+        A = (S + sp.diags(d)).tocsr()
+        res = np.linalg.norm(A @ x - b)
+        scale = abs(A).sum(axis=1).max() * np.linalg.norm(x) + np.linalg.norm(b)
+        assert res <= 1e-10 * scale, (which, k)
