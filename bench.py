@@ -350,6 +350,20 @@ def run_ours(args):
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_extras:
+        # CG steps on the implicit S (Algorithm 3, step 2; the paper uses 2): time
+        # to tolerance with 3 and 4 steps, float64, on the same host factor
+        more = {}
+        for k in (3, 4):
+            try:
+                P.factor(**{**FACTOR, "cg_steps": k}, precision=B.PREC_FP64, autotune=1)
+                r = P.solve(prob.b, allow_fail=True)
+                more[f"cg{k}"] = {"iterations": r.info["iterations"], "seconds": r.info["solve_seconds"],
+                                  "ratio": r.info["ratio"], "status": r.status,
+                                  "x_rel_diff_vs_cg2": float(np.linalg.norm(r.x - x64) / np.linalg.norm(x64))}
+            except Exception as e:  # recorded, so the headline line still prints
+                more[f"cg{k}"] = {"error": f"{type(e).__name__}: {e}"}
+        out["time_to_tol"]["fp64_more_cg_steps"] = more
     del P
     if rank == 0 and not args.no_extras:
         # the other forms, sampled so the default run stays within minutes
