@@ -391,3 +391,16 @@ def test_fused_levels_batch_and_noalloc(cfg0):
     B.trsv_noalloc(P, B.SYS_U, bd, xd)
     torch.cuda.synchronize()
     assert rel(xd.cpu().numpy(), f.solve_U(b)) <= 1e-12
+
+
+@pytest.mark.parametrize("steps", [1, 3, 4])
+def test_apply_and_solve_other_cg_step_counts(cfg0, steps):
+    """CG(k) on the implicit S with k other than 2 (more loop steps of the same
+    kernels): one apply within 1e-12 and the solve against the oracle's CG(k)."""
+    P = make(cfg0, B.CORR_CG, cg_steps=steps)
+    f = oracle_factor(cfg0, oracle.CG, steps=steps)
+    b = np.random.default_rng(40 + steps).standard_normal(cfg0.n)
+    assert rel(P.apply(b), f.apply(b)) <= 1e-12
+    ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
+    res = P.solve(cfg0.b)
+    _check_solve(cfg0, res, ref)
