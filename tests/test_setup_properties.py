@@ -120,3 +120,41 @@ def test_fused_systems_solve_the_original(case, k):
         res = np.linalg.norm(A @ x - b)
         scale = abs(A).sum(axis=1).max() * np.linalg.norm(x) + np.linalg.norm(b)
         assert res <= 1e-10 * scale, (which, k)
+
+
+@settings(max_examples=80, deadline=None, derandomize=True)
+@given(problems())
+def test_oracle_nodrop_pins_on_random_problems(case):
+    """The oracle with nothing dropped (p < 0, tau = 0), on random shapes:
+    the exact threshold-pivoted LU (L1 U = P A D, L2 U = A2 D, multipliers
+    bounded by 1/mu), the dense-correction apply to A^T b is the least-squares
+    solution (Sec. 3.1, Lemma 3.1), and the NONE apply is (A1^T A1)^{-1}."""
+    from hypothesis import assume
+
+    prob, kw, _ = case
+    mu = kw["mu"]
+    f = oracle.Factor(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, p=-1, tau=0.0, mu=mu,
+                      scale=kw["scale_columns"])
+    assume(f.sizes()["nmod"] == 0)
+    A = prob.to_scipy().toarray()
+    assume(np.linalg.cond(A) < 1e6)
+    prow, a2 = f.perm()
+    n = prob.n
+    L1 = f.L1().to_scipy().toarray() + np.eye(n)
+    L2 = f.L2().to_scipy().toarray()
+    Uc, ud = f.U()
+    U = Uc.to_scipy().toarray() + np.diag(ud)
+    Ah = A * f.scaling()
+    tol = 1e-12 * max(1.0, np.abs(Ah).max()) * n
+    np.testing.assert_allclose(L1 @ U, Ah[prow], rtol=0, atol=tol)
+    np.testing.assert_allclose(L2 @ U, Ah[a2], rtol=0, atol=tol)
+    assert np.abs(L1).max() <= 1.0 / mu + 1e-12
+    b = np.random.default_rng(prob.m).standard_normal(prob.m)
+    f.set_correction(oracle.DENSE)
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    np.testing.assert_allclose(f.apply(A.T @ b), x_ls, rtol=1e-8, atol=1e-8 * np.abs(x_ls).max())
+    f.set_correction(oracle.NONE)
+    A1 = A[prow]
+    s = np.random.default_rng(prob.n).standard_normal(n)
+    ref = np.linalg.solve(A1.T @ A1, s)
+    np.testing.assert_allclose(f.apply(s), ref, rtol=1e-7, atol=1e-7 * np.abs(ref).max())
