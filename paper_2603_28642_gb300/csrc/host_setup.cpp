@@ -599,6 +599,10 @@ void columns_pipelined(const HostCSR& a, const HostCSR& ac, const IlupParams& pr
             K.act[s].x = r.x;
             r.x = static_cast<double>(s);
         }
+        // the U drop of these positions now (off the ordered chain): an entry
+        // outside their p best is beaten by p entries of the column anyway,
+        // so dropping again with the later positions keeps the same ones
+        dual_drop(K.cand, prm.p, prm.tau);
         // the rows the finish is likely to need (off the ordered chain)
         K.big.clear();
         const size_t want = static_cast<size_t>(prm.p) + 9;
