@@ -366,6 +366,8 @@ int32_t rlsq_setup_threads(int32_t requested, int64_t m, int64_t n);
 /* sizes[0..7] = nnz(L1 strict), nnz(L2), nnz(U strict), nmod,
    levels of L1, L1^T, U, U^T */
 int rlsq_setup_sizes(rlsq_setup s, int64_t *sizes);
+/* The same arrays, layouts and errors as rlsq_get_split, rlsq_get_factor
+   (sizes from rlsq_setup_sizes) and rlsq_get_levels of a factored handle. */
 int rlsq_setup_split(rlsq_setup s, int32_t *prow, int32_t *a2rows, double *d, double *udiag);
 int rlsq_setup_factor(rlsq_setup s, int32_t part, int64_t *ptr, int32_t *idx, double *val);
 int rlsq_setup_levels(rlsq_setup s, int32_t which, int32_t *level);
