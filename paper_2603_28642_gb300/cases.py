@@ -8,8 +8,13 @@ part worth capturing inside an NVTX range named `timed`:
     python -m paper_2603_28642_gb300.cases trsv --system L1 --schedule auto --merge 0 --autotune --scale 1
     python -m paper_2603_28642_gb300.cases iteration --scale 0.75
 
+    python -m paper_2603_28642_gb300.cases setup --scale 1 --threads 8
+
 `trsv` calls rlsq_trsv on one system a few times; `iteration` autotunes and
-profiles one preconditioned LSMR iteration.  Everything runs through the C ABI.
+profiles one preconditioned LSMR iteration; `setup` times the host-only set-up
+(ILUP, split, level sets; no GPU needed) with a given thread count and prints a
+checksum of the factor, which is the same for every thread count.  Everything
+runs through the C ABI.
 """
 from __future__ import annotations
 
@@ -52,9 +57,30 @@ def main(argv=None) -> int:
     it = sub.add_parser("iteration")
     it.add_argument("--scale", type=float, default=0.75)
     it.add_argument("--fp32", action="store_true")
+    su = sub.add_parser("setup")
+    su.add_argument("--scale", type=float, default=1.0)
+    su.add_argument("--threads", type=int, default=0, help="host threads (0: the library's default)")
     args = ap.parse_args(argv)
 
     prob = synth.config_problem(1, scale=args.scale)
+    if args.case == "setup":
+        import hashlib
+        import time
+
+        t0 = time.perf_counter()
+        H = B.HostSetup(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, p=FACTOR["p"], tau=FACTOR["tau"],
+                        mu=FACTOR["mu"], host_threads=args.threads)
+        dt = time.perf_counter() - t0
+        h = hashlib.sha1()
+        for a in H.split():
+            h.update(np.ascontiguousarray(a).tobytes())
+        for part in (B.PART_L1, B.PART_L2, B.PART_U):
+            for a in H.factor_csr(part):
+                h.update(np.ascontiguousarray(a).tobytes())
+        threads = B.load().rlsq_setup_threads(args.threads, prob.m, prob.n)
+        print(f"setup {prob.m} x {prob.n}: {dt:.2f} s on {threads} threads, sizes {H.sizes()}, "
+              f"factor sha1 {h.hexdigest()[:16]}")
+        return 0
     P = B.Problem.from_problem(prob)
     if args.case == "trsv":
         P.factor(**FACTOR, trsv_schedule=SCHEDULES[args.schedule], level_merge=args.merge,
