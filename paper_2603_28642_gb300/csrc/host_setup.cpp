@@ -1007,15 +1007,26 @@ struct Fuser {
     const HostCSR& strict;
     const double* diag;
     const Levels& lev;
-    std::vector<std::vector<std::pair<int32_t, double>>> Trow, Rrow;
+    // the rows built so far, appended to one arena each for T and R (a row
+    // built again is appended again; its newest copy counts)
+    struct Span {
+        int64_t at = 0;
+        int32_t len = 0;
+    };
+    std::vector<Span> Tspan, Rspan;
+    std::vector<int32_t> Tcol, Rcol;
+    std::vector<double> Tval, Rval;
     std::vector<double> accT, accR;
     std::vector<int64_t> markT, markR;  // stamp of the build that last touched a column
     std::vector<int32_t> listT, listR;
     int64_t stamp = 0;
     Fuser(const HostCSR& s, const double* d, const Levels& l)
-        : strict(s), diag(d), lev(l), Trow(static_cast<size_t>(s.rows)), Rrow(static_cast<size_t>(s.rows)),
+        : strict(s), diag(d), lev(l), Tspan(static_cast<size_t>(s.rows)), Rspan(static_cast<size_t>(s.rows)),
           accT(static_cast<size_t>(s.rows), 0.0), accR(static_cast<size_t>(s.rows), 0.0),
-          markT(static_cast<size_t>(s.rows), -1), markR(static_cast<size_t>(s.rows), -1) {}
+          markT(static_cast<size_t>(s.rows), -1), markR(static_cast<size_t>(s.rows), -1) {
+        Tcol.reserve(static_cast<size_t>(s.nnz()));
+        Tval.reserve(static_cast<size_t>(s.nnz()));
+    }
 
     // builds (or rebuilds) row i for group g of its level; returns its stored entries
     template <class GroupOf>
@@ -1040,38 +1051,42 @@ struct Fuser {
             }
             const double f = diag ? a / diag[j] : a;
             addR(j, -f);
-            for (const auto& rc : Rrow[j]) addR(rc.first, -f * rc.second);
-            for (const auto& tc : Trow[j]) addT(tc.first, -f * tc.second);
+            const Span rj = Rspan[j], tj = Tspan[j];
+            for (int32_t q = 0; q < rj.len; ++q) addR(Rcol[rj.at + q], -f * Rval[rj.at + q]);
+            for (int32_t q = 0; q < tj.len; ++q) addT(Tcol[tj.at + q], -f * Tval[tj.at + q]);
         }
         std::sort(listT.begin(), listT.end());
         std::sort(listR.begin(), listR.end());
-        Trow[i].clear();
-        Rrow[i].clear();
-        for (int32_t c : listT) Trow[i].push_back({c, accT[c]});
-        for (int32_t c : listR) Rrow[i].push_back({c, accR[c]});
+        Tspan[i] = Span{static_cast<int64_t>(Tcol.size()), static_cast<int32_t>(listT.size())};
+        for (int32_t c : listT) {
+            Tcol.push_back(c);
+            Tval.push_back(accT[c]);
+        }
+        Rspan[i] = Span{static_cast<int64_t>(Rcol.size()), static_cast<int32_t>(listR.size())};
+        for (int32_t c : listR) {
+            Rcol.push_back(c);
+            Rval.push_back(accR[c]);
+        }
         return static_cast<int64_t>(listT.size() + listR.size());
     }
 
     void finish(MergedTri& M) {
         const int64_t n = strict.rows;
-        auto to_csr = [&](const std::vector<std::vector<std::pair<int32_t, double>>>& rows, HostCSR& out) {
+        auto to_csr = [&](const std::vector<Span>& span, const std::vector<int32_t>& col,
+                          const std::vector<double>& val, HostCSR& out) {
             out.rows = n;
             out.cols = n;
             out.ptr.assign(static_cast<size_t>(n) + 1, 0);
-            for (int64_t i = 0; i < n; ++i) out.ptr[i + 1] = out.ptr[i] + static_cast<int64_t>(rows[i].size());
+            for (int64_t i = 0; i < n; ++i) out.ptr[i + 1] = out.ptr[i] + span[i].len;
             out.idx.resize(static_cast<size_t>(out.ptr[n]));
             out.val.resize(static_cast<size_t>(out.ptr[n]));
             for (int64_t i = 0; i < n; ++i) {
-                int64_t w = out.ptr[i];
-                for (const auto& p : rows[i]) {
-                    out.idx[w] = p.first;
-                    out.val[w] = p.second;
-                    ++w;
-                }
+                std::copy(col.begin() + span[i].at, col.begin() + span[i].at + span[i].len, out.idx.begin() + out.ptr[i]);
+                std::copy(val.begin() + span[i].at, val.begin() + span[i].at + span[i].len, out.val.begin() + out.ptr[i]);
             }
         };
-        to_csr(Trow, M.T);
-        to_csr(Rrow, M.R);
+        to_csr(Tspan, Tcol, Tval, M.T);
+        to_csr(Rspan, Rcol, Rval, M.R);
         // lower systems depend on smaller ids, upper ones on larger ids; the
         // merged dependencies keep that direction
         bool lower = true;
