@@ -87,6 +87,24 @@ def max_over_ranks(value: float, dist) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: float, dist) -> float:
+    """The sum of `value` over all ranks (every rank gets it)."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(items, rank: int, world: int):
+    """The independent problems one rank solves: every world-th, from its rank
+    on (sizes are drawn per problem, so the shares stay balanced)."""
+    return list(items[rank::world])
+
+
 def whole_job_rate(steps_per_rank: int, world: int, max_ms: float) -> float:
     """Iterations per second of the whole job: every rank runs its own replica
     for `steps_per_rank` iterations, timed by the slowest rank."""
@@ -427,24 +445,32 @@ def measure_sparse_dense(scale=1.0):
     }
 
 
-def measure_batched(count=512, first=None, sample=16):
+def measure_batched(count=512, first=None, sample=16, rank=0, world=1, dist=None):
     """Batched form: the first `first` problems of the 512-problem recipe solved
     together (float32 apply, float64 recurrences), against the same problems
-    solved one at a time in float64 (timed on `sample` of them)."""
+    solved one at a time in float64 (timed on `sample` of them).  With several
+    ranks every rank solves its shard of the problems (no collective on the
+    data path); the job's time is the slowest rank's and its iterations are all
+    ranks' iterations."""
     from paper_2603_28642_gb300 import binding as B
     from paper_2603_28642_gb300 import synth
 
-    probs = synth.batch_problems(count, first=first)
+    every = synth.batch_problems(count, first=first)
+    probs = shard(every, rank, world)
     hs = factor_all(probs, mu=1.0, p=10, tau=1e-2, correction=B.CORR_AUTO, cg_steps=2,
                     precision=B.PREC_FP32)
     B.batch_solve(hs[:2], [p.b for p in probs[:2]])  # warm-up (graph capture, lazy loading)
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     xs, infos, code = B.batch_solve(hs, [p.b for p in probs])
-    wall = time.perf_counter() - t0
-    its = sum(i["iterations"] for i in infos)
-    # one at a time, float64 apply, the same problems (a sample)
-    step = max(1, len(probs) // sample)
-    idx = list(range(0, len(probs), step))[:sample]
+    wall = max_over_ranks(time.perf_counter() - t0, dist)
+    its = sum_over_ranks(sum(i["iterations"] for i in infos), dist)
+    code = -int(max_over_ranks(abs(code), dist))  # the worst status (0 or a negative error)
+    worst = max_over_ranks(max(i["ratio"] for i in infos), dist)
+    # one at a time, float64 apply, the same problems (a sample of each shard)
+    step = max(1, len(probs) // max(1, sample // world))
+    idx = list(range(0, len(probs), step))[:max(1, sample // world)]
     t_one, its_one = 0.0, 0
     for k in idx:
         hs[k].factor(mu=1.0, p=10, tau=1e-2, correction=B.CORR_AUTO, cg_steps=2, precision=B.PREC_FP64)
@@ -453,15 +479,19 @@ def measure_batched(count=512, first=None, sample=16):
         r = hs[k].solve(probs[k].b)
         t_one += time.perf_counter() - t1
         its_one += r.info["iterations"]
-    one_total = t_one / len(idx) * len(probs)
+    t_one = sum_over_ranks(t_one, dist)
+    its_one = sum_over_ranks(its_one, dist)
+    n_one = sum_over_ranks(len(idx), dist)
+    one_total = t_one / n_one * len(every)  # all problems one at a time on one GPU
     return {
-        "problems": len(probs), "sum_n": int(sum(p.n for p in probs)), "sum_nnz": int(sum(p.nnz for p in probs)),
-        "status": code, "iterations_total": its, "batched_wall_s": wall,
+        "problems": len(every), "ranks": world, "sum_n": int(sum(p.n for p in every)),
+        "sum_nnz": int(sum(p.nnz for p in every)),
+        "status": code, "iterations_total": int(its), "batched_wall_s": wall,
         "aggregate_iter_per_s": its / wall,
-        "one_at_a_time_fp64_s_estimated": one_total, "one_at_a_time_sample": len(idx),
+        "one_at_a_time_fp64_s_estimated": one_total, "one_at_a_time_sample": int(n_one),
         "one_at_a_time_iter_per_s": its_one / t_one if t_one else None,
         "speedup_time_to_tol": one_total / wall if wall else None,
-        "max_ratio": max(i["ratio"] for i in infos),
+        "max_ratio": worst,
     }
 
 
@@ -508,19 +538,37 @@ def measure_served(nmat=64, n_hi=200000, rates=(100, 1000, 5000), requests=500):
 
 
 def run_workload(args):
-    """One JSON line for a non-default workload at its full recipe size."""
+    """One JSON line for a non-default workload at its full recipe size.  The
+    batched form shards its problems over the ranks of a torchrun job; the
+    others run on rank 0 alone."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if args.workload == "batched" and world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    elif rank != 0:
+        return
+    n_gpus = world if dist is not None else 1
     if args.workload == "sparse-dense":
         r = measure_sparse_dense(args.scale)
         metric, value, unit = "preconditioned LSMR iterations/s (sparse-dense)", r["iter_per_s"], "iter/s"
     elif args.workload == "batched":
-        r = measure_batched(args.count or 512)
+        r = measure_batched(args.count or 512, rank=rank if dist is not None else 0, world=n_gpus, dist=dist)
         metric, value, unit = "batched aggregate LSMR iterations/s", r["aggregate_iter_per_s"], "iter/s"
     else:
         r = measure_served(args.count or 64, requests=args.requests or 2000, rates=(100, 300, 1000, 3000, 5000))
         metric, value, unit = "served solves/s at the highest rate", r["rates"][-1]["solves_per_s"], "solves/s"
-    print(json.dumps({"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "higher_is_better": True,
-                      "dtype": "f32 apply / f64 recurrences", "data": "synthetic",
-                      "config": {"workload": args.workload}, "result": r}))
+    if rank == 0:
+        print(json.dumps({"metric": metric, "value": value, "unit": unit, "n_gpus": n_gpus, "higher_is_better": True,
+                          "scaling": "strong" if args.workload == "batched" else "weak",
+                          "dtype": "f32 apply / f64 recurrences", "data": "synthetic",
+                          "config": {"workload": args.workload}, "result": r}))
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
