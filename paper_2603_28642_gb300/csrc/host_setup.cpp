@@ -127,6 +127,12 @@ void transpose_into(int64_t rows, int64_t cols, const int64_t* ptr, const int32_
 
 }  // namespace
 
+HostCSR transpose(const HostCSR& a, int threads) {
+    HostCSR t;
+    transpose_into(a.rows, a.cols, a.ptr.data(), a.idx.data(), a.val.data(), nullptr, threads, t);
+    return t;
+}
+
 bool column_scaling(const HostCSR& a, std::vector<double>& d) {
     std::vector<double> ss(static_cast<size_t>(a.cols), 0.0);
     for (int64_t r = 0; r < a.rows; ++r)

@@ -26,6 +26,8 @@ struct HostCSR {
 // Transpose (rows x cols -> cols x rows); entries of each output row keep
 // ascending column order.
 HostCSR transpose(const HostCSR& a);
+// The same on up to `threads` threads (the same arrays for any count).
+HostCSR transpose(const HostCSR& a, int threads);
 
 struct IlupParams {
     int p = 10;          // max off-diagonal entries kept per column of L and U (< 0: all)

@@ -787,7 +787,7 @@ static void layout_A(rlsq_problem_s* P, int64_t threshold) {
         P->row_perm_d.release();
         P->Ad.release();
         P->dA.upload(A, st);
-        P->dAt.upload(transpose(A), st);
+        P->dAt.upload(transpose(A, ilup_threads(0, A.rows, A.cols)), st);
         return;
     }
     std::vector<char> is_dense(static_cast<size_t>(m), 0);
@@ -810,7 +810,7 @@ static void layout_A(rlsq_problem_s* P, int64_t threshold) {
     }
     for (int64_t i = P->ms; i < m; ++i) S.ptr[i + 1] = S.ptr[i];
     P->dA.upload(S, st);
-    P->dAt.upload(transpose(S), st);
+    P->dAt.upload(transpose(S, ilup_threads(0, S.rows, S.cols)), st);
     std::vector<double> ad(static_cast<size_t>(P->md * n), 0.0);
     for (int64_t q = 0; q < P->md; ++q) {
         const int32_t r = dense[q];
