@@ -93,6 +93,25 @@ int main(int argc, char **argv) {
     print_csr(s, RLSQ_PART_L2, "L2", m - n, sizes[1]);
     print_csr(s, RLSQ_PART_U, "U", n, sizes[2]);
 
+    /* error statuses of the update and S^{-1} calls (nothing changes on error) */
+    int64_t one_ptr[2] = {0, 1};
+    int32_t bad_col[1] = {(int32_t)n};
+    double one_val[1] = {1.0};
+    printf("errors %d %d %d %d\n",
+           rlsq_setup_schur_inverse(s, 0, NULL),                 /* ARG: no output */
+           rlsq_setup_remove_rows(s, m - n, a2),                 /* SHAPE: no row of A2 would remain */
+           rlsq_setup_remove_rows(s, 1, prow),                   /* ARG: a pivot row */
+           rlsq_setup_add_rows(s, 1, one_ptr, bad_col, one_val)); /* CSR: column out of range */
+    double *sinv = malloc(sizeof(double) * (size_t)((m - n) * (m - n)));
+    if (rlsq_setup_schur_inverse(s, 0, sinv) != RLSQ_OK) {
+        fprintf(stderr, "rlsq_setup_schur_inverse: %s\n", rlsq_last_error());
+        return 3;
+    }
+    printf("sinv");
+    for (int64_t k = 0; k < (m - n) * (m - n); ++k) printf(" %a", sinv[k]);
+    printf("\n");
+    free(sinv);
+
     rlsq_setup_destroy(s);
     free(prow);
     free(a2);

@@ -73,3 +73,7 @@ def test_c_client_matches_binding_and_oracle(client, tmp_path, which, threads):
     assert np.array_equal(ints(got["prow"]), oprow) and np.array_equal(ints(got["a2"]), oa2)
     L2 = f.L2()
     assert np.array_equal(floats(got["L2.val"]), L2.val)
+    # statuses reach C (ARG, SHAPE, ARG, CSR) and nothing changed on error
+    assert got["errors"] == ["-1", "-2", "-1", "-3"]
+    X = floats(got["sinv"]).reshape(prob.m - prob.n, prob.m - prob.n)
+    assert np.array_equal(X.view(np.uint64), s.schur_inverse().view(np.uint64))
