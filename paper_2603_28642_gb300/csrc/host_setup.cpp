@@ -933,8 +933,10 @@ int64_t slot_bytes(int64_t m) {
     return 16 * std::max<int64_t>(m, 1);
 }
 
-// Columns in flight per thread: up to 8 while all slots fit in 2 GiB.
+// Columns in flight per thread: up to 8 while all slots fit in 2 GiB; one
+// for a single thread, which never waits for another.
 int ilup_depth(int threads, int64_t m) {
+    if (threads <= 1) return 1;
     const int64_t fit = (int64_t(1) << 31) / (slot_bytes(m) * std::max(threads, 1));
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(8, fit)));
 }
@@ -982,10 +984,11 @@ IlupResult ilup_factor(const HostCSR& a, const IlupParams& prm) {
     R.Udiag.assign(static_cast<size_t>(n), 0.0);
 
     ColumnFactor C;
-    // The pipeline stores L in place, so it needs a bound on the entries of an
-    // L column (p >= 0) that keeps n p entries to a sensible size (2^27).  If
-    // the system refuses a thread, the serial loop does the work instead.
-    bool serial = !(prm.p >= 0 && prm.threads > 1 &&
+    // The pipelined loop (also on one thread, where it is the faster of the
+    // two) stores L in place, so it needs a bound on the entries of an L column
+    // (p >= 0) that keeps n p entries to a sensible size (2^27).  If the system
+    // refuses a thread, the serial loop does the work instead.
+    bool serial = !(prm.p >= 0 && prm.threads >= 1 &&
                     static_cast<double>(n) * static_cast<double>(prm.p) <= static_cast<double>(int64_t(1) << 27));
     if (!serial) {
         try {

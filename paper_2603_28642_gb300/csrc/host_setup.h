@@ -35,7 +35,7 @@ struct IlupParams {
     double mu = 0.1;     // threshold pivoting parameter (Algorithm 5)
     double small = 1e-10;// smallest admissible |U_jj| (Algorithm 6)
     bool scale = true;   // prescale columns to unit 2-norm
-    int threads = 1;     // threads of the column loop; > 1 pipelines it (same factor bit for bit)
+    int threads = 1;     // threads of the (pipelined) column loop; the factor is the same for any count
 };
 
 // Level structure of one triangular system: level of every row, rows sorted
