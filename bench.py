@@ -416,7 +416,7 @@ def factor_all(problems, threads=None, **kw):
         P.factor(**{"host_threads": 1, **kw})
         return P
 
-    with ThreadPoolExecutor(threads or os.cpu_count() or 4) as ex:
+    with ThreadPoolExecutor(threads or host_threads()) as ex:
         return list(ex.map(one, problems))
 
 
