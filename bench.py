@@ -65,12 +65,20 @@ def parse():
     return ap.parse_args()
 
 
-# DRAM bytes (read + write) of one iteration's launches of a kernel class, from
-# the ncu capture summarised in profiles/trsv_L1_syncfree_cfg1_traffic.md (same
-# kernels and workload): keyed by (class, schedule the class ran with).  The
-# bench reports it only when its dominant class ran that way.
-MEASURED_TRAFFIC = {("trsv_L1", 2): 4 * 80.09e6}  # 4 L1 solves per iteration, sync-free schedule
+# DRAM bytes (read + write) of ONE launch of a kernel class's solve kernel,
+# from an ncu capture summarised under profiles/ (same kernel, same recipe),
+# keyed by (class, schedule the class ran with).  The bench reports it only
+# when its dominant class ran that way.
+MEASURED_TRAFFIC = {}
 CLASS_SYSTEM = {"trsv_L1": 0, "trsv_L1t": 1, "trsv_U": 2, "trsv_Ut": 3}
+# solves per iteration of each triangular-solve class with CG(k): L1 and L1^T
+# once each around the correction and once per CG step; U and U^T once
+CLASS_SOLVES = {"trsv_L1": FACTOR["cg_steps"] + 2, "trsv_L1t": FACTOR["cg_steps"] + 2, "trsv_U": 1, "trsv_Ut": 1}
+
+
+def finfo_ms_per_iter(P, prob):
+    """A short untimed estimate of one iteration's time (for the clock soak)."""
+    return P.profile(prob.b, warmup=1, iters=3)["ms_per_iter"] / 1000.0
 
 
 # ---------------------------------------------------------------------------
@@ -183,9 +191,11 @@ class OracleSample:
         self.scale = cpu_scale
         self.prob = synth.config_problem(1, scale=cpu_scale)
         p = self.prob
+        t0 = time.perf_counter()
         self.f = oracle.Factor(p.m, p.n, p.rowptr, p.colidx, p.vals, p=FACTOR["p"], tau=FACTOR["tau"],
                                mu=FACTOR["mu"], small=FACTOR["small"])
         self.f.set_correction(oracle.CG, FACTOR["cg_steps"])
+        self.factor_seconds = time.perf_counter() - t0
         self.anorm = oracle.norm2(p.m, p.n, p.rowptr, p.colidx, p.vals)
         self.factor = p.nnz / full_nnz
 
@@ -212,12 +222,52 @@ class OracleSample:
                 "sample": self.describe(its, dt, runs)}
 
 
+def oracle_time_to_tol(prob, correction, cg_steps=2):
+    """The oracle's factor time and LSMR time to ratio < 1e-8 on one problem
+    (ILUP(p=10, tau=1e-2, mu=1), single thread)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    f = oracle.Factor(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, p=FACTOR["p"], tau=FACTOR["tau"],
+                      mu=FACTOR["mu"], small=FACTOR["small"])
+    f.set_correction(correction, cg_steps)
+    t_factor = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    r = oracle.lsmr(f, prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, prob.b)
+    t_solve = time.perf_counter() - t1
+    return {"m": prob.m, "n": prob.n, "nnz": prob.nnz, "factor_seconds": t_factor, "iterations": r.its,
+            "seconds_to_tol": t_solve, "seconds_per_iteration": t_solve / max(r.its, 1), "ratio": r.ratio}
+
+
 def cpu_oracle_sample(cpu_scale: float, full_nnz: int, iters_target_s: float = 12.0):
-    """One bounded run of the oracle on the scaled recipe (about iters_target_s)."""
+    """One bounded run of the oracle on the scaled recipe (about iters_target_s),
+    then its factor time and time to tolerance on config 0 (dense S, as the
+    recipe gives), on that sample (CG(2)) and on a mid-size problem of the
+    batched recipe (CG(2))."""
+    import oracle
+    from paper_2603_28642_gb300 import synth
+
     o = OracleSample(cpu_scale, full_nnz)
     its = max(3, int(iters_target_s / max(o.seconds_per_iteration(), 1e-6)))
     done, dt = o.run(its)
-    return o.baseline(done, dt)
+    out = o.baseline(done, dt)
+    t0 = time.perf_counter()
+    r = o.oracle.lsmr(o.f, o.prob.m, o.prob.n, o.prob.rowptr, o.prob.colidx, o.prob.vals, o.prob.b,
+                      anorm=o.anorm)
+    sample_tol = {"m": o.prob.m, "n": o.prob.n, "nnz": o.prob.nnz, "factor_seconds": o.factor_seconds,
+                  "iterations": r.its, "seconds_to_tol": time.perf_counter() - t0, "ratio": r.ratio}
+    sample_tol["seconds_per_iteration"] = sample_tol["seconds_to_tol"] / max(r.its, 1)
+    import numpy as np
+
+    bn, bm, bd = synth.batch_problem_sizes(512)
+    mid = int(np.argsort(bn)[len(bn) // 2])  # the median-size problem of the batched recipe
+    mid_prob = synth.sparse_problem(int(bm[mid]), int(bn[mid]), int(bd[mid]), seed=3000 + mid)
+    out["time_to_tol"] = {
+        "config0_dense": oracle_time_to_tol(synth.config_problem(0), oracle.DENSE),
+        f"config1_scale{cpu_scale}_cg2": sample_tol,
+        f"batched_problem{mid}_cg2": oracle_time_to_tol(mid_prob, oracle.CG),
+    }
+    return out
 
 
 def full_nnz_estimate(scale):
@@ -292,10 +342,16 @@ def run_ours(args):
 
     barrier()
     clk = Clocks(local)
+    # about one second of the same iteration first, so that the clock sampler
+    # (10 samples a second) sees this load; then W warm-up and K timed steps
+    soak_t0 = time.perf_counter()
+    P.profile(prob.b, warmup=0, iters=max(1, int(1.0 / max(finfo_ms_per_iter(P, prob), 1e-4))))
+    soak_s = time.perf_counter() - soak_t0
     torch.cuda.nvtx.range_push("timed")
     prof = P.profile(prob.b, warmup=max(3, args.warmup), iters=args.steps)
     torch.cuda.nvtx.range_pop()
     clocks = clk.stop()
+    clocks["window"] = f"{soak_s:.2f} s of the same iteration before the timed steps, and the timed steps"
     barrier()
     total_ms = max_over_ranks(prof["total_ms"], dist)
     ms_per_step = total_ms / args.steps
@@ -319,19 +375,29 @@ def run_ours(args):
     x64 = tol64.x
     err32 = float(np.linalg.norm(tol32.x - x64) / np.linalg.norm(x64))
 
-    # roofline of the dominant kernel class
+    # roofline of the dominant kernel class: the method's algorithmic bytes
+    # (each stored entry of the factor system once, row pointers, vector in
+    # and out) over the class's device time; the entries that level fusion
+    # adds are reported beside it as overhead, not counted as achieved bytes
     hbm, src = peaks()
     cls = prof["classes"]
     dom = max(cls, key=lambda k: cls[k]["ms"])
     d = cls[dom]
     achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
     sched = finfo["trsv_schedule"][CLASS_SYSTEM[dom]] if dom in CLASS_SYSTEM else None
+    per_launch = d["bytes"] / max(1, CLASS_SOLVES.get(dom, d["launches"]))
     traffic = MEASURED_TRAFFIC.get((dom, sched))
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": traffic, "traffic_unit": "bytes per iteration of the class",
-            "peak_source": src,
+            "frac": achieved / hbm, "peak_source": src,
+            "algorithmic_bytes_per_launch": per_launch,
+            "traffic": traffic, "traffic_over_algorithmic": traffic / per_launch if traffic else None,
             "iteration_achieved": prof["bytes_per_iter"] / (ms_per_step / 1000.0) / 1e9,
-            "iteration_frac": prof["bytes_per_iter"] / (ms_per_step / 1000.0) / 1e9 / hbm}
+            "iteration_frac": prof["bytes_per_iter"] / (ms_per_step / 1000.0) / 1e9 / hbm,
+            "bytes_per_iteration": prof["bytes_per_iter"]}
+    if dom in CLASS_SYSTEM:
+        w = CLASS_SYSTEM[dom]
+        own = finfo["nnz_L1"] if w < 2 else finfo["nnz_U"]
+        roof["schedule_entries_over_factor_entries"] = finfo["solve_entries"][w] / max(1, own)
     launches = sum(c["launches"] for c in cls.values())
 
     out = {
@@ -495,56 +561,72 @@ def measure_batched(count=512, first=None, sample=16, rank=0, world=1, dist=None
     }
 
 
-def measure_served(nmat=64, n_hi=200000, rates=(100, 1000, 5000), requests=500):
+def measure_served(nmat=64, n_hi=200000, rates=(100, 1000, 5000), requests=500, rank=0, world=1, dist=None):
     """Served form: Poisson arrivals of new right-hand sides for resident
-    matrices (m = 1.5 n), float32 apply, float64 recurrences, 150 GB budget."""
+    matrices (m = 1.5 n), float32 apply, float64 recurrences, 150 GB budget.
+    With several ranks, each rank owns whole matrices (balanced by nonzeros)
+    and serves the requests for them on its own GPU; the request stream is
+    the same on every rank, and the job's p50 / p99 are over all requests."""
     import numpy as np
 
     from paper_2603_28642_gb300 import binding as B
-    from paper_2603_28642_gb300 import synth
+    from paper_2603_28642_gb300 import serving, synth
 
     mats = synth.serving_matrices(nmat, n_hi=n_hi)
-    hs = factor_all(mats, mu=1.0, p=10, tau=1e-2, correction=B.CORR_AUTO, cg_steps=2,
-                    precision=B.PREC_FP32)
-    out = {"matrices": nmat, "n_max": int(max(p.n for p in mats)), "sum_n": int(sum(p.n for p in mats)),
-           "budget_bytes": 150 * 2**30, "rates": []}
+    owner = serving.owners([p.nnz for p in mats], world)
+    mine = [k for k in range(nmat) if owner[k] == rank]
+    hs = dict(zip(mine, factor_all([mats[k] for k in mine], mu=1.0, p=10, tau=1e-2, correction=B.CORR_AUTO,
+                                    cg_steps=2, precision=B.PREC_FP32)))
+    out = {"matrices": nmat, "ranks": world, "n_max": int(max(p.n for p in mats)),
+           "sum_n": int(sum(p.n for p in mats)), "budget_bytes": 150 * 2**30, "rates": []}
     for rate in rates:
         srv = B.Server(hbm_budget_bytes=150 * 2**30, max_slots=64)
-        ids = [srv.register(P) for P in hs]
+        ids = {k: srv.register(P) for k, P in hs.items()}
         rng = np.random.default_rng(rate)
         which = rng.integers(0, nmat, size=requests)
-        rhs = [synth.serving_rhs(mats[w], r) for r, w in enumerate(which)]
         arrive = synth.poisson_arrivals(rate, requests, seed=rate)
+        todo = serving.requests_for(which, owner, rank)
+        rhs = {int(r): synth.serving_rhs(mats[int(which[r])], int(r)) for r in todo}
+        lat_ms = []
         pending = {}
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
         sent = 0
-        while sent < requests or pending:
+        while sent < len(todo) or pending:
             now = time.perf_counter() - t0
-            while sent < requests and arrive[sent] <= now:
-                pending[srv.submit(ids[int(which[sent])], rhs[sent])] = int(which[sent])
+            while sent < len(todo) and arrive[todo[sent]] <= now:
+                r = int(todo[sent])
+                pending[srv.submit(ids[int(which[r])], rhs[r])] = int(which[r])
                 sent += 1
             for t, w in list(pending.items()):
-                if srv.poll(t, mats[w].n) is not None:
+                got = srv.poll(t, mats[w].n)
+                if got is not None:
+                    lat_ms.append(1000.0 * got[1]["solve_seconds"])  # submit -> result, as the server counts it
                     del pending[t]
             time.sleep(0.0005)
+        wall = time.perf_counter() - t0
         st = srv.stats()
-        out["rates"].append({"rate_per_s": rate, "requests": requests, "p50_ms": st["p50_ms"],
-                             "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
-                             "solves_per_s": st["solves_per_s"], "ticks": st["ticks"],
-                             "tick_ms": st["tick_ms"], "tick_device_ms": st["tick_device_ms"],
-                             "peak_state_bytes": st["peak_bytes"]})
         srv.close()
+        merged = serving.merge_latencies(serving.gather(lat_ms, dist))
+        wall = max(serving.gather(wall, dist))
+        out["rates"].append({"rate_per_s": rate, "requests": requests, "p50_ms": merged["p50_ms"],
+                             "p99_ms": merged["p99_ms"], "mean_ms": merged["mean_ms"],
+                             "solves_per_s": merged["requests"] / wall if wall else None,
+                             "ticks": st["ticks"], "tick_ms": st["tick_ms"], "tick_device_ms": st["tick_device_ms"],
+                             "peak_state_bytes": st["peak_bytes"]})
     return out
 
 
 def run_workload(args):
-    """One JSON line for a non-default workload at its full recipe size.  The
-    batched form shards its problems over the ranks of a torchrun job; the
-    others run on rank 0 alone."""
+    """One JSON line for a non-default workload at its full recipe size.  Under
+    torchrun the batched form shards its problems over the ranks and the
+    served form routes each request to the rank owning its matrix (no
+    collective on the data path); the sparse-dense form runs on rank 0 alone."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     dist = None
-    if args.workload == "batched" and world > 1:
+    if args.workload in ("batched", "served") and world > 1:
         import torch
         import torch.distributed as dist
 
@@ -560,11 +642,12 @@ def run_workload(args):
         r = measure_batched(args.count or 512, rank=rank if dist is not None else 0, world=n_gpus, dist=dist)
         metric, value, unit = "batched aggregate LSMR iterations/s", r["aggregate_iter_per_s"], "iter/s"
     else:
-        r = measure_served(args.count or 64, requests=args.requests or 2000, rates=(100, 300, 1000, 3000, 5000))
+        r = measure_served(args.count or 64, requests=args.requests or 2000, rates=(100, 300, 1000, 3000, 5000),
+                           rank=rank if dist is not None else 0, world=n_gpus, dist=dist)
         metric, value, unit = "served solves/s at the highest rate", r["rates"][-1]["solves_per_s"], "solves/s"
     if rank == 0:
         print(json.dumps({"metric": metric, "value": value, "unit": unit, "n_gpus": n_gpus, "higher_is_better": True,
-                          "scaling": "strong" if args.workload == "batched" else "weak",
+                          "scaling": "strong" if args.workload in ("batched", "served") else "weak",
                           "dtype": "f32 apply / f64 recurrences", "data": "synthetic",
                           "config": {"workload": args.workload}, "result": r}))
     if dist is not None:

@@ -163,6 +163,9 @@ typedef struct {
     double ilup_seconds;   /* host ILUP (Algorithms 4-6), split, transposes and level sets of the
                               factorisation in use (part of factor_seconds) */
     int32_t ilup_threads;  /* threads of its column loop */
+    int64_t solve_entries[4]; /* stored entries the GPU reads per solve, per system, after level fusion
+                                 (substituted and right-hand-side terms; the diagonal of U, U^T
+                                 included); bytes_per_iter counts the factor's own entries */
 } rlsq_info;
 
 /* Server options and statistics (continuous batching of right-hand sides). */
@@ -338,9 +341,11 @@ int rlsq_profile(rlsq_problem h, const double *b, int32_t warmup, int32_t iters,
  * (8 MiB + 512 B) that every GPU which loads the library keeps until the
  * process exits.
  *  - n > RLSQ_NOALLOC_MAX_ROWS is rejected with RLSQ_ERR_SHAPE (nothing runs).
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - The first call on a device (and the first after a device reset) looks
+ *    up the array's device address (cudaGetSymbolAddress) with that device
+ *    current; make that first call before any stream capture.
+ *  - The call is synchronous: it waits on `stream` for the solve to finish
+ *    and reads the error word back before it returns.
  *  - Every call reuses the same array and clears what must start at zero;
  *    calls that overlap on the GPU (other streams, other threads, other
  *    problems) race on it and must be serialised by the caller.

@@ -67,6 +67,7 @@ class Info(C.Structure):
         ("levels_Ut", C.c_int32), ("correction", C.c_int32), ("precision", C.c_int32),
         ("bytes_per_iter", C.c_double), ("solve_levels", C.c_int32 * 4), ("level_merge", C.c_int32 * 4),
         ("trsv_schedule", C.c_int32 * 4), ("ilup_seconds", C.c_double), ("ilup_threads", C.c_int32),
+        ("solve_entries", C.c_int64 * 4),
     ]
 
     def as_dict(self):

@@ -10,6 +10,8 @@
 // every GPU that loads the library holds until the process exits.
 #include <mutex>
 
+#include <cuda.h>
+
 #include "common.h"
 
 // The scratch memory of rlsq_trsv_noalloc (8 MiB + 512 B per device).
@@ -31,27 +33,57 @@ static_assert(kHeaderWords == 128, "header size");
 
 std::mutex g_mutex;
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
+// The array's device address, per device ordinal, with the id of the CUDA
+// context it was looked up in: a device reset (cudaDeviceReset) ends that
+// context, the next one gets a new id, and the address is looked up again.
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    void* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// cuCtxGetId through the runtime's driver entry point (no link to libcuda).
+unsigned long long current_context_id() {
+    static CtxGetIdFn fn = []() -> CtxGetIdFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<CtxGetIdFn>(f);
+    }();
+    if (!fn) throw ApiError(RLSQ_ERR_CUDA, "cuCtxGetId is not available from the driver");
+    unsigned long long id = 0;
+    if (fn(nullptr, &id) != CUDA_SUCCESS) throw ApiError(RLSQ_ERR_CUDA, "cuCtxGetId failed");
+    return id;
+}
 
 // Device address of g_trsv_scratch on the current device, looked up once per
-// device.  (In host code the symbol's name is only a stand-in; its device
-// address comes from cudaGetSymbolAddress.)
+// device and context.  (In host code the symbol's name is only a stand-in;
+// its device address comes from cudaGetSymbolAddress.)
 int32_t* scratch_on_current_device() {
     int dev = 0;
     RLSQ_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) throw ApiError(RLSQ_ERR_ARG, "device ordinal out of range");
+    RLSQ_CUDA(cudaSetDevice(dev));  // makes the device's primary context current on this thread
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    ScratchAddr& a = g_scratch_addr[dev];
+    if (!a.addr || a.ctx_id != ctx) {
         void* p = nullptr;
         RLSQ_CUDA(cudaGetSymbolAddress(&p, g_trsv_scratch));
-        g_scratch_addr[dev] = p;
+        a.addr = p;
+        a.ctx_id = ctx;
     }
-    return static_cast<int32_t*>(g_scratch_addr[dev]);
+    return static_cast<int32_t*>(a.addr);
 }
 
 template <class F>
 void with_lanes(int G, F&& f) {
     switch (G) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
         case 2: f(std::integral_constant<int, 2>{}); break;
         case 4: f(std::integral_constant<int, 4>{}); break;
         case 8: f(std::integral_constant<int, 8>{}); break;

@@ -200,12 +200,22 @@ struct RecScope {
     }
 };
 
+// Algorithmic bytes of one solve with system `which` of the factor (not of
+// its fused form): every stored entry once (value + int32 index), the row
+// pointers, the right-hand side in and the solution out.  Entries that level
+// fusion adds are the schedule's overhead and are not counted here.
 template <typename T>
-static double trsv_bytes(const rlsq_problem_s* P, const DevFactor<T>& F, int which) {
+static double trsv_bytes(const rlsq_problem_s* P, int which) {
     const double n = static_cast<double>(P->n), v = sizeof(T);
-    return (v + 4.0) * static_cast<double>(F.tri[which].nnz + F.rtri[which].nnz) + 8.0 * n + 3.0 * v * n +
-           ((which >= 2) ? v * n : 0.0);
+    double nnz = 0.0;
+    if (P->F) {
+        const IlupResult& F = *P->F;
+        nnz = (which < 2) ? static_cast<double>(F.L1.nnz()) : static_cast<double>(F.U.nnz()) + n;  // U: + diagonal
+    }
+    return (v + 4.0) * nnz + 4.0 * n + 2.0 * v * n;
 }
+// A sparse product y = M x: every stored entry once, the row pointers, x read
+// and y written once each.
 template <typename T>
 static double mv_bytes(const DevCsr<T>& M, double in_bytes_per_col, double out_bytes_per_row) {
     return (sizeof(T) + 4.0) * static_cast<double>(M.nnz) + 4.0 * M.rows +
@@ -234,7 +244,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
     const Tri<T> tri = F.tview(which);
     const int n = tri.n;
     const int G = P->map.G_tri[which];
-    RecScope rs(P, RLSQ_KCLASS_TRSV_L1 + which, trsv_bytes(P, F, which), st);
+    RecScope rs(P, RLSQ_KCLASS_TRSV_L1 + which, trsv_bytes<T>(P, which), st);
     if (P->map.sched[which] == RLSQ_TRSV_LEVEL) {
         const auto& lp = F.level_ptr[which];
         for (size_t l = 0; l + 1 < lp.size(); ++l) {
@@ -367,7 +377,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
             for (int it = 0; it < P->opts.cg_steps; ++it) {
                 const bool first = (it == 0);
                 {
-                    RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, sizeof(T), first ? sizeof(T) : 2 * sizeof(T)), st);
+                    RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, sizeof(T), sizeof(T)), st);
                     with_G(P->map.G_L2t, [&](auto g) {
                         constexpr int GG = decltype(g)::value;
                         if (first) k_l2t_cg<T, GG, true><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S);
@@ -376,7 +386,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
                 }
                 launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{c1, nullptr, nullptr}, c2, slot++, S, st);
                 launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{c2, nullptr, nullptr}, c3, slot++, S, st);
-                RecScope rs2(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), first ? 3 * sizeof(T) : 4 * sizeof(T)), st);
+                RecScope rs2(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
                 with_G(P->map.G_L2, [&](auto g) {
                     constexpr int GG = decltype(g)::value;
                     if (first)
@@ -461,7 +471,7 @@ static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, 
         enqueue_dense_av<true>(P, P->tx.p, S, st);
     }
     {
-        RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 16.0, 32.0), st);
+        RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 8.0, 8.0), st);
         with_G(P->map.G_A, [&](auto g) {
             k_spmv_lsmr<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
                 P->dA.view(), P->tx.p, P->qr.p, P->b.p, S, P->part.p, P->counter.p, static_cast<int>(P->ms),
@@ -473,7 +483,7 @@ static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, 
         enqueue_dense_atv<true>(P, P->qr.p + P->ms, S, st);
     }
     {
-        RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 16.0, 16.0), st);
+        RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 8.0, 8.0), st);
         with_G(P->map.G_At, [&](auto g) {
             k_spmvt_lsmr<decltype(g)::value, false>
                 <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
@@ -596,33 +606,38 @@ static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain,
     return ex;
 }
 
+// Algorithmic HBM bytes of one LSMR iteration: every stored entry of A, A^T
+// and of each factor system once per use (value + int32 index), row
+// pointers, each product's and solve's input and output vector once, and
+// the LSMR vector passes (12 n-vectors and 6 m-vectors of float64).  Work
+// the schedule adds -- fused level groups' extra entries, the explicit
+// residual A x_k and A^T r_k the stopping test uses -- is not counted.
 static double algorithmic_bytes(const rlsq_problem_s* P, bool plain) {
     const double m = static_cast<double>(P->m), n = static_cast<double>(P->n);
     const double dnnz = static_cast<double>(P->md) * n;
-    double bytes = 2.0 * 12.0 * (static_cast<double>(P->nnz) - dnnz) + 4.0 * (m + n);  // sparse A, A^T
-    bytes += 2.0 * 8.0 * dnnz;  // dense-row block, once for A and once for A^T
-    bytes += 8.0 * (2 * n + 4 * m);   // SpMV: gathers of v^ and x, q in/out, b in, r out
-    bytes += 8.0 * (2 * m + 2 * n);   // SpMV^T: gathers of u and r, s in/out
-    bytes += 8.0 * 7 * n;             // LSMR update: t, h, h-bar, x in; h, h-bar, x out
-    if (plain || !P->F) return bytes + 8.0 * 3 * n;
+    double bytes = 2.0 * 12.0 * (static_cast<double>(P->nnz) - dnnz) + 2.0 * 8.0 * dnnz;  // A, A^T; dense block
+    bytes += 4.0 * (m + n) + 16.0 * (m + n);  // row pointers of A and A^T; v^ -> q and u -> s
+    bytes += 12.0 * 8.0 * n + 6.0 * 8.0 * m;  // LSMR vector passes
+    if (plain || !P->F) return bytes;
     const IlupResult& F = *P->F;
     const double wv = (P->precision == RLSQ_PREC_FP32) ? 4.0 : 8.0;
     const double wf = wv + 4.0;
     const double m2 = m - n;
-    auto tri = [&](const HostCSR& a) { return wf * a.nnz() + 8.0 * n + 3.0 * wv * n; };
-    auto l2 = [&](const HostCSR& a) { return wf * a.nnz() + 4.0 * a.rows + wv * (a.rows + a.cols); };
+    const double tri_l1 = wf * F.L1.nnz() + 4.0 * n + 2.0 * wv * n;
+    const double tri_u = wf * (F.U.nnz() + n) + 4.0 * n + 2.0 * wv * n;
+    const double l2 = wf * F.L2.nnz() + 4.0 * (m2 + n) / 2.0 + wv * m;  // mean of L2 (m2 rows) and L2^T (n rows)
     const int k = P->opts.cg_steps;
-    double ap = tri(F.Ut) + tri(F.L1t) + tri(F.L1) + tri(F.U) + 8.0 * n + wv * n + 2 * 8.0 * n;
-    if (P->correction != RLSQ_CORR_NONE) {
-        ap += tri(F.L1) + tri(F.L1t) + l2(F.L2) + l2(F.L2t);
-        if (P->correction == RLSQ_CORR_CG) {
-            ap += k * (tri(F.L1) + tri(F.L1t) + l2(F.L2) + l2(F.L2t));
-            ap += k * wv * (3 * m2 + 5 * m2);  // p, Sp, r, w traffic of the CG steps
-        } else if (P->correction == RLSQ_CORR_DENSE) {
-            ap += wv * m2 * m2;
-        }
+    int c_l1 = 2, c_l2 = 0;
+    double dense = 0.0;
+    if (P->correction == RLSQ_CORR_SI || P->correction == RLSQ_CORR_DENSE) {
+        c_l1 = 4;
+        c_l2 = 2;
+        if (P->correction == RLSQ_CORR_DENSE) dense = wv * m2 * m2;
+    } else if (P->correction == RLSQ_CORR_CG) {
+        c_l1 = 4 + 2 * k;
+        c_l2 = 2 + 2 * k;
     }
-    return bytes + ap;
+    return bytes + 2.0 * tri_u + c_l1 * tri_l1 + c_l2 * l2 + dense;
 }
 
 static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
@@ -651,6 +666,7 @@ static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
         info->solve_levels[w] = P->merged[w].lev.nlevels;
         info->level_merge[w] = P->merged[w].k;
         info->trsv_schedule[w] = P->map.sched[w];
+        info->solve_entries[w] = P->merged[w].T.nnz() + P->merged[w].R.nnz() + (w >= 2 ? P->n : 0);
     }
     info->bytes_per_iter = algorithmic_bytes(P, !P->factored);
 }

@@ -47,6 +47,11 @@ def test_gpu_arm_cpu_baseline_helper():
     import bench
 
     cb = bench.cpu_oracle_sample(0.02, bench.full_nnz_estimate(1.0), iters_target_s=1.0)
-    assert set(cb) == {"value", "unit", "cores", "kind", "sample"}
+    assert set(cb) == {"value", "unit", "cores", "kind", "sample", "time_to_tol"}
     assert cb["value"] > 0 and cb["unit"] == "iter/s" and cb["cores"] == 1 and cb["kind"] == "oracle"
     assert "scale 0.02" in cb["sample"]
+    tt = cb["time_to_tol"]
+    assert set(tt) >= {"config0_dense", "config1_scale0.02_cg2"} and len(tt) == 3
+    for v in tt.values():
+        assert v["factor_seconds"] > 0 and v["seconds_to_tol"] > 0 and v["ratio"] < 1e-8
+        assert 0 < v["iterations"] < 2000

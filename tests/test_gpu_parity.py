@@ -4,12 +4,15 @@ CPU oracle on the same seeded inputs.
 Tolerances (float64):
   * SpMV / SpMV^T: |y - y_ref| <= 1e-13 (|A| |x|)_i  (reordered sums of <= ~20 terms)
   * each triangular solve and one full preconditioner application: relative
-    2-norm error <= 1e-12
+    error <= 1e-12 in the 2-norm and, element by element, in the max-norm
+    (max_i |x_i - ref_i| <= 1e-12 max_i |ref_i|)
   * solves: x within 1e-6 relative of the oracle's x, iteration count equal
     (+-1 when the final ratio sits within 1e-3 of the threshold)
 float32 apply: the error against the float64 oracle is measured and bounded
-by 1e-3 relative (float32 unit roundoff 6e-8 times the conditioning of the
-triangular factors); the test prints it.
+by 5e-6 relative in the 2-norm and the max-norm, about 10x the largest error
+measured on GB300 (3.2e-7 .. 4.3e-7 for the four modes on config 0: float32
+unit roundoff 6e-8 times the growth through the triangular factors); the
+test prints it.
 """
 import numpy as np
 import pytest
@@ -26,6 +29,16 @@ MU = 1.0  # workload pivoting threshold (see the design notes on mu = 0.1)
 def rel(a, b):
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def rel_inf(a, b):
+    nb = np.max(np.abs(b)) if b.size else 0.0
+    return np.max(np.abs(a - b)) / (nb if nb > 0 else 1.0) if b.size else 0.0
+
+
+def close(a, b, tol):
+    """Both the normwise and the elementwise (max-norm) relative error within tol."""
+    return a.shape == b.shape and rel(a, b) <= tol and rel_inf(a, b) <= tol
 
 
 def make(prob, mode=B.CORR_CG, prec=B.PREC_FP64, sched=B.TRSV_AUTO, mu=MU, **kw):
@@ -123,7 +136,7 @@ def test_triangular_solves(sched, which, request):
     for sys_id, name in SOLVES:
         x = P.trsv(sys_id, b)
         ref = getattr(f, name)(b)
-        assert rel(x, ref) <= 1e-12, (sys_id, rel(x, ref))
+        assert close(x, ref, 1e-12), (sys_id, rel(x, ref), rel_inf(x, ref))
 
 
 @pytest.fixture(scope="module")
@@ -148,8 +161,9 @@ def test_triangular_solves_many_rounds(wide, sched, k):
     b = np.random.default_rng(11).standard_normal(prob.n)
     for sys_id, name in SOLVES:
         x = P.trsv(sys_id, b)
-        assert rel(x, getattr(f, name)(b)) <= 1e-12, (sys_id, rel(x, getattr(f, name)(b)))
-    assert rel(P.apply(b), f.apply(b)) <= 1e-12
+        ref = getattr(f, name)(b)
+        assert close(x, ref, 1e-12), (sys_id, rel(x, ref), rel_inf(x, ref))
+    assert close(P.apply(b), f.apply(b), 1e-12)
 
 
 def test_triangular_solves_all_lane_counts(cfg0):
@@ -159,7 +173,7 @@ def test_triangular_solves_all_lane_counts(cfg0):
     f = oracle_factor(cfg0, oracle.NONE)
     b = np.random.default_rng(4).standard_normal(cfg0.n)
     for sys_id, name in SOLVES:
-        assert rel(P.trsv(sys_id, b), getattr(f, name)(b)) <= 1e-12
+        assert close(P.trsv(sys_id, b), getattr(f, name)(b), 1e-12)
 
 
 # ---------------------------------------------------------------------------
@@ -175,7 +189,7 @@ def test_apply_fp64(cfg0, modes, sched):
     for _ in range(2):
         s = rng.standard_normal(cfg0.n)
         t = P.apply(s)
-        assert rel(t, f.apply(s)) <= 1e-12
+        assert close(t, f.apply(s), 1e-12)
 
 
 @pytest.mark.parametrize("modes", [MODES[0], MODES[2]], ids=["NONE", "CG"])
@@ -184,7 +198,7 @@ def test_apply_fp64_mid(mid, modes):
     P = make(mid, bm)
     f = oracle_factor(mid, om)
     s = np.random.default_rng(6).standard_normal(mid.n)
-    assert rel(P.apply(s), f.apply(s)) <= 1e-12
+    assert close(P.apply(s), f.apply(s), 1e-12)
 
 
 @pytest.mark.parametrize("modes", MODES, ids=["NONE", "SI", "CG", "DENSE"])
@@ -193,9 +207,9 @@ def test_apply_fp32_error(cfg0, modes):
     P = make(cfg0, bm, prec=B.PREC_FP32)
     f = oracle_factor(cfg0, om)
     s = np.random.default_rng(7).standard_normal(cfg0.n)
-    err = rel(P.apply(s), f.apply(s))
-    print(f"fp32 apply relative error ({bm}): {err:.3e}")
-    assert err <= 1e-3
+    t, ref = P.apply(s), f.apply(s)
+    print(f"fp32 apply relative error ({bm}): {rel(t, ref):.3e}, elementwise {rel_inf(t, ref):.3e}")
+    assert close(t, ref, 5e-6)
 
 
 # ---------------------------------------------------------------------------
@@ -373,8 +387,8 @@ def test_fused_levels_solves(mid, k, sched):
     f = oracle_factor(mid, oracle.CG)
     b = np.random.default_rng(9).standard_normal(mid.n)
     for sys_id, name in SOLVES:
-        assert rel(P.trsv(sys_id, b), getattr(f, name)(b)) <= 1e-12
-    assert rel(P.apply(b), f.apply(b)) <= 1e-12
+        assert close(P.trsv(sys_id, b), getattr(f, name)(b), 1e-12)
+    assert close(P.apply(b), f.apply(b), 1e-12)
 
 
 def test_fused_levels_batch_and_noalloc(cfg0):
@@ -390,7 +404,7 @@ def test_fused_levels_batch_and_noalloc(cfg0):
     xd = torch.empty_like(bd)
     B.trsv_noalloc(P, B.SYS_U, bd, xd)
     torch.cuda.synchronize()
-    assert rel(xd.cpu().numpy(), f.solve_U(b)) <= 1e-12
+    assert close(xd.cpu().numpy(), f.solve_U(b), 1e-12)
 
 
 @pytest.mark.parametrize("steps", [1, 3, 4])
@@ -400,7 +414,7 @@ def test_apply_and_solve_other_cg_step_counts(cfg0, steps):
     P = make(cfg0, B.CORR_CG, cg_steps=steps)
     f = oracle_factor(cfg0, oracle.CG, steps=steps)
     b = np.random.default_rng(40 + steps).standard_normal(cfg0.n)
-    assert rel(P.apply(b), f.apply(b)) <= 1e-12
+    assert close(P.apply(b), f.apply(b), 1e-12)
     ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
     res = P.solve(cfg0.b)
     _check_solve(cfg0, res, ref)

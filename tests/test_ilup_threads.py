@@ -158,3 +158,27 @@ def test_threads_bitexact_stress(case):
     ref = setup_arrays(prob, 1, **kw)
     for t in (3, 8):
         assert_same(setup_arrays(prob, t, **kw), ref)
+
+
+@pytest.mark.slow
+def test_fullsize_config1_threaded_setup_matches_oracle():
+    """The headline 2M x 1M recipe at full size (p = 10, tau = 1e-2, mu = 1):
+    the threaded host set-up (the library's default thread count) against the
+    single-threaded oracle, bit for bit: row selection, A2 rows, scaling, the
+    L1, L2 and U arrays and U's diagonal, the level sets of L1 and U (both
+    from the oracle's level routine).  About two minutes, mostly the oracle."""
+    kw = dict(p=10, tau=1e-2, mu=1.0)
+    prob = synth.config_problem(1)
+    got = setup_arrays(prob, 0, **kw)
+    f = oracle.Factor(prob.m, prob.n, prob.rowptr, prob.colidx, prob.vals, **kw)
+    oprow, oa2 = f.perm()
+    assert np.array_equal(got["split"][0], oprow) and np.array_equal(got["split"][1], oa2)
+    assert np.array_equal(got["split"][2], f.scaling())
+    oU, oud = f.U()
+    assert np.array_equal(got["split"][3], oud)
+    oL1 = f.L1()
+    for name, ref in (("L1", oL1), ("L2", f.L2()), ("U", oU)):
+        ptr, idx, val = got[name]
+        assert np.array_equal(ptr, ref.ptr) and np.array_equal(idx, ref.idx) and np.array_equal(val, ref.val)
+    assert np.array_equal(got["lev_L1"], oracle.levels(oL1, True)[0])
+    assert np.array_equal(got["lev_U"], oracle.levels(oU, False)[0])

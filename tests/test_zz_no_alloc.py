@@ -26,13 +26,21 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+# (nonzeros per row of A, p): with p = 10 the factor rows average at most 12
+# entries and the solves take one lane per row; with 24 per row and p = 30
+# (13 entries per row of L1, 24 of U) they take groups of 4 and 8 lanes.
+ROWS = [(6, 10), (24, 30)]
+
+
 @pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL])
-def test_noalloc_matches_trsv_on_two_calls(sched):
+@pytest.mark.parametrize("rows", ROWS)
+def test_noalloc_matches_trsv_on_two_calls(sched, rows):
     import torch
 
-    prob = synth.sparse_problem(30_000, 20_000, 6, seed=7)
+    per_row, p = rows
+    prob = synth.sparse_problem(30_000, 20_000, per_row, seed=7)
     P = B.Problem.from_problem(prob)
-    P.factor(mu=1.0, correction=B.CORR_NONE, trsv_schedule=sched)
+    P.factor(mu=1.0, p=p, tau=1e-2, correction=B.CORR_NONE, trsv_schedule=sched)
     rng = np.random.default_rng(11)
     for which in SYSTEMS:
         for call in range(2):
