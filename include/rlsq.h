@@ -78,6 +78,9 @@ extern "C" {
 #define RLSQ_TRSV_COOP 3     /* one persistent launch, grid barrier between levels (bounded waits) */
 #define RLSQ_TRSV_WAVE 4     /* one co-resident launch, a fixed row sequence per thread, rows wait on
                                 their inputs and levels overlap (bounded waits) */
+#define RLSQ_TRSV_BINNED 5   /* one persistent launch, grid barrier between level groups; within a
+                                group rows are binned by length so that each lane gathers at most
+                                four entries of its row per round (bounded waits) */
 
 /* Krylov solvers of rlsq_solve */
 #define RLSQ_SOLVER_LSMR 0  /* LSMR in x-space (the default) */
@@ -128,6 +131,10 @@ typedef struct {
                               cost model (per level and per stored entry) among
                               k = 1..4 and groups grown level by level (a level
                               joins while the fill it adds costs less than a level) */
+    int32_t trsv_rows;     /* RLSQ_TRSV_SYNCFREE without autotuning: 0 = blocks take chunks of
+                              rows from the ticket counter; 1, 2 or 4 = warps take chunks and
+                              each group of lanes solves that many rows, loading all their
+                              structure before it waits on an unknown */
 } rlsq_factor_opts;
 
 /* Options of a solve. */

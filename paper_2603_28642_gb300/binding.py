@@ -26,7 +26,7 @@ ERR_BREAKDOWN, ERR_MAXIT, ERR_DEVICE_TIMEOUT = -7, -8, -9
 HOST_PTRS, DEVICE_PTRS = 0, 1
 CORR_NONE, CORR_SI, CORR_CG, CORR_DENSE, CORR_AUTO = 0, 1, 2, 3, 4
 PREC_FP64, PREC_FP32 = 0, 1
-TRSV_AUTO, TRSV_LEVEL, TRSV_SYNCFREE, TRSV_COOP, TRSV_WAVE = 0, 1, 2, 3, 4
+TRSV_AUTO, TRSV_LEVEL, TRSV_SYNCFREE, TRSV_COOP, TRSV_WAVE, TRSV_BINNED = 0, 1, 2, 3, 4, 5
 SOLVER_LSMR, SOLVER_CGLS = 0, 1
 SYS_L1, SYS_L1T, SYS_U, SYS_UT = 0, 1, 2, 3
 PART_L1, PART_L2, PART_U = 0, 1, 2
@@ -44,7 +44,7 @@ class FactorOpts(C.Structure):
         ("scale_columns", C.c_int32), ("correction", C.c_int32), ("cg_steps", C.c_int32),
         ("dense_cap", C.c_int64), ("precision", C.c_int32), ("trsv_schedule", C.c_int32),
         ("autotune", C.c_int32), ("dense_row_min", C.c_int64), ("host_threads", C.c_int32),
-        ("level_merge", C.c_int32),
+        ("level_merge", C.c_int32), ("trsv_rows", C.c_int32),
     ]
 
 

@@ -5,6 +5,8 @@
 // (median of a few runs after a warm-up) on the problem's own matrices; the
 // fastest wins.  Results are cached on the handle until the next factor.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -91,30 +93,43 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
         P->map.G_L2t = best_mv_lanes<T>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p);
     }
     static const int cands[] = {1, 2, 4, 8, 16, 32};
+    const bool log = std::getenv("RLSQ_TUNE_LOG") != nullptr;
     for (int w = 0; w < 4; ++w) {
         int bestG = P->map.G_tri[w], bestS = P->map.sched[w];
         float tbest = 1e30f;
-        int bestB = P->map.sf_blocks[w], bestK = P->map.wave_kp[w];
-        for (int sched : {RLSQ_TRSV_WAVE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_LEVEL, RLSQ_TRSV_COOP}) {
+        int bestB = P->map.sf_blocks[w], bestK = P->map.wave_kp[w], bestR = P->map.sf_rows[w];
+        for (int sched : {RLSQ_TRSV_WAVE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_LEVEL, RLSQ_TRSV_COOP, RLSQ_TRSV_BINNED}) {
             for (int G : cands) {
-                // the persistent and wavefront solves run one thread per row
-                if ((sched == RLSQ_TRSV_COOP || sched == RLSQ_TRSV_WAVE) && G != 1) continue;
-                for (int nb : {1, 2, 3, 6}) {
-                    // nb: resident blocks per SM (sync-free) or entries loaded ahead (wavefront: 4, 8)
-                    if (sched == RLSQ_TRSV_WAVE ? (nb != 1 && nb != 2) : (sched != RLSQ_TRSV_SYNCFREE && nb != 1))
-                        continue;
-                    P->map.sched[w] = sched;
-                    P->map.G_tri[w] = G;
-                    if (sched == RLSQ_TRSV_WAVE) P->map.wave_kp[w] = 4 * nb;
-                    else P->map.sf_blocks[w] = nb;
-                    float ms = 0.f;
-                    if (rlsq_trsv_time(P, w, &ms) != RLSQ_OK) continue;
-                    if (ms < tbest) {
-                        tbest = ms;
-                        bestG = G;
-                        bestS = sched;
-                        if (sched == RLSQ_TRSV_WAVE) bestK = 4 * nb;
-                        else bestB = nb;
+                // the persistent and wavefront solves run one thread per row; the
+                // binned solve picks lanes per row itself
+                if ((sched == RLSQ_TRSV_COOP || sched == RLSQ_TRSV_WAVE || sched == RLSQ_TRSV_BINNED) && G != 1)
+                    continue;
+                for (int R : {0, 1, 2, 4}) {
+                    // R: rows per lane group of the warp-ticketed sync-free solve (0: block tickets)
+                    if (R > 0 && (sched != RLSQ_TRSV_SYNCFREE || G > 8)) continue;
+                    for (int nb : {1, 2, 3, 4, 6, 8}) {
+                        // nb: resident blocks per SM (sync-free) or entries loaded ahead (wavefront: 4, 8)
+                        if (sched == RLSQ_TRSV_WAVE ? (nb != 1 && nb != 2) : (sched != RLSQ_TRSV_SYNCFREE && nb != 1))
+                            continue;
+                        if (sched == RLSQ_TRSV_SYNCFREE && R == 0 && (nb == 4 || nb == 8)) continue;
+                        P->map.sched[w] = sched;
+                        P->map.G_tri[w] = G;
+                        P->map.sf_rows[w] = R;
+                        if (sched == RLSQ_TRSV_WAVE) P->map.wave_kp[w] = 4 * nb;
+                        else P->map.sf_blocks[w] = nb;
+                        float ms = 0.f;
+                        if (rlsq_trsv_time(P, w, &ms) != RLSQ_OK) continue;
+                        if (log)
+                            std::fprintf(stderr, "tune system %d sched %d G %d R %d nb %d: %.4f ms\n", w, sched, G, R,
+                                         nb, ms);
+                        if (ms < tbest) {
+                            tbest = ms;
+                            bestG = G;
+                            bestS = sched;
+                            bestR = R;
+                            if (sched == RLSQ_TRSV_WAVE) bestK = 4 * nb;
+                            else bestB = nb;
+                        }
                     }
                 }
             }
@@ -123,6 +138,7 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
         P->map.sched[w] = bestS;
         P->map.sf_blocks[w] = bestB;
         P->map.wave_kp[w] = bestK;
+        P->map.sf_rows[w] = bestR;
     }
 }
 

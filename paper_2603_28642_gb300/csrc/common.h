@@ -94,6 +94,8 @@ struct Mapping {
     int sched[4] = {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE};
     int G_L2 = 4, G_L2t = 4;
     int sf_blocks[4] = {2, 2, 2, 2};    // sync-free solve: resident blocks per SM (bounds the polling rows)
+    int sf_rows[4] = {0, 0, 0, 0};      // sync-free solve: 0 = block tickets (k_trsv_sentinel); R = 1, 2, 4:
+                                        // warp tickets, R rows per lane group (k_trsv_warp)
     int wave_kp[4] = {4, 4, 4, 4};      // wavefront solve: entries per row loaded ahead (4 or 8)
 };
 
@@ -111,6 +113,13 @@ struct DevFactor {
     DevArray<int32_t> ell_idx[4];
     DevArray<T> ell_val[4];
     int ell_kp[4] = {4, 4, 4, 4};
+    // the binned form of each system (k_trsv_binned): rows of a level group
+    // sorted by the lanes they need, right-hand-side terms in the entry list
+    DevArray<int32_t> bptr[4], bidx[4], border[4], bgseg[4], bgitems[4], bgpos[4];
+    DevArray<T> bval[4], bdiag[4];
+    DevArray<BinSeg> bseg[4];
+    int bngroups[4] = {0, 0, 0, 0};
+    int64_t bentries[4] = {0, 0, 0, 0};
     DevCsr<T> L2, L2t;
     DevArray<T> d;
     DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
@@ -122,11 +131,20 @@ struct DevFactor {
             rtri[w].ptr.release(); rtri[w].idx.release(); rtri[w].val.release(); rtri[w].nnz = 0;
             diag[w].release(); order[w].release(); level_ptr[w].clear(); level_ptr_d[w].release();
             ell_idx[w].release(); ell_val[w].release();
+            for (auto* a : {&bptr[w], &bidx[w], &border[w], &bgseg[w], &bgitems[w], &bgpos[w]}) a->release();
+            bval[w].release(); bdiag[w].release(); bseg[w].release();
+            bngroups[w] = 0;
+            bentries[w] = 0;
         }
         for (auto* c : {&L2, &L2t}) { c->ptr.release(); c->idx.release(); c->val.release(); }
         d.release(); sinv.release();
         for (auto& v : vn) v.release();
         for (auto& v : vm) v.release();
+    }
+    BinTri<T> bview(int which) const {
+        return BinTri<T>{tri[which].rows, bngroups[which], bptr[which].p, bidx[which].p, bval[which].p,
+                         border[which].p, (which >= 2) ? bdiag[which].p : nullptr, bseg[which].p,
+                         bgseg[which].p, bgitems[which].p, bgpos[which].p};
     }
     // tri[w], diag[w] are stored by solve position (rows in level order)
     Tri<T> tview(int which) const {

@@ -685,6 +685,90 @@ k_trsv_sentinel(Tri<T> tri, Rhs<T> rhs, T* x, int slot, unsigned* tickets, const
     }
 }
 
+// Sync-free solve with warp-level tickets.  A warp takes R * (32 / G)
+// consecutive positions from the ticket counter; each group of G lanes
+// solves R of them (row r of the group at chunk + r * (32 / G) + lane / G),
+// reading the structure and the full right-hand sides of all R rows before
+// it waits on any unknown, so those loads are in flight together.  There is
+// no block-wide barrier: a warp whose rows wait holds up no other warp.
+// Readiness as in k_trsv_sentinel (all-one bytes = not yet solved).  A row
+// depends only on earlier positions, which sit in chunks taken earlier by
+// running warps or earlier in this warp's own chunk (an earlier r, or the
+// same r on a lower lane group), so every wait ends; the bound only guards
+// against faults.
+template <typename T, int G, int K, int R>
+__global__ void __launch_bounds__(kBlock)
+k_trsv_warp(Tri<T> tri, Rhs<T> rhs, T* x, int slot, unsigned* tickets, const LsmrState* S, int* err) {
+    if (S->done) return;
+    const int n = tri.n;
+    const unsigned mask = group_mask<G>();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (G - 1);
+    constexpr int per_pass = 32 / G;
+    constexpr int chunk_rows = per_pass * R;
+    for (;;) {
+        __syncwarp();
+        unsigned c = 0;
+        if (lane == 0) c = atomicAdd(&tickets[slot], 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        const long long c0 = (long long)c * chunk_rows;
+        if (c0 >= n) break;
+        int row[R], e0[R], e1[R];
+        T rv[R], dg[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long t = c0 + r * per_pass + lane / G;
+            row[r] = -1;
+            e0[r] = 0;
+            e1[r] = 0;
+            rv[r] = (T)0;
+            dg[r] = (T)1;
+            if (t < n) {
+                row[r] = tri.order[t];
+                e0[r] = tri.ptr[t] + sub;
+                e1[r] = tri.ptr[t + 1];
+                if (sub == 0) {
+                    rv[r] = rhs_full<T, K>(tri, rhs, (int)t, row[r]);
+                    if (tri.idiag) dg[r] = tri.idiag[t];
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            T sum = (T)0;
+            bool ok = true;
+            int e = e0[r];
+            const int e_end = e1[r];
+            for (; e + 3 * G < e_end; e += 4 * G) {
+                const int j0 = tri.idx[e], j1 = tri.idx[e + G], j2 = tri.idx[e + 2 * G], j3 = tri.idx[e + 3 * G];
+                const T a0 = tri.val[e], a1 = tri.val[e + G], a2 = tri.val[e + 2 * G], a3 = tri.val[e + 3 * G];
+                T v0 = ld_relaxed(&x[j0]), v1 = ld_relaxed(&x[j1]), v2 = ld_relaxed(&x[j2]), v3 = ld_relaxed(&x[j3]);
+                if (is_pending(v0)) v0 = wait_value(&x[j0], err, ok);
+                if (is_pending(v1)) v1 = wait_value(&x[j1], err, ok);
+                if (is_pending(v2)) v2 = wait_value(&x[j2], err, ok);
+                if (is_pending(v3)) v3 = wait_value(&x[j3], err, ok);
+                sum += a0 * v0 + a1 * v1 + a2 * v2 + a3 * v3;
+            }
+            for (; e < e_end; e += G) {
+                const int j = tri.idx[e];
+                T v = ld_relaxed(&x[j]);
+                if (is_pending(v)) v = wait_value(&x[j], err, ok);
+                sum += tri.val[e] * v;
+            }
+            if (G > 1) {
+                sum = group_sum<G>(sum, mask);
+                ok = __all_sync(mask, ok);
+            }
+            if (sub == 0 && row[r] >= 0) {
+                T v = rv[r] - sum;
+                if (tri.idiag) v = v * dg[r];
+                if (!ok) v = (T)NAN;
+                st_relaxed(&x[row[r]], v);
+            }
+        }
+    }
+}
+
 // Persistent level-synchronous solve: one co-resident block of kCoopBlock
 // threads per SM walks the levels in order, with a grid-wide barrier between
 // levels.  The barrier is split: a block arrives as soon as its rows of level
@@ -848,6 +932,228 @@ __device__ __forceinline__ void solve_row_csr(const Tri<T>& tri, const Rhs<T>& r
     T res = rhs_full<T, K>(tri, rhs, t, row) - sum;
     if (tri.idiag) res = res * dg;
     x[row] = res;
+}
+
+// ---- binned persistent solve ----------------------------------------------
+// A system stored for k_trsv_binned.  Rows are stored by "binned position":
+// the positions of a level group are the group's rows, sorted by the lanes
+// their entry count needs.  Each row is one flat entry list:
+//   x_i = -(sum_e val_e * v_e) * d_i,
+// where an entry with idx >= 0 reads the unknown x[idx] (a substituted or
+// triangular dependency, val = its coefficient) and an entry with idx < 0
+// reads the right-hand side at (idx & 0x7fffffff) (the row's own term with
+// val = -1, a fused right-hand-side term c with val = -c).  The whole row is
+// then one dot product whose gathers can all be in flight together.
+// A segment is a run of rows of one group that all take G lanes each; the
+// warps of the grid deal the segment's work items (32 / G rows each) among
+// themselves.
+struct BinSeg {
+    int32_t p0, p1;       // binned positions [p0, p1)
+    int32_t G;            // lanes per row (1, 2, 4, 8, 16, 32)
+    int32_t item0;        // first work item of the segment within its group
+};
+
+template <typename T>
+struct BinTri {
+    int32_t n, ngroups;
+    const int32_t* ptr;      // n + 1 entry offsets, by binned position
+    const int32_t* idx;      // see above
+    const T* val;
+    const int32_t* order;    // unknown solved at each binned position
+    const T* idiag;          // inverse diagonal by binned position; nullptr: unit diagonal
+    const BinSeg* seg;
+    const int32_t* gseg;     // segments of group g: [gseg[g], gseg[g + 1])
+    const int32_t* gitems;   // work items of group g
+    const int32_t* gpos;     // first binned position of group g (ngroups + 1 entries)
+};
+
+// Bulk prefetch of [p, p + bytes) into L2, in pieces of at most 1 MiB.  Only
+// whole 16-byte units inside the range are asked for (the instruction wants
+// 16-byte aligned addresses and sizes), so nothing outside it is touched.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    uintptr_t lo = (a + 15) & ~(uintptr_t)15;
+    const uintptr_t hi = (a + bytes) & ~(uintptr_t)15;
+    while (lo < hi) {
+        const uintptr_t piece = (hi - lo < ((uintptr_t)1 << 20)) ? hi - lo : ((uintptr_t)1 << 20);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)piece) : "memory");
+        lo += piece;
+    }
+}
+
+// What a lane holds of its row in a work item before the unknowns it needs
+// are ready: the right-hand-side part of the row's sum (those entries depend
+// on no unknown), and the first four unknown entries of its share.
+template <typename T>
+struct BinLane {
+    int t;        // binned position (-1: no row for this lane)
+    int e, e1;    // next entry of this lane's share still to read, end of the row
+    T part;       // sum over the right-hand-side entries read so far
+    int j[4];     // unknown ids of pending entries (-1: none)
+    T a[4];
+};
+
+// Work item `item` of segment sg: 32 / G consecutive binned positions, G
+// lanes per row (lane & (G - 1) takes entries sub, sub + G, ...).  Reads the
+// lane's first four entries; right-hand-side entries are gathered and summed
+// at once, unknown entries are kept for after the wait.
+template <typename T, int K>
+__device__ __forceinline__ void binned_prepare(const BinTri<T>& bt, const Rhs<T>& rhs, const BinSeg& sg, int item,
+                                               int lane, BinLane<T>& L) {
+    const int G = sg.G;
+    const int t = sg.p0 + item * (32 / G) + lane / G;
+    L.t = t < sg.p1 ? t : -1;
+    L.part = (T)0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        L.j[q] = -1;
+        L.a[q] = (T)0;
+    }
+    if (L.t < 0) {
+        L.e = L.e1 = 0;
+        return;
+    }
+    const int sub = lane & (G - 1);
+    const int e0 = __ldg(&bt.ptr[t]) + sub;
+    L.e1 = __ldg(&bt.ptr[t + 1]);
+    int jj[4];
+    T aa[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool in = e0 + q * G < L.e1;
+        jj[q] = in ? __ldg(&bt.idx[e0 + q * G]) : 0;
+        aa[q] = in ? __ldg(&bt.val[e0 + q * G]) : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (jj[q] < 0) {
+            L.part += aa[q] * rhs_at<T, K>(rhs, jj[q] & 0x7fffffff);
+        } else if (e0 + q * G < L.e1) {
+            L.j[q] = jj[q];
+            L.a[q] = aa[q];
+        }
+    }
+    L.e = e0 + 4 * G;
+}
+
+// The rest of the item once every unknown of earlier groups is stored: the
+// pending gathers, the lane's remaining entries (rows longer than 4 G), the
+// reduction over the row's lanes and the store.
+template <typename T, int K>
+__device__ __forceinline__ void binned_finish(const BinTri<T>& bt, const Rhs<T>& rhs, const BinSeg& sg, int lane,
+                                              const BinLane<T>& L, T* x) {
+    const int G = sg.G;
+    T v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = L.j[q] >= 0 ? __ldcg(&x[L.j[q]]) : (T)0;
+    T sum = L.part;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sum += L.a[q] * v[q];
+    for (int e = L.e; e < L.e1; e += 4 * G) {
+        int jj[4];
+        T aa[4], vv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool in = e + q * G < L.e1;
+            jj[q] = in ? __ldg(&bt.idx[e + q * G]) : 0;
+            aa[q] = in ? __ldg(&bt.val[e + q * G]) : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vv[q] = jj[q] >= 0 ? __ldcg(&x[jj[q]]) : rhs_at<T, K>(rhs, jj[q] & 0x7fffffff);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sum += aa[q] * vv[q];
+    }
+    // sum over the row's G lanes (all of them have the same t, so all take part)
+    const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    for (int off = G / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(mask, sum, off, G);
+    if (L.t >= 0 && (lane & (G - 1)) == 0) {
+        T r = -sum;
+        if (bt.idiag) r = r * __ldg(&bt.idiag[L.t]);
+        x[__ldg(&bt.order[L.t])] = r;
+    }
+}
+
+// Finds the segment of work item k of a group (segments in item order).
+__device__ __forceinline__ int binned_seg(const BinSeg* seg, int s, int s1, int k) {
+    while (s + 1 < s1 && __ldg(&seg[s + 1].item0) <= k) ++s;
+    return s;
+}
+
+constexpr int kBinBlock = 1024;
+
+// Persistent level-synchronous solve over binned groups.  Every block walks
+// the groups in order; within a group the warps of the whole grid deal the
+// work items of its segments (warp w takes items w, w + W, ...; warps are
+// numbered across blocks first, so a small group still spreads over every
+// SM).  Between groups a grid barrier, split: a block arrives once its rows
+// are stored, then every warp reads the structure of its first item of the
+// next group and gathers that item's right-hand-side entries -- none of it
+// depends on an unknown -- and only then does the block wait (bounded by
+// kWaitNs).  After the wait only the gathers of unknowns remain.  Block 0
+// also asks L2 for the next-but-one group's entries (bulk prefetch).  x is
+// read through L2 (__ldcg): other SMs wrote it.  No pre-fill of x is needed.
+template <typename T, int K>
+__global__ void __launch_bounds__(kBinBlock, 1)
+k_trsv_binned(BinTri<T> bt, Rhs<T> rhs, T* x, unsigned* bar, const LsmrState* S, int* err) {
+    if (S->done) return;
+    const int warps_per_block = blockDim.x >> 5;
+    const int W = gridDim.x * warps_per_block;
+    const int gw = blockIdx.x + gridDim.x * (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    auto prefetch_group = [&](int g) {
+        if (g >= bt.ngroups || threadIdx.x != 0) return;
+        const int p0 = __ldg(&bt.gpos[g]), p1 = __ldg(&bt.gpos[g + 1]);
+        const long long e0 = __ldg(&bt.ptr[p0]), e1 = __ldg(&bt.ptr[p1]);
+        const long long per = (e1 - e0 + gridDim.x - 1) / gridDim.x;
+        const long long a = e0 + per * blockIdx.x, b = min(e1, a + per);
+        if (a < b) {
+            prefetch_l2(bt.idx + a, (size_t)(b - a) * sizeof(int32_t));
+            prefetch_l2(bt.val + a, (size_t)(b - a) * sizeof(T));
+        }
+        const long long pp = (p1 - p0 + gridDim.x - 1) / gridDim.x;
+        const long long q0 = p0 + pp * blockIdx.x, q1 = min((long long)p1, q0 + pp);
+        if (q0 < q1) {
+            prefetch_l2(bt.order + q0, (size_t)(q1 - q0) * sizeof(int32_t));
+            prefetch_l2(bt.ptr + q0, (size_t)(q1 - q0 + 1) * sizeof(int32_t));
+            if (bt.idiag) prefetch_l2(bt.idiag + q0, (size_t)(q1 - q0) * sizeof(T));
+        }
+    };
+    prefetch_group(0);
+    prefetch_group(1);
+    // the warp's first item of group 0, prepared
+    BinLane<T> L;
+    int s = __ldg(&bt.gseg[0]);
+    bool have = false;
+    if (gw < __ldg(&bt.gitems[0])) {
+        s = binned_seg(bt.seg, s, __ldg(&bt.gseg[1]), gw);
+        binned_prepare<T, K>(bt, rhs, bt.seg[s], gw - __ldg(&bt.seg[s].item0), lane, L);
+        have = true;
+    }
+    for (int g = 0; g < bt.ngroups; ++g) {
+        const int s0 = __ldg(&bt.gseg[g]), s1 = __ldg(&bt.gseg[g + 1]);
+        const int items = __ldg(&bt.gitems[g]);
+        if (g > 0) {
+            // first item of this group: structure and right-hand sides while others finish
+            have = gw < items;
+            if (have) {
+                s = binned_seg(bt.seg, s0, s1, gw);
+                binned_prepare<T, K>(bt, rhs, bt.seg[s], gw - __ldg(&bt.seg[s].item0), lane, L);
+            }
+            prefetch_group(g + 1);
+            grid_wait(bar, (unsigned)g * gridDim.x, err);
+            if (*(volatile int*)err != 0) return;
+        }
+        if (have) {
+            binned_finish<T, K>(bt, rhs, bt.seg[s], lane, L, x);
+            for (int k = gw + W; k < items; k += W) {
+                s = binned_seg(bt.seg, s, s1, k);
+                const BinSeg sg = bt.seg[s];
+                binned_prepare<T, K>(bt, rhs, sg, k - sg.item0, lane, L);
+                binned_finish<T, K>(bt, rhs, sg, lane, L, x);
+            }
+        }
+        if (g + 1 < bt.ngroups) grid_arrive(bar);
+    }
 }
 
 // Dynamic shared memory of k_trsv_coop.

@@ -57,10 +57,99 @@ static void upload_vec(DevArray<T>& dst, const std::vector<double>& src, cudaStr
     RLSQ_CUDA(cudaStreamSynchronize(s));
 }
 
+// Lanes per row of the binned solve: enough that every lane gathers at most
+// four entries in one round (32 lanes for rows longer than 64 entries).
+static int binned_lanes(int64_t entries) {
+    int g = 1;
+    while (g < 32 && 4 * g < entries) g *= 2;
+    return g;
+}
+
+// The binned form of one fused system (see BinTri): within each level group
+// the rows are ordered by lanes per row, most first (ties: solve position);
+// a row's entries are its own right-hand side (-1), its right-hand-side
+// terms (-c) and its dependencies (c).
+template <typename T>
+static void upload_binned(DevFactor<T>& D, int w, const IlupResult& F, const MergedTri& M, cudaStream_t s) {
+    const std::vector<int32_t>& ord = M.lev.order;
+    const std::vector<int32_t>& lp = M.lev.level_ptr;
+    const int64_t n = static_cast<int64_t>(ord.size());
+    const int ng = static_cast<int>(lp.size()) - 1;
+    const bool fused = M.R.nnz() > 0;
+    auto count = [&](int32_t r) {
+        return (M.T.ptr[r + 1] - M.T.ptr[r]) + (fused ? M.R.ptr[r + 1] - M.R.ptr[r] : 0) + 1;
+    };
+    std::vector<int32_t> bord(ord.size());
+    std::vector<BinSeg> seg;
+    std::vector<int32_t> gseg(static_cast<size_t>(ng) + 1, 0), gitems(static_cast<size_t>(std::max(ng, 1)), 0),
+        gpos(static_cast<size_t>(ng) + 1, 0);
+    for (int g = 0; g < ng; ++g) {
+        const int32_t p0 = lp[g], p1 = lp[g + 1];
+        gpos[g] = p0;
+        gseg[g] = static_cast<int32_t>(seg.size());
+        // counting sort of the group's rows by lanes (32, 16, ..., 1)
+        int32_t at = p0;
+        int32_t item = 0;
+        for (int G = 32; G >= 1; G /= 2) {
+            const int32_t s0 = at;
+            for (int32_t t = p0; t < p1; ++t)
+                if (binned_lanes(count(ord[t])) == G) bord[at++] = ord[t];
+            if (at > s0) {
+                seg.push_back(BinSeg{s0, at, G, item});
+                item += (at - s0 + (32 / G) - 1) / (32 / G);
+            }
+        }
+        gitems[g] = item;
+    }
+    gseg[ng] = static_cast<int32_t>(seg.size());
+    gpos[ng] = static_cast<int32_t>(n);
+    std::vector<int32_t> bp(static_cast<size_t>(n) + 1, 0);
+    for (int64_t t = 0; t < n; ++t) bp[t + 1] = bp[t] + static_cast<int32_t>(count(bord[t]));
+    const int64_t ne = bp[n];
+    if (ne >= (int64_t(1) << 31)) throw ApiError(RLSQ_ERR_SHAPE, "binned solve: more than 2^31 - 1 entries");
+    std::vector<int32_t> bi(static_cast<size_t>(std::max<int64_t>(ne, 1)));
+    std::vector<T> bv(bi.size());
+    const int32_t flag = static_cast<int32_t>(0x80000000u);
+    for (int64_t t = 0; t < n; ++t) {
+        const int32_t r = bord[t];
+        int64_t e = bp[t];
+        bi[e] = r | flag;
+        bv[e++] = (T)-1.0;
+        if (fused)
+            for (int64_t q = M.R.ptr[r]; q < M.R.ptr[r + 1]; ++q) {
+                bi[e] = M.R.idx[q] | flag;
+                bv[e++] = (T)(-M.R.val[q]);
+            }
+        for (int64_t q = M.T.ptr[r]; q < M.T.ptr[r + 1]; ++q) {
+            bi[e] = M.T.idx[q];
+            bv[e++] = (T)M.T.val[q];
+        }
+    }
+    D.bptr[w].upload(bp.data(), bp.size(), s);
+    D.bidx[w].upload(bi.data(), bi.size(), s);
+    D.bval[w].upload(bv.data(), bv.size(), s);
+    D.border[w].upload(bord.data(), bord.size(), s);
+    if (w >= 2) {
+        std::vector<T> dl(static_cast<size_t>(n));
+        for (int64_t t = 0; t < n; ++t) dl[t] = (T)(1.0 / F.Udiag[bord[t]]);
+        D.bdiag[w].upload(dl.data(), dl.size(), s);
+        RLSQ_CUDA(cudaStreamSynchronize(s));
+    }
+    D.bseg[w].upload(seg.data(), seg.size(), s);
+    D.bgseg[w].upload(gseg.data(), gseg.size(), s);
+    D.bgitems[w].upload(gitems.data(), gitems.size(), s);
+    D.bgpos[w].upload(gpos.data(), gpos.size(), s);
+    D.bngroups[w] = ng;
+    D.bentries[w] = ne;
+    // the host vectors die at return
+    RLSQ_CUDA(cudaStreamSynchronize(s));
+}
+
 template <typename T>
 void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h,
                           cudaStream_t s) {
     for (int w = 0; w < 4; ++w) {
+        upload_binned<T>(*this, w, F, merged[w], s);
         // rows permuted into solve order so each level is contiguous
         const MergedTri& M = merged[w];
         const std::vector<int32_t>& ord = M.lev.order;
@@ -293,6 +382,25 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
             RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, F.level_ptr_d[which].p + lead, nlev,
                                          P->barriers.p + slot, static_cast<const LsmrState*>(S), error_word(S)));
         });
+    } else if (P->map.sched[which] == RLSQ_TRSV_BINNED) {
+        if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
+        const BinTri<T> bt = F.bview(which);
+        with_rhs(rk, [&](auto k) {
+            auto kern = k_trsv_binned<T, decltype(k)::value>;
+            int occ = 0;
+            RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBinBlock, 0));
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(static_cast<unsigned>(std::max(1, occ) * P->num_sms));
+            cfg.blockDim = dim3(kBinBlock);
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, bt, rhs, x, P->barriers.p + slot, static_cast<const LsmrState*>(S),
+                                         error_word(S)));
+        });
     } else if (P->map.sched[which] == RLSQ_TRSV_WAVE) {
         // all-one bytes mark "not yet solved" (see k_trsv_wave)
         RLSQ_CUDA(cudaMemsetAsync(x, 0xff, sizeof(T) * static_cast<size_t>(n), st));
@@ -322,20 +430,27 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
         if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
         // all-one bytes mark "not yet solved" (see k_trsv_sentinel)
         RLSQ_CUDA(cudaMemsetAsync(x, 0xff, sizeof(T) * static_cast<size_t>(n), st));
+        const int R = P->map.sf_rows[which];
         with_G(G, [&](auto g) {
             constexpr int GG = decltype(g)::value;
-            constexpr int ROUNDS = 1;
-            const int chunk_rows = (kBlock / GG) * ROUNDS;
-            const int chunks = (n + chunk_rows - 1) / chunk_rows;
             with_rhs(rk, [&](auto k) {
-                auto kern = k_trsv_sentinel<T, GG, decltype(k)::value, ROUNDS>;
-                int occ = 0;
-                RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, 0));
-                // rows in flight = grid * kBlock / G; every one of them polls, so
-                // the window is kept to a few levels rather than the whole GPU
-                occ = std::max(1, std::min(occ, P->map.sf_blocks[which]));
-                const int grid = std::max(1, std::min(chunks, occ * P->num_sms));
-                kern<<<grid, kBlock, 0, st>>>(tri, rhs, x, slot, P->tickets.p, S, error_word(S));
+                constexpr int KK = decltype(k)::value;
+                // rows in flight = grid * kBlock / G (times R); every one of them
+                // polls, so the window is kept to a few levels rather than the
+                // whole GPU
+                auto run = [&](auto kern, int chunk_rows) {
+                    int occ = 0;
+                    RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, 0));
+                    occ = std::max(1, std::min(occ, P->map.sf_blocks[which]));
+                    const int chunks = (n + chunk_rows - 1) / chunk_rows;
+                    const int blocks_needed = (chunks + kBlock / 32 - 1) / (kBlock / 32);
+                    const int grid = std::max(1, std::min(R > 0 ? blocks_needed : chunks, occ * P->num_sms));
+                    kern<<<grid, kBlock, 0, st>>>(tri, rhs, x, slot, P->tickets.p, S, error_word(S));
+                };
+                if (R >= 4) run(k_trsv_warp<T, GG, KK, 4>, (32 / GG) * 4);
+                else if (R == 2) run(k_trsv_warp<T, GG, KK, 2>, (32 / GG) * 2);
+                else if (R == 1) run(k_trsv_warp<T, GG, KK, 1>, 32 / GG);
+                else run(k_trsv_sentinel<T, GG, KK, 1>, kBlock / GG);
             });
         });
     }
@@ -915,6 +1030,9 @@ void default_mapping(rlsq_problem_s* P) {
             const double avg = nz / std::max(1.0, n);
             P->map.G_tri[w] = avg <= 12.0 ? 1 : pow2_lanes(avg / 4.0, 1, 32);
             P->map.sched[w] = RLSQ_TRSV_SYNCFREE;
+            P->map.sf_blocks[w] = 2;
+            P->map.sf_rows[w] = 0;
+            P->map.wave_kp[w] = 4;
         }
         P->map.G_L2 = pow2_lanes(F.L2.nnz() / std::max(1.0, m - n) / 4.0, 1, 32);
         P->map.G_L2t = pow2_lanes(F.L2t.nnz() / std::max(1.0, n) / 4.0, 1, 32);
@@ -1111,6 +1229,8 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
             (opts.precision != RLSQ_PREC_FP64 && opts.precision != RLSQ_PREC_FP32))
             throw ApiError(RLSQ_ERR_ARG, "bad factor option");
         if (opts.cg_steps > 16) throw ApiError(RLSQ_ERR_ARG, "cg_steps must be <= 16");
+        if (opts.trsv_rows != 0 && opts.trsv_rows != 1 && opts.trsv_rows != 2 && opts.trsv_rows != 4)
+            throw ApiError(RLSQ_ERR_ARG, "trsv_rows must be 0, 1, 2 or 4");
         const auto t0 = std::chrono::steady_clock::now();
         h->factored = false;
         drop_graphs(h);
@@ -1236,8 +1356,14 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         h->precision = opts.precision;
         default_mapping(h);
         if (opts.trsv_schedule == RLSQ_TRSV_LEVEL || opts.trsv_schedule == RLSQ_TRSV_SYNCFREE ||
-            opts.trsv_schedule == RLSQ_TRSV_COOP || opts.trsv_schedule == RLSQ_TRSV_WAVE)
+            opts.trsv_schedule == RLSQ_TRSV_COOP || opts.trsv_schedule == RLSQ_TRSV_WAVE ||
+            opts.trsv_schedule == RLSQ_TRSV_BINNED)
             for (int w = 0; w < 4; ++w) h->map.sched[w] = opts.trsv_schedule;
+        for (int w = 0; w < 4; ++w) {
+            h->map.sf_rows[w] = opts.trsv_rows;
+            // the warp-ticketed solve takes at most 8 lanes per row
+            if (opts.trsv_rows > 0) h->map.G_tri[w] = std::min(h->map.G_tri[w], 8);
+        }
         h->factored = true;
         if (opts.autotune) autotune(h);
         h->factor_seconds =

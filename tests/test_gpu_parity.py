@@ -125,7 +125,7 @@ SOLVES = [(B.SYS_L1, "solve_L1"), (B.SYS_L1T, "solve_L1t"), (B.SYS_U, "solve_U")
           (B.SYS_UT, "solve_Ut")]
 
 
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE, B.TRSV_BINNED])
 @pytest.mark.parametrize("which", ["cfg0", "mid"])
 def test_triangular_solves(sched, which, request):
     prob = request.getfixturevalue(which)
@@ -139,6 +139,28 @@ def test_triangular_solves(sched, which, request):
         assert close(x, ref, 1e-12), (sys_id, rel(x, ref), rel_inf(x, ref))
 
 
+@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("which", ["cfg0", "mid"])
+def test_triangular_solves_warp_tickets(rows, which, request):
+    """The sync-free solve with warp-level tickets, `rows` rows per lane group."""
+    prob = request.getfixturevalue(which)
+    P = make(prob, B.CORR_CG, sched=B.TRSV_SYNCFREE, trsv_rows=rows)
+    f = oracle_factor(prob, oracle.CG)
+    b = np.random.default_rng(13).standard_normal(prob.n)
+    for sys_id, name in SOLVES:
+        x = P.trsv(sys_id, b)
+        ref = getattr(f, name)(b)
+        assert close(x, ref, 1e-12), (sys_id, rel(x, ref), rel_inf(x, ref))
+    assert close(P.apply(b), f.apply(b), 1e-12)
+
+
+def test_trsv_rows_option_checked(cfg0):
+    P = B.Problem.from_problem(cfg0)
+    with pytest.raises(B.RlsqError) as e:
+        P.factor(mu=MU, trsv_rows=3)
+    assert e.value.code == -1
+
+
 @pytest.fixture(scope="module")
 def wide():
     # more rows than the wavefront solve has resident threads, so every thread
@@ -148,13 +170,16 @@ def wide():
 
 
 @pytest.mark.parametrize("k", [0, 1, 2, 4])
-@pytest.mark.parametrize("sched", [B.TRSV_WAVE, B.TRSV_SYNCFREE, B.TRSV_COOP])
+@pytest.mark.parametrize("sched", [B.TRSV_WAVE, B.TRSV_SYNCFREE, B.TRSV_COOP, B.TRSV_BINNED, "warp"])
 def test_triangular_solves_many_rounds(wide, sched, k):
     # k = 0: fused groups chosen by the cost model (fixed k or level by level);
     # k = 4: the first groups are wider than the persistent grid, which then
-    # starts with level launches
+    # starts with level launches; "warp": the sync-free solve with warp tickets
     prob, f = wide
-    P = make(prob, B.CORR_CG, sched=sched, level_merge=k)
+    if sched == "warp":
+        P = make(prob, B.CORR_CG, sched=B.TRSV_SYNCFREE, level_merge=k, trsv_rows=4)
+    else:
+        P = make(prob, B.CORR_CG, sched=sched, level_merge=k)
     info = P.info()
     assert all(s <= l for s, l in zip(info["solve_levels"], [info["levels_L1"], info["levels_L1t"],
                                                              info["levels_U"], info["levels_Ut"]]))
@@ -180,7 +205,7 @@ def test_triangular_solves_all_lane_counts(cfg0):
 # one preconditioner application, every correction mode
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("modes", MODES, ids=["NONE", "SI", "CG", "DENSE"])
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE, B.TRSV_BINNED])
 def test_apply_fp64(cfg0, modes, sched):
     bm, om = modes
     P = make(cfg0, bm, sched=sched)
@@ -375,7 +400,7 @@ def test_dense_block_off_gives_same_solution(sparse_dense):
 # fused levels: same solutions, fewer levels
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("k", [1, 2, 3])
-@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE])
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE, B.TRSV_BINNED])
 def test_fused_levels_solves(mid, k, sched):
     P = make(mid, B.CORR_CG, sched=sched, level_merge=k)
     info = P.info()
