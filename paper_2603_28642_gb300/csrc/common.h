@@ -115,7 +115,7 @@ struct DevFactor {
     int ell_kp[4] = {4, 4, 4, 4};
     // the binned form of each system (k_trsv_binned): rows of a level group
     // sorted by the lanes they need, right-hand-side terms in the entry list
-    DevArray<int32_t> bptr[4], bidx[4], border[4], bgseg[4], bgitems[4], bgpos[4];
+    DevArray<int32_t> bidx[4], border[4], bgseg[4], bgitems[4], bgpos[4], bgentry[4];
     DevArray<T> bval[4], bdiag[4];
     DevArray<BinSeg> bseg[4];
     int bngroups[4] = {0, 0, 0, 0};
@@ -131,7 +131,7 @@ struct DevFactor {
             rtri[w].ptr.release(); rtri[w].idx.release(); rtri[w].val.release(); rtri[w].nnz = 0;
             diag[w].release(); order[w].release(); level_ptr[w].clear(); level_ptr_d[w].release();
             ell_idx[w].release(); ell_val[w].release();
-            for (auto* a : {&bptr[w], &bidx[w], &border[w], &bgseg[w], &bgitems[w], &bgpos[w]}) a->release();
+            for (auto* a : {&bidx[w], &border[w], &bgseg[w], &bgitems[w], &bgpos[w], &bgentry[w]}) a->release();
             bval[w].release(); bdiag[w].release(); bseg[w].release();
             bngroups[w] = 0;
             bentries[w] = 0;
@@ -142,9 +142,9 @@ struct DevFactor {
         for (auto& v : vm) v.release();
     }
     BinTri<T> bview(int which) const {
-        return BinTri<T>{tri[which].rows, bngroups[which], bptr[which].p, bidx[which].p, bval[which].p,
+        return BinTri<T>{tri[which].rows, bngroups[which], bidx[which].p, bval[which].p,
                          border[which].p, (which >= 2) ? bdiag[which].p : nullptr, bseg[which].p,
-                         bgseg[which].p, bgitems[which].p, bgpos[which].p};
+                         bgseg[which].p, bgitems[which].p, bgpos[which].p, bgentry[which].p};
     }
     // tri[w], diag[w] are stored by solve position (rows in level order)
     Tri<T> tview(int which) const {

@@ -940,23 +940,27 @@ __device__ __forceinline__ void solve_row_csr(const Tri<T>& tri, const Rhs<T>& r
 // their entry count needs.  Each row is one flat entry list:
 //   x_i = -(sum_e val_e * v_e) * d_i,
 // where an entry with idx >= 0 reads the unknown x[idx] (a substituted or
-// triangular dependency, val = its coefficient) and an entry with idx < 0
+// triangular dependency, val = its coefficient), an entry with idx < -1
 // reads the right-hand side at (idx & 0x7fffffff) (the row's own term with
-// val = -1, a fused right-hand-side term c with val = -c).  The whole row is
-// then one dot product whose gathers can all be in flight together.
-// A segment is a run of rows of one group that all take G lanes each; the
-// warps of the grid deal the segment's work items (32 / G rows each) among
-// themselves.
+// val = -1, a fused right-hand-side term c with val = -c), and idx = -1 is
+// padding.  The whole row is one dot product whose gathers can all be in
+// flight together.  A segment is a run of rows of one group that all take G
+// lanes each; each of its rows owns a slot of `cap` entries (the segment's
+// longest row, rounded up to a multiple of G) at base + (t - p0) * cap, so a
+// row's entries need no row-pointer lookup and lane `sub` reads entries
+// sub, sub + G, ... (coalesced across the warp).  The warps of the grid deal
+// the segment's work items (32 / G rows each) among themselves.
 struct BinSeg {
     int32_t p0, p1;       // binned positions [p0, p1)
     int32_t G;            // lanes per row (1, 2, 4, 8, 16, 32)
     int32_t item0;        // first work item of the segment within its group
+    int32_t cap;          // entries per row slot
+    int32_t base;         // entry offset of the segment's first slot
 };
 
 template <typename T>
 struct BinTri {
     int32_t n, ngroups;
-    const int32_t* ptr;      // n + 1 entry offsets, by binned position
     const int32_t* idx;      // see above
     const T* val;
     const int32_t* order;    // unknown solved at each binned position
@@ -965,6 +969,7 @@ struct BinTri {
     const int32_t* gseg;     // segments of group g: [gseg[g], gseg[g + 1])
     const int32_t* gitems;   // work items of group g
     const int32_t* gpos;     // first binned position of group g (ngroups + 1 entries)
+    const int32_t* gentry;   // first entry of group g (ngroups + 1 entries)
 };
 
 // Bulk prefetch of [p, p + bytes) into L2, in pieces of at most 1 MiB.  Only
@@ -982,95 +987,85 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 }
 
 // What a lane holds of its row in a work item before the unknowns it needs
-// are ready: the right-hand-side part of the row's sum (those entries depend
-// on no unknown), and the first four unknown entries of its share.
+// are ready: where the row goes, and the first four entries of its share.
 template <typename T>
 struct BinLane {
     int t;        // binned position (-1: no row for this lane)
-    int e, e1;    // next entry of this lane's share still to read, end of the row
-    T part;       // sum over the right-hand-side entries read so far
-    int j[4];     // unknown ids of pending entries (-1: none)
+    int row;      // unknown solved there
+    int slot;     // entry offset of the row's slot
+    T dg;         // inverse diagonal (1: unit)
+    int j[4];     // entry ids (-1: padding or none)
     T a[4];
 };
 
 // Work item `item` of segment sg: 32 / G consecutive binned positions, G
-// lanes per row (lane & (G - 1) takes entries sub, sub + G, ...).  Reads the
-// lane's first four entries; right-hand-side entries are gathered and summed
-// at once, unknown entries are kept for after the wait.
-template <typename T, int K>
-__device__ __forceinline__ void binned_prepare(const BinTri<T>& bt, const Rhs<T>& rhs, const BinSeg& sg, int item,
-                                               int lane, BinLane<T>& L) {
+// lanes per row.  Reads the lane's first four entries and the row's
+// placement, none of which depends on an unknown.
+template <typename T>
+__device__ __forceinline__ void binned_prepare(const BinTri<T>& bt, const BinSeg& sg, int item, int lane,
+                                               BinLane<T>& L) {
     const int G = sg.G;
     const int t = sg.p0 + item * (32 / G) + lane / G;
-    L.t = t < sg.p1 ? t : -1;
-    L.part = (T)0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        L.j[q] = -1;
-        L.a[q] = (T)0;
-    }
-    if (L.t < 0) {
-        L.e = L.e1 = 0;
-        return;
-    }
     const int sub = lane & (G - 1);
-    const int e0 = __ldg(&bt.ptr[t]) + sub;
-    L.e1 = __ldg(&bt.ptr[t + 1]);
-    int jj[4];
-    T aa[4];
+    L.t = t < sg.p1 ? t : -1;
+    L.row = 0;
+    L.dg = (T)1;
+    L.slot = sg.base + (t - sg.p0) * sg.cap;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const bool in = e0 + q * G < L.e1;
-        jj[q] = in ? __ldg(&bt.idx[e0 + q * G]) : 0;
-        aa[q] = in ? __ldg(&bt.val[e0 + q * G]) : (T)0;
+        const int k = sub + q * G;
+        const bool in = L.t >= 0 && k < sg.cap;
+        L.j[q] = in ? __ldg(&bt.idx[L.slot + k]) : -1;
+        L.a[q] = in ? __ldg(&bt.val[L.slot + k]) : (T)0;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (jj[q] < 0) {
-            L.part += aa[q] * rhs_at<T, K>(rhs, jj[q] & 0x7fffffff);
-        } else if (e0 + q * G < L.e1) {
-            L.j[q] = jj[q];
-            L.a[q] = aa[q];
-        }
+    if (L.t >= 0 && sub == 0) {
+        L.row = __ldg(&bt.order[t]);
+        if (bt.idiag) L.dg = __ldg(&bt.idiag[t]);
     }
-    L.e = e0 + 4 * G;
+}
+
+template <typename T, int K>
+__device__ __forceinline__ T binned_value(const Rhs<T>& rhs, const T* x, int j) {
+    if (j >= 0) return __ldcg(&x[j]);
+    if (j == -1) return (T)0;
+    return rhs_at<T, K>(rhs, j & 0x7fffffff);
 }
 
 // The rest of the item once every unknown of earlier groups is stored: the
-// pending gathers, the lane's remaining entries (rows longer than 4 G), the
-// reduction over the row's lanes and the store.
+// gathers of the prepared entries (unknowns and right-hand sides together),
+// the lane's remaining entries (rows longer than 4 G), the reduction over the
+// row's lanes and the store.
 template <typename T, int K>
 __device__ __forceinline__ void binned_finish(const BinTri<T>& bt, const Rhs<T>& rhs, const BinSeg& sg, int lane,
                                               const BinLane<T>& L, T* x) {
     const int G = sg.G;
+    const int sub = lane & (G - 1);
     T v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = L.j[q] >= 0 ? __ldcg(&x[L.j[q]]) : (T)0;
-    T sum = L.part;
+    for (int q = 0; q < 4; ++q) v[q] = binned_value<T, K>(rhs, x, L.j[q]);
+    T sum = (T)0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) sum += L.a[q] * v[q];
-    for (int e = L.e; e < L.e1; e += 4 * G) {
-        int jj[4];
-        T aa[4], vv[4];
+    if (L.t >= 0) {
+        for (int k = sub + 4 * G; k < sg.cap; k += 4 * G) {
+            int jj[4];
+            T aa[4], vv[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const bool in = e + q * G < L.e1;
-            jj[q] = in ? __ldg(&bt.idx[e + q * G]) : 0;
-            aa[q] = in ? __ldg(&bt.val[e + q * G]) : (T)0;
+            for (int q = 0; q < 4; ++q) {
+                const bool in = k + q * G < sg.cap;
+                jj[q] = in ? __ldg(&bt.idx[L.slot + k + q * G]) : -1;
+                aa[q] = in ? __ldg(&bt.val[L.slot + k + q * G]) : (T)0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vv[q] = binned_value<T, K>(rhs, x, jj[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sum += aa[q] * vv[q];
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) vv[q] = jj[q] >= 0 ? __ldcg(&x[jj[q]]) : rhs_at<T, K>(rhs, jj[q] & 0x7fffffff);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sum += aa[q] * vv[q];
     }
     // sum over the row's G lanes (all of them have the same t, so all take part)
     const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     for (int off = G / 2; off > 0; off >>= 1) sum += __shfl_xor_sync(mask, sum, off, G);
-    if (L.t >= 0 && (lane & (G - 1)) == 0) {
-        T r = -sum;
-        if (bt.idiag) r = r * __ldg(&bt.idiag[L.t]);
-        x[__ldg(&bt.order[L.t])] = r;
-    }
+    if (L.t >= 0 && sub == 0) x[L.row] = (-sum) * L.dg;
 }
 
 // Finds the segment of work item k of a group (segments in item order).
@@ -1086,12 +1081,12 @@ constexpr int kBinBlock = 1024;
 // work items of its segments (warp w takes items w, w + W, ...; warps are
 // numbered across blocks first, so a small group still spreads over every
 // SM).  Between groups a grid barrier, split: a block arrives once its rows
-// are stored, then every warp reads the structure of its first item of the
-// next group and gathers that item's right-hand-side entries -- none of it
-// depends on an unknown -- and only then does the block wait (bounded by
-// kWaitNs).  After the wait only the gathers of unknowns remain.  Block 0
-// also asks L2 for the next-but-one group's entries (bulk prefetch).  x is
-// read through L2 (__ldcg): other SMs wrote it.  No pre-fill of x is needed.
+// are stored, then every warp reads the entries of its first item of the
+// next group -- they depend on no unknown -- and only then does the block
+// wait (bounded by kWaitNs).  After the wait one round of gathers finishes
+// the item.  Block 0 of each slice also asks L2 for the next-but-one group's
+// entries (bulk prefetch).  x is read through L2 (__ldcg): other SMs wrote
+// it.  No pre-fill of x is needed.
 template <typename T, int K>
 __global__ void __launch_bounds__(kBinBlock, 1)
 k_trsv_binned(BinTri<T> bt, Rhs<T> rhs, T* x, unsigned* bar, const LsmrState* S, int* err) {
@@ -1102,42 +1097,42 @@ k_trsv_binned(BinTri<T> bt, Rhs<T> rhs, T* x, unsigned* bar, const LsmrState* S,
     const int lane = threadIdx.x & 31;
     auto prefetch_group = [&](int g) {
         if (g >= bt.ngroups || threadIdx.x != 0) return;
-        const int p0 = __ldg(&bt.gpos[g]), p1 = __ldg(&bt.gpos[g + 1]);
-        const long long e0 = __ldg(&bt.ptr[p0]), e1 = __ldg(&bt.ptr[p1]);
+        const long long e0 = __ldg(&bt.gentry[g]), e1 = __ldg(&bt.gentry[g + 1]);
         const long long per = (e1 - e0 + gridDim.x - 1) / gridDim.x;
         const long long a = e0 + per * blockIdx.x, b = min(e1, a + per);
         if (a < b) {
             prefetch_l2(bt.idx + a, (size_t)(b - a) * sizeof(int32_t));
             prefetch_l2(bt.val + a, (size_t)(b - a) * sizeof(T));
         }
+        const int p0 = __ldg(&bt.gpos[g]), p1 = __ldg(&bt.gpos[g + 1]);
         const long long pp = (p1 - p0 + gridDim.x - 1) / gridDim.x;
         const long long q0 = p0 + pp * blockIdx.x, q1 = min((long long)p1, q0 + pp);
         if (q0 < q1) {
             prefetch_l2(bt.order + q0, (size_t)(q1 - q0) * sizeof(int32_t));
-            prefetch_l2(bt.ptr + q0, (size_t)(q1 - q0 + 1) * sizeof(int32_t));
             if (bt.idiag) prefetch_l2(bt.idiag + q0, (size_t)(q1 - q0) * sizeof(T));
         }
     };
     prefetch_group(0);
     prefetch_group(1);
-    // the warp's first item of group 0, prepared
     BinLane<T> L;
     int s = __ldg(&bt.gseg[0]);
     bool have = false;
     if (gw < __ldg(&bt.gitems[0])) {
         s = binned_seg(bt.seg, s, __ldg(&bt.gseg[1]), gw);
-        binned_prepare<T, K>(bt, rhs, bt.seg[s], gw - __ldg(&bt.seg[s].item0), lane, L);
+        const BinSeg sg = bt.seg[s];
+        binned_prepare<T>(bt, sg, gw - sg.item0, lane, L);
         have = true;
     }
     for (int g = 0; g < bt.ngroups; ++g) {
         const int s0 = __ldg(&bt.gseg[g]), s1 = __ldg(&bt.gseg[g + 1]);
         const int items = __ldg(&bt.gitems[g]);
         if (g > 0) {
-            // first item of this group: structure and right-hand sides while others finish
+            // first item of this group read while the other blocks finish
             have = gw < items;
             if (have) {
                 s = binned_seg(bt.seg, s0, s1, gw);
-                binned_prepare<T, K>(bt, rhs, bt.seg[s], gw - __ldg(&bt.seg[s].item0), lane, L);
+                const BinSeg sg = bt.seg[s];
+                binned_prepare<T>(bt, sg, gw - sg.item0, lane, L);
             }
             prefetch_group(g + 1);
             grid_wait(bar, (unsigned)g * gridDim.x, err);
@@ -1148,7 +1143,7 @@ k_trsv_binned(BinTri<T> bt, Rhs<T> rhs, T* x, unsigned* bar, const LsmrState* S,
             for (int k = gw + W; k < items; k += W) {
                 s = binned_seg(bt.seg, s, s1, k);
                 const BinSeg sg = bt.seg[s];
-                binned_prepare<T, K>(bt, rhs, sg, k - sg.item0, lane, L);
+                binned_prepare<T>(bt, sg, k - sg.item0, lane, L);
                 binned_finish<T, K>(bt, rhs, sg, lane, L, x);
             }
         }

@@ -68,7 +68,8 @@ static int binned_lanes(int64_t entries) {
 // The binned form of one fused system (see BinTri): within each level group
 // the rows are ordered by lanes per row, most first (ties: solve position);
 // a row's entries are its own right-hand side (-1), its right-hand-side
-// terms (-c) and its dependencies (c).
+// terms (-c) and its dependencies (c), in a slot of the segment's capacity
+// (padding: index -1, value 0).
 template <typename T>
 static void upload_binned(DevFactor<T>& D, int w, const IlupResult& F, const MergedTri& M, cudaStream_t s) {
     const std::vector<int32_t>& ord = M.lev.order;
@@ -82,50 +83,60 @@ static void upload_binned(DevFactor<T>& D, int w, const IlupResult& F, const Mer
     std::vector<int32_t> bord(ord.size());
     std::vector<BinSeg> seg;
     std::vector<int32_t> gseg(static_cast<size_t>(ng) + 1, 0), gitems(static_cast<size_t>(std::max(ng, 1)), 0),
-        gpos(static_cast<size_t>(ng) + 1, 0);
+        gpos(static_cast<size_t>(ng) + 1, 0), gentry(static_cast<size_t>(ng) + 1, 0);
+    int64_t base = 0;
     for (int g = 0; g < ng; ++g) {
         const int32_t p0 = lp[g], p1 = lp[g + 1];
         gpos[g] = p0;
         gseg[g] = static_cast<int32_t>(seg.size());
+        gentry[g] = static_cast<int32_t>(base);
         // counting sort of the group's rows by lanes (32, 16, ..., 1)
         int32_t at = p0;
         int32_t item = 0;
         for (int G = 32; G >= 1; G /= 2) {
             const int32_t s0 = at;
-            for (int32_t t = p0; t < p1; ++t)
-                if (binned_lanes(count(ord[t])) == G) bord[at++] = ord[t];
+            int64_t maxc = 0;
+            for (int32_t t = p0; t < p1; ++t) {
+                const int64_t c = count(ord[t]);
+                if (binned_lanes(c) == G) {
+                    bord[at++] = ord[t];
+                    maxc = std::max(maxc, c);
+                }
+            }
             if (at > s0) {
-                seg.push_back(BinSeg{s0, at, G, item});
+                const int64_t cap = ((maxc + G - 1) / G) * G;
+                if (base + cap * (at - s0) >= (int64_t(1) << 31))
+                    throw ApiError(RLSQ_ERR_SHAPE, "binned solve: more than 2^31 - 1 entries");
+                seg.push_back(BinSeg{s0, at, G, item, static_cast<int32_t>(cap), static_cast<int32_t>(base)});
                 item += (at - s0 + (32 / G) - 1) / (32 / G);
+                base += cap * (at - s0);
             }
         }
         gitems[g] = item;
     }
     gseg[ng] = static_cast<int32_t>(seg.size());
     gpos[ng] = static_cast<int32_t>(n);
-    std::vector<int32_t> bp(static_cast<size_t>(n) + 1, 0);
-    for (int64_t t = 0; t < n; ++t) bp[t + 1] = bp[t] + static_cast<int32_t>(count(bord[t]));
-    const int64_t ne = bp[n];
-    if (ne >= (int64_t(1) << 31)) throw ApiError(RLSQ_ERR_SHAPE, "binned solve: more than 2^31 - 1 entries");
-    std::vector<int32_t> bi(static_cast<size_t>(std::max<int64_t>(ne, 1)));
-    std::vector<T> bv(bi.size());
+    gentry[ng] = static_cast<int32_t>(base);
+    std::vector<int32_t> bi(static_cast<size_t>(std::max<int64_t>(base, 1)), -1);
+    std::vector<T> bv(bi.size(), (T)0);
     const int32_t flag = static_cast<int32_t>(0x80000000u);
-    for (int64_t t = 0; t < n; ++t) {
-        const int32_t r = bord[t];
-        int64_t e = bp[t];
-        bi[e] = r | flag;
-        bv[e++] = (T)-1.0;
-        if (fused)
-            for (int64_t q = M.R.ptr[r]; q < M.R.ptr[r + 1]; ++q) {
-                bi[e] = M.R.idx[q] | flag;
-                bv[e++] = (T)(-M.R.val[q]);
+    for (const BinSeg& sg : seg) {
+        for (int32_t t = sg.p0; t < sg.p1; ++t) {
+            const int32_t r = bord[t];
+            int64_t e = sg.base + static_cast<int64_t>(t - sg.p0) * sg.cap;
+            bi[e] = r | flag;
+            bv[e++] = (T)-1.0;
+            if (fused)
+                for (int64_t q = M.R.ptr[r]; q < M.R.ptr[r + 1]; ++q) {
+                    bi[e] = M.R.idx[q] | flag;
+                    bv[e++] = (T)(-M.R.val[q]);
+                }
+            for (int64_t q = M.T.ptr[r]; q < M.T.ptr[r + 1]; ++q) {
+                bi[e] = M.T.idx[q];
+                bv[e++] = (T)M.T.val[q];
             }
-        for (int64_t q = M.T.ptr[r]; q < M.T.ptr[r + 1]; ++q) {
-            bi[e] = M.T.idx[q];
-            bv[e++] = (T)M.T.val[q];
         }
     }
-    D.bptr[w].upload(bp.data(), bp.size(), s);
     D.bidx[w].upload(bi.data(), bi.size(), s);
     D.bval[w].upload(bv.data(), bv.size(), s);
     D.border[w].upload(bord.data(), bord.size(), s);
@@ -139,8 +150,9 @@ static void upload_binned(DevFactor<T>& D, int w, const IlupResult& F, const Mer
     D.bgseg[w].upload(gseg.data(), gseg.size(), s);
     D.bgitems[w].upload(gitems.data(), gitems.size(), s);
     D.bgpos[w].upload(gpos.data(), gpos.size(), s);
+    D.bgentry[w].upload(gentry.data(), gentry.size(), s);
     D.bngroups[w] = ng;
-    D.bentries[w] = ne;
+    D.bentries[w] = base;
     // the host vectors die at return
     RLSQ_CUDA(cudaStreamSynchronize(s));
 }
