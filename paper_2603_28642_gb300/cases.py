@@ -5,6 +5,7 @@ Each case builds the 2M x 1M workload recipe (scaled by --scale), factors it
 part worth capturing inside an NVTX range named `timed`:
 
     python -m paper_2603_28642_gb300.cases trsv --system U --schedule coop --scale 0.25
+    python -m paper_2603_28642_gb300.cases trsv --system L1 --schedule binned --merge 0 --scale 0.5
     python -m paper_2603_28642_gb300.cases trsv --system L1 --schedule auto --merge 0 --autotune --scale 1
     python -m paper_2603_28642_gb300.cases iteration --scale 0.75
 
@@ -28,7 +29,7 @@ from . import synth
 
 SYSTEMS = {"L1": B.SYS_L1, "L1t": B.SYS_L1T, "U": B.SYS_U, "Ut": B.SYS_UT}
 SCHEDULES = {"auto": B.TRSV_AUTO, "level": B.TRSV_LEVEL, "syncfree": B.TRSV_SYNCFREE, "coop": B.TRSV_COOP,
-             "wave": B.TRSV_WAVE}
+             "wave": B.TRSV_WAVE, "binned": B.TRSV_BINNED}
 FACTOR = dict(p=10, tau=1e-2, mu=1.0, correction=B.CORR_CG, cg_steps=2)
 
 

@@ -945,8 +945,8 @@ __device__ __forceinline__ void solve_row_csr(const Tri<T>& tri, const Rhs<T>& r
 // val = -1, a fused right-hand-side term c with val = -c), and idx = -1 is
 // padding.  The whole row is one dot product whose gathers can all be in
 // flight together.  A segment is a run of rows of one group that all take G
-// lanes each; each of its rows owns a slot of `cap` entries (the segment's
-// longest row, rounded up to a multiple of G) at base + (t - p0) * cap, so a
+// lanes each and round up to the same slot size `cap` (a multiple of G);
+// each of its rows owns the slot at base + (t - p0) * cap, so a
 // row's entries need no row-pointer lookup and lane `sub` reads entries
 // sub, sub + G, ... (coalesced across the warp).  The warps of the grid deal
 // the segment's work items (32 / G rows each) among themselves.
@@ -1068,10 +1068,16 @@ __device__ __forceinline__ void binned_finish(const BinTri<T>& bt, const Rhs<T>&
     if (L.t >= 0 && sub == 0) x[L.row] = (-sum) * L.dg;
 }
 
-// Finds the segment of work item k of a group (segments in item order).
+// Finds the segment of work item k of a group: the last segment in
+// [s, s1) whose first item is <= k (segments in item order; seg[s].item0 <= k).
 __device__ __forceinline__ int binned_seg(const BinSeg* seg, int s, int s1, int k) {
-    while (s + 1 < s1 && __ldg(&seg[s + 1].item0) <= k) ++s;
-    return s;
+    int lo = s, hi = s1 - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&seg[mid].item0) <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 constexpr int kBinBlock = 1024;

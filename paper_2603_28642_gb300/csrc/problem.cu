@@ -66,10 +66,10 @@ static int binned_lanes(int64_t entries) {
 }
 
 // The binned form of one fused system (see BinTri): within each level group
-// the rows are ordered by lanes per row, most first (ties: solve position);
-// a row's entries are its own right-hand side (-1), its right-hand-side
-// terms (-c) and its dependencies (c), in a slot of the segment's capacity
-// (padding: index -1, value 0).
+// the rows are ordered by lanes per row and slot size, most first (ties:
+// solve position); a row's entries are its own right-hand side (-1), its
+// right-hand-side terms (-c) and its dependencies (c), in a slot of the
+// segment's size (padding: index -1, value 0).
 template <typename T>
 static void upload_binned(DevFactor<T>& D, int w, const IlupResult& F, const MergedTri& M, cudaStream_t s) {
     const std::vector<int32_t>& ord = M.lev.order;
@@ -90,27 +90,36 @@ static void upload_binned(DevFactor<T>& D, int w, const IlupResult& F, const Mer
         gpos[g] = p0;
         gseg[g] = static_cast<int32_t>(seg.size());
         gentry[g] = static_cast<int32_t>(base);
-        // counting sort of the group's rows by lanes (32, 16, ..., 1)
-        int32_t at = p0;
+        // rows ordered by lanes (32, 16, ..., 1), then by slot size (the entry
+        // count rounded up to the lanes; most first), then by solve position;
+        // every (lanes, slot size) run is one segment, so a slot pads its row
+        // by fewer than G entries
+        std::vector<std::pair<int64_t, int32_t>> key;
+        key.reserve(static_cast<size_t>(p1 - p0));
+        for (int32_t t = p0; t < p1; ++t) {
+            const int64_t c = count(ord[t]);
+            const int G = binned_lanes(c);
+            const int64_t cap = ((c + G - 1) / G) * G;
+            key.emplace_back((static_cast<int64_t>(G) << 40) | cap, t);
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<int64_t, int32_t>& a, const std::pair<int64_t, int32_t>& b) {
+                             return a.first > b.first;
+                         });
         int32_t item = 0;
-        for (int G = 32; G >= 1; G /= 2) {
-            const int32_t s0 = at;
-            int64_t maxc = 0;
-            for (int32_t t = p0; t < p1; ++t) {
-                const int64_t c = count(ord[t]);
-                if (binned_lanes(c) == G) {
-                    bord[at++] = ord[t];
-                    maxc = std::max(maxc, c);
-                }
-            }
-            if (at > s0) {
-                const int64_t cap = ((maxc + G - 1) / G) * G;
-                if (base + cap * (at - s0) >= (int64_t(1) << 31))
-                    throw ApiError(RLSQ_ERR_SHAPE, "binned solve: more than 2^31 - 1 entries");
-                seg.push_back(BinSeg{s0, at, G, item, static_cast<int32_t>(cap), static_cast<int32_t>(base)});
-                item += (at - s0 + (32 / G) - 1) / (32 / G);
-                base += cap * (at - s0);
-            }
+        for (size_t q = 0; q < key.size();) {
+            size_t r = q;
+            while (r < key.size() && key[r].first == key[q].first) ++r;
+            const int G = static_cast<int>(key[q].first >> 40);
+            const int64_t cap = key[q].first & ((int64_t(1) << 40) - 1);
+            const int32_t s0 = p0 + static_cast<int32_t>(q), s1 = p0 + static_cast<int32_t>(r);
+            for (size_t u = q; u < r; ++u) bord[p0 + u] = ord[key[u].second];
+            if (base + cap * (s1 - s0) >= (int64_t(1) << 31))
+                throw ApiError(RLSQ_ERR_SHAPE, "binned solve: more than 2^31 - 1 entries");
+            seg.push_back(BinSeg{s0, s1, G, item, static_cast<int32_t>(cap), static_cast<int32_t>(base)});
+            item += (s1 - s0 + (32 / G) - 1) / (32 / G);
+            base += cap * (s1 - s0);
+            q = r;
         }
         gitems[g] = item;
     }
