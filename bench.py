@@ -470,8 +470,11 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # the other forms: sparse-dense, batched, served
 # ---------------------------------------------------------------------------
-def factor_all(problems, threads=None, **kw):
-    """Creates and factors problems concurrently (the host set-up releases the GIL)."""
+def factor_all(problems, threads=None, tune=True, **kw):
+    """Creates and factors problems concurrently (the host set-up releases the
+    GIL); then, one problem at a time so that the timings do not disturb each
+    other, tunes each problem's own product lanes (autotune = 2; the host
+    factor is reused), which is what its slot in a batch runs with."""
     from concurrent.futures import ThreadPoolExecutor
 
     from paper_2603_28642_gb300 import binding as B
@@ -483,7 +486,11 @@ def factor_all(problems, threads=None, **kw):
         return P
 
     with ThreadPoolExecutor(threads or host_threads()) as ex:
-        return list(ex.map(one, problems))
+        hs = list(ex.map(one, problems))
+    if tune:
+        for P in hs:
+            P.factor(**{"host_threads": 1, **kw}, autotune=2)
+    return hs
 
 
 def measure_sparse_dense(scale=1.0):
@@ -514,7 +521,8 @@ def measure_sparse_dense(scale=1.0):
 def measure_batched(count=512, first=None, sample=16, rank=0, world=1, dist=None):
     """Batched form: the first `first` problems of the 512-problem recipe solved
     together (float32 apply, float64 recurrences), against the same problems
-    solved one at a time in float64 (timed on `sample` of them).  With several
+    solved one at a time in float64 (timed on `sample` of them; all of them
+    in the full `--workload batched` run).  With several
     ranks every rank solves its shard of the problems (no collective on the
     data path); the job's time is the slowest rank's and its iterations are all
     ranks' iterations."""
@@ -548,13 +556,16 @@ def measure_batched(count=512, first=None, sample=16, rank=0, world=1, dist=None
     t_one = sum_over_ranks(t_one, dist)
     its_one = sum_over_ranks(its_one, dist)
     n_one = sum_over_ranks(len(idx), dist)
-    one_total = t_one / n_one * len(every)  # all problems one at a time on one GPU
+    # all problems one at a time on one GPU: measured when every problem was
+    # timed, else the sample's mean time per problem times the count
+    one_total = t_one if int(n_one) == len(every) else t_one / n_one * len(every)
     return {
         "problems": len(every), "ranks": world, "sum_n": int(sum(p.n for p in every)),
         "sum_nnz": int(sum(p.nnz for p in every)),
         "status": code, "iterations_total": int(its), "batched_wall_s": wall,
         "aggregate_iter_per_s": its / wall,
-        "one_at_a_time_fp64_s_estimated": one_total, "one_at_a_time_sample": int(n_one),
+        "one_at_a_time_fp64_s": one_total, "one_at_a_time_timed": int(n_one),
+        "one_at_a_time_measured": int(n_one) == len(every),
         "one_at_a_time_iter_per_s": its_one / t_one if t_one else None,
         "speedup_time_to_tol": one_total / wall if wall else None,
         "max_ratio": worst,
@@ -639,7 +650,8 @@ def run_workload(args):
         r = measure_sparse_dense(args.scale)
         metric, value, unit = "preconditioned LSMR iterations/s (sparse-dense)", r["iter_per_s"], "iter/s"
     elif args.workload == "batched":
-        r = measure_batched(args.count or 512, rank=rank if dist is not None else 0, world=n_gpus, dist=dist)
+        r = measure_batched(args.count or 512, sample=args.count or 512, rank=rank if dist is not None else 0,
+                            world=n_gpus, dist=dist)
         metric, value, unit = "batched aggregate LSMR iterations/s", r["aggregate_iter_per_s"], "iter/s"
     else:
         r = measure_served(args.count or 64, requests=args.requests or 2000, rates=(100, 300, 1000, 3000, 5000),

@@ -115,7 +115,10 @@ typedef struct {
                               float64 buffer that forms S fits in 2 GiB, else CG */
     int32_t precision;     /* RLSQ_PREC_* */
     int32_t trsv_schedule; /* RLSQ_TRSV_* */
-    int32_t autotune;      /* 1: time candidate kernel mappings on this matrix */
+    int32_t autotune;      /* 1: time candidate kernel mappings on this matrix (lanes of the sparse
+                              products, triangular-solve schedules); 2: only the lanes of the
+                              sparse products A, A^T, L2, L2^T (all the batched and served forms
+                              use); 0: heuristics */
     int64_t dense_row_min; /* rows of A with at least this many nonzeros are kept as dense
                               rows and multiplied by a dense-row GEMV block; 0 = automatic,
                               < 0 = never */

@@ -1,9 +1,9 @@
 // Autotuner for the kernel mappings of one problem: lanes per row (G) of the
-// A / A^T products and of the L2 / L2^T products, and, for each of the four
-// triangular systems, the schedule (one launch per level vs. sync-free) and
-// G.  Each candidate is timed with CUDA events on the problem's stream
-// (median of a few runs after a warm-up) on the problem's own matrices; the
-// fastest wins.  Results are cached on the handle until the next factor.
+// A / A^T products and of the L2 / L2^T products, and (mode 1), for each of
+// the four triangular systems, the schedule and its parameters.  Each
+// candidate is timed with CUDA events on the problem's stream (median of a
+// few runs after a warm-up) on the problem's own matrices; the fastest wins.
+// Results are cached on the handle until the next factor.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -81,7 +81,7 @@ int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y) {
 int rlsq_trsv_time(rlsq_problem_s* P, int which, float* ms);
 
 template <typename T>
-static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
+static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F, bool schedules) {
     const int n = static_cast<int>(P->n);
     // inputs: any finite vectors will do for timing
     std::vector<T> ones(static_cast<size_t>(std::max<int64_t>(P->m, 1)), (T)1);
@@ -92,6 +92,7 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F) {
         P->map.G_L2 = best_mv_lanes<T>(P, F.L2.view(), F.vn[3].p, F.vm[1].p);
         P->map.G_L2t = best_mv_lanes<T>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p);
     }
+    if (!schedules) return;
     static const int cands[] = {1, 2, 4, 8, 16, 32};
     const bool log = std::getenv("RLSQ_TUNE_LOG") != nullptr;
     for (int w = 0; w < 4; ++w) {
@@ -186,11 +187,13 @@ static void tune_products(rlsq_problem_s* P) {
     }
 }
 
-void autotune(rlsq_problem_s* P) {
+// mode 1: every mapping; mode 2: the lanes of the sparse products only (A,
+// A^T, L2, L2^T), which is all the batched and served forms use.
+void autotune(rlsq_problem_s* P, int mode) {
     tune_products(P);
     if (!P->factored) return;
-    if (P->precision == RLSQ_PREC_FP32) tune_factor<float>(P, P->f32);
-    else tune_factor<double>(P, P->f64);
+    if (P->precision == RLSQ_PREC_FP32) tune_factor<float>(P, P->f32, mode == 1);
+    else tune_factor<double>(P, P->f64, mode == 1);
 }
 
 }  // namespace rlsq

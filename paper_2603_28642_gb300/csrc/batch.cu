@@ -28,6 +28,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <type_traits>
 #include <unordered_map>
 
 #include "common.h"
@@ -35,9 +36,25 @@
 namespace rlsq {
 namespace {
 
-// lanes per row in batched mode: fixed, so a slot's arithmetic does not
-// depend on the batch it runs in
-constexpr int kBG_A = 4, kBG_At = 4, kBG_L2 = 2, kBG_L2t = 2;
+// Lanes per row of a slot's products (A, A^T, L2, L2^T) come from its own
+// problem's mapping (the heuristic of rlsq_factor, or its autotuner when the
+// problem was factored with autotune != 0), so a slot's arithmetic depends on
+// its problem only, never on the batch it runs in.  Launch grids are sized
+// for the widest mapping (kBG_Max lanes); blocks a slot does not own return.
+constexpr int kBG_Max = 32;
+
+// dispatch on a slot's lanes per row (1 .. 32), uniform per block
+template <class F>
+__device__ __forceinline__ void with_slot_lanes(int g, F&& f) {
+    switch (g) {
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 16: f(std::integral_constant<int, 16>{}); break;
+        default: f(std::integral_constant<int, 32>{}); break;
+    }
+}
 
 enum Cond { C_ALL = 0, C_CORR = 1, C_NOCORR = 2, C_CG = 3, C_E = 4, C_DENSE = 5 };
 constexpr int SEL_W = 100;  // "w of the correction": vm[0] for S^ = I, vm[3] otherwise
@@ -45,6 +62,7 @@ constexpr int SEL_W = 100;  // "w of the correction": vm[0] for S^ = I, vm[3] ot
 template <typename T>
 struct BSlot {
     int32_t m, n, m2, corr, cg_steps;
+    int32_t gA, gAt, gL2, gL2t;  // lanes per row of the A, A^T, L2, L2^T products
     int32_t nlev[4];
     Csr<double> A, At;
     Tri<T> tri[4];
@@ -139,78 +157,82 @@ __global__ void __launch_bounds__(kBlock) kb_start(const BSlot<T>* slots, const 
 template <typename T>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 kb_spmv(const BSlot<T>* slots, const int32_t* phase, int cap) {
-    constexpr int G = kBG_A;
     const BSlot<T>* D = gate(slots, phase, 2, C_ALL);
     if (!D) return;
-    const int own = own_blocks(D->m, G, cap);
-    if ((int)blockIdx.x >= own) return;
-    LsmrState* S = D->S;
-    const double inv_alpha = S->inv_alpha, alpha = S->alpha, inv_beta = S->inv_beta;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (own * kBlock) / G;
-    double acc[2] = {0.0, 0.0};
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->m; row += groups) {
-        double s1 = 0.0, s2 = 0.0;
-        row_dot_pair<G>(D->A, row, lane, D->tx, s1, s2);
-        s1 = group_sum<G>(s1, mask);
-        s2 = group_sum<G>(s2, mask);
-        if (lane == 0) {
-            const double2 old = D->qr[row];
-            const double qn = s1 * inv_alpha - alpha * (old.x * inv_beta);
-            const double rr = D->b[row] - s2;
-            D->qr[row] = make_double2(qn, rr);
-            acc[0] += qn * qn;
-            acc[1] += rr * rr;
+    with_slot_lanes(D->gA, [&](auto gc) {
+        constexpr int G = decltype(gc)::value;
+        const int own = own_blocks(D->m, G, cap);
+        if ((int)blockIdx.x >= own) return;
+        LsmrState* S = D->S;
+        const double inv_alpha = S->inv_alpha, alpha = S->alpha, inv_beta = S->inv_beta;
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (own * kBlock) / G;
+        double acc[2] = {0.0, 0.0};
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->m; row += groups) {
+            double s1 = 0.0, s2 = 0.0;
+            row_dot_pair<G>(D->A, row, lane, D->tx, s1, s2);
+            s1 = group_sum<G>(s1, mask);
+            s2 = group_sum<G>(s2, mask);
+            if (lane == 0) {
+                const double2 old = D->qr[row];
+                const double qn = s1 * inv_alpha - alpha * (old.x * inv_beta);
+                const double rr = D->b[row] - s2;
+                D->qr[row] = make_double2(qn, rr);
+                acc[0] += qn * qn;
+                acc[1] += rr * rr;
+            }
         }
-    }
-    double tot[2];
-    if (last_block_total_ctx<2>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0) {
-        const double beta = sqrt(tot[0]);
-        S->beta = beta;
-        S->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
-        S->rnorm = sqrt(tot[1]);
-    }
+        double tot[2];
+        if (last_block_total_ctx<2>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0) {
+            const double beta = sqrt(tot[0]);
+            S->beta = beta;
+            S->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+            S->rnorm = sqrt(tot[1]);
+        }
+    });
 }
 
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock, kMinBlocks)
 kb_spmvt(const BSlot<T>* slots, const int32_t* phase, int cap) {
-    constexpr int G = kBG_At;
     const BSlot<T>* D = gate(slots, phase, FIRST ? 1 : 2, C_ALL);
     if (!D) return;
-    const int own = own_blocks(D->n, G, cap);
-    if ((int)blockIdx.x >= own) return;
-    LsmrState* S = D->S;
-    const double inv_alpha = S->inv_alpha, beta = S->beta, inv_beta = S->inv_beta;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (own * kBlock) / G;
-    double acc[1] = {0.0};
-    for (int col = (blockIdx.x * kBlock + threadIdx.x) / G; col < D->n; col += groups) {
-        double s1 = 0.0, s2 = 0.0;
-        row_dot_pair<G>(D->At, col, lane, D->qr, s1, s2);
-        s1 = group_sum<G>(s1, mask);
-        s2 = group_sum<G>(s2, mask);
-        if (lane == 0) {
-            D->s[col] = FIRST ? s1 * inv_beta : s1 * inv_beta - beta * (D->s[col] * inv_alpha);
-            acc[0] += s2 * s2;
+    with_slot_lanes(D->gAt, [&](auto gc) {
+        constexpr int G = decltype(gc)::value;
+        const int own = own_blocks(D->n, G, cap);
+        if ((int)blockIdx.x >= own) return;
+        LsmrState* S = D->S;
+        const double inv_alpha = S->inv_alpha, beta = S->beta, inv_beta = S->inv_beta;
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (own * kBlock) / G;
+        double acc[1] = {0.0};
+        for (int col = (blockIdx.x * kBlock + threadIdx.x) / G; col < D->n; col += groups) {
+            double s1 = 0.0, s2 = 0.0;
+            row_dot_pair<G>(D->At, col, lane, D->qr, s1, s2);
+            s1 = group_sum<G>(s1, mask);
+            s2 = group_sum<G>(s2, mask);
+            if (lane == 0) {
+                D->s[col] = FIRST ? s1 * inv_beta : s1 * inv_beta - beta * (D->s[col] * inv_alpha);
+                acc[0] += s2 * s2;
+            }
         }
-    }
-    double tot[1];
-    if (last_block_total_ctx<1>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0 && !FIRST) {
-        const double arn = sqrt(tot[0]);
-        S->arnorm = arn;
-        const double ratio = S->rnorm > 0.0 ? arn / (S->anorm * S->rnorm) : 0.0;
-        S->ratio = ratio;
-        if (ratio < S->atol) {
-            S->done = 1;
-            S->status = kOk;
-        } else if (S->k >= S->maxit) {
-            S->done = 1;
-            S->status = kErrMaxit;
+        double tot[1];
+        if (last_block_total_ctx<1>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0 && !FIRST) {
+            const double arn = sqrt(tot[0]);
+            S->arnorm = arn;
+            const double ratio = S->rnorm > 0.0 ? arn / (S->anorm * S->rnorm) : 0.0;
+            S->ratio = ratio;
+            if (ratio < S->atol) {
+                S->done = 1;
+                S->status = kOk;
+            } else if (S->k >= S->maxit) {
+                S->done = 1;
+                S->status = kErrMaxit;
+            }
         }
-    }
+    });
 }
 
 // slot s if it takes part (phase, not done, condition), else nullptr
@@ -346,13 +368,13 @@ kb_csr_mv(const BSlot<T>* slots, const int32_t* phase, int want, int cond, int m
     const BSlot<T>* D = gate(slots, phase, want, cond);
     if (!D) return;
     const Csr<T>& M = mat == 0 ? D->L2 : D->L2t;
-    const int G = mat == 0 ? kBG_L2 : kBG_L2t;
+    const int G = mat == 0 ? D->gL2 : D->gL2t;
     const int own = own_blocks(M.rows, G, cap);
     if ((int)blockIdx.x >= own) return;
     const T* x = vsel(*D, in_sel);
     T* y = vsel(*D, out_sel);
     const int lane = threadIdx.x & (G - 1);
-    const unsigned mask = (G == 2) ? (3u << ((threadIdx.x & 31u) & ~1u)) : 0xfu << ((threadIdx.x & 31u) & ~3u);
+    const unsigned mask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(G - 1));
     const int groups = (own * kBlock) / G;
     for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < M.rows; row += groups) {
         T s = (T)0;
@@ -365,96 +387,102 @@ kb_csr_mv(const BSlot<T>* slots, const int32_t* phase, int want, int cond, int m
 // e = L2 q1 -> r (vm0), rr = <e, e>
 template <typename T>
 __global__ void __launch_bounds__(kBlock) kb_l2_start(const BSlot<T>* slots, const int32_t* phase, int want, int cap) {
-    constexpr int G = kBG_L2;
     const BSlot<T>* D = gate(slots, phase, want, C_CG);
     if (!D) return;
-    const int own = own_blocks(D->m2, G, cap);
-    if ((int)blockIdx.x >= own) return;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (own * kBlock) / G;
-    const T* q1 = D->vn[2];
-    T* r = D->vm[0];
-    double acc[1] = {0.0};
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->m2; row += groups) {
-        T s = (T)0;
-        row_dot<G>(D->L2, row, lane, q1, s);
-        s = group_sum<G>(s, mask);
-        if (lane == 0) {
-            r[row] = s;
-            acc[0] += (double)(s * s);
+    with_slot_lanes(D->gL2, [&](auto gc) {
+        constexpr int G = decltype(gc)::value;
+        const int own = own_blocks(D->m2, G, cap);
+        if ((int)blockIdx.x >= own) return;
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (own * kBlock) / G;
+        const T* q1 = D->vn[2];
+        T* r = D->vm[0];
+        double acc[1] = {0.0};
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->m2; row += groups) {
+            T s = (T)0;
+            row_dot<G>(D->L2, row, lane, q1, s);
+            s = group_sum<G>(s, mask);
+            if (lane == 0) {
+                r[row] = s;
+                acc[0] += (double)(s * s);
+            }
         }
-    }
-    double tot[1];
-    if (last_block_total_ctx<1>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0) {
-        D->S->cg_rr = tot[0];
-        D->S->cg_beta = 0.0;
-    }
+        double tot[1];
+        if (last_block_total_ctx<1>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0) {
+            D->S->cg_rr = tot[0];
+            D->S->cg_beta = 0.0;
+        }
+    });
 }
 
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
 kb_l2t_cg(const BSlot<T>* slots, const int32_t* phase, int want, int it, int cap) {
-    constexpr int G = kBG_L2t;
     const BSlot<T>* D = gate(slots, phase, want, C_CG);
     if (!D || it >= D->cg_steps) return;
-    const int own = own_blocks(D->n, G, cap);
-    if ((int)blockIdx.x >= own) return;
-    const T beta = (T)D->S->cg_beta;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (own * kBlock) / G;
-    const T* r = D->vm[0];
-    const T* p = D->vm[1];
-    T* c1 = D->vn[3];
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->n; row += groups) {
-        T s = (T)0;
-        const int e1 = D->L2t.ptr[row + 1];
-        for (int e = D->L2t.ptr[row] + lane; e < e1; e += G) {
-            const int j = D->L2t.idx[e];
-            const T pj = FIRST ? r[j] : r[j] + beta * p[j];
-            s += D->L2t.val[e] * pj;
+    with_slot_lanes(D->gL2t, [&](auto gc) {
+        constexpr int G = decltype(gc)::value;
+        const int own = own_blocks(D->n, G, cap);
+        if ((int)blockIdx.x >= own) return;
+        const T beta = (T)D->S->cg_beta;
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (own * kBlock) / G;
+        const T* r = D->vm[0];
+        const T* p = D->vm[1];
+        T* c1 = D->vn[3];
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->n; row += groups) {
+            T s = (T)0;
+            const int e1 = D->L2t.ptr[row + 1];
+            for (int e = D->L2t.ptr[row] + lane; e < e1; e += G) {
+                const int j = D->L2t.idx[e];
+                const T pj = FIRST ? r[j] : r[j] + beta * p[j];
+                s += D->L2t.val[e] * pj;
+            }
+            s = group_sum<G>(s, mask);
+            if (lane == 0) c1[row] = s;
         }
-        s = group_sum<G>(s, mask);
-        if (lane == 0) c1[row] = s;
-    }
+    });
 }
 
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
 kb_l2_sp(const BSlot<T>* slots, const int32_t* phase, int want, int it, int cap) {
-    constexpr int G = kBG_L2;
     const BSlot<T>* D = gate(slots, phase, want, C_CG);
     if (!D || it >= D->cg_steps) return;
-    const int own = own_blocks(D->m2, G, cap);
-    if ((int)blockIdx.x >= own) return;
-    LsmrState* S = D->S;
-    const T beta = (T)S->cg_beta;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (own * kBlock) / G;
-    const T* c3 = D->vn[2];
-    const T* r = D->vm[0];
-    T* p = D->vm[1];
-    T* sp = D->vm[2];
-    double acc[1] = {0.0};
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->m2; row += groups) {
-        T s = (T)0;
-        row_dot<G>(D->L2, row, lane, c3, s);
-        s = group_sum<G>(s, mask);
-        if (lane == 0) {
-            const T pv = FIRST ? r[row] : r[row] + beta * p[row];
-            const T spv = pv + s;
-            p[row] = pv;
-            sp[row] = spv;
-            acc[0] += (double)(pv * spv);
+    with_slot_lanes(D->gL2, [&](auto gc) {
+        constexpr int G = decltype(gc)::value;
+        const int own = own_blocks(D->m2, G, cap);
+        if ((int)blockIdx.x >= own) return;
+        LsmrState* S = D->S;
+        const T beta = (T)S->cg_beta;
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (own * kBlock) / G;
+        const T* c3 = D->vn[2];
+        const T* r = D->vm[0];
+        T* p = D->vm[1];
+        T* sp = D->vm[2];
+        double acc[1] = {0.0};
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < D->m2; row += groups) {
+            T s = (T)0;
+            row_dot<G>(D->L2, row, lane, c3, s);
+            s = group_sum<G>(s, mask);
+            if (lane == 0) {
+                const T pv = FIRST ? r[row] : r[row] + beta * p[row];
+                const T spv = pv + s;
+                p[row] = pv;
+                sp[row] = spv;
+                acc[0] += (double)(pv * spv);
+            }
         }
-    }
-    double tot[1];
-    if (last_block_total_ctx<1>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0) {
-        const double rr = S->cg_rr;
-        S->cg_a = (rr != 0.0 && tot[0] != 0.0) ? rr / tot[0] : 0.0;
-    }
+        double tot[1];
+        if (last_block_total_ctx<1>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0) {
+            const double rr = S->cg_rr;
+            S->cg_a = (rr != 0.0 && tot[0] != 0.0) ? rr / tot[0] : 0.0;
+        }
+    });
 }
 
 template <typename T, bool FIRST>
@@ -704,6 +732,10 @@ struct Engine {
         D.m2 = static_cast<int32_t>(P->m - P->n);
         D.corr = P->correction;
         D.cg_steps = P->opts.cg_steps;
+        D.gA = P->map.G_A;
+        D.gAt = P->map.G_At;
+        D.gL2 = P->map.G_L2;
+        D.gL2t = P->map.G_L2t;
         for (int w = 0; w < 4; ++w) {
             D.nlev[w] = static_cast<int32_t>(F.level_ptr[w].size()) - 1;
             D.tri[w] = F.tview(w);
@@ -788,29 +820,29 @@ struct Engine {
         if (any_corr) {
             trsv(want, C_CORR, 0, RHS_VEC, 1, 0, 2);  // L1^{-1} -> vn2
             if (any_cg) {
-                kb_l2_start<T><<<dim3(gx(max_m2, kBG_L2), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, cap);
+                kb_l2_start<T><<<dim3(gx(max_m2, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, cap);
                 for (int it = 0; it < maxcg; ++it) {
                     if (it == 0)
-                        kb_l2t_cg<T, true><<<dim3(gx(max_n, kBG_L2t), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
+                        kb_l2t_cg<T, true><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                     else
-                        kb_l2t_cg<T, false><<<dim3(gx(max_n, kBG_L2t), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
+                        kb_l2t_cg<T, false><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                     trsv(want, C_CG, 1, RHS_VEC, 3, 0, 4);
                     trsv(want, C_CG, 0, RHS_VEC, 4, 0, 2);
                     if (it == 0) {
-                        kb_l2_sp<T, true><<<dim3(gx(max_m2, kBG_L2), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
+                        kb_l2_sp<T, true><<<dim3(gx(max_m2, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                         kb_cg_update<T, true><<<dim3(gx(max_m2, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                     } else {
-                        kb_l2_sp<T, false><<<dim3(gx(max_m2, kBG_L2), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
+                        kb_l2_sp<T, false><<<dim3(gx(max_m2, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                         kb_cg_update<T, false><<<dim3(gx(max_m2, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                     }
                 }
             }
             if (any_e) {
-                kb_csr_mv<T><<<dim3(gx(max_m2, kBG_L2), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, C_E, 0, 2, -1, cap);
+                kb_csr_mv<T><<<dim3(gx(max_m2, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, C_E, 0, 2, -1, cap);
                 if (any_dense)
                     kb_dense_gemv<T><<<dim3(gx(max_m2, 32), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want);
             }
-            kb_csr_mv<T><<<dim3(gx(max_n, kBG_L2t), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, C_CORR, 1, SEL_W, 3, cap);
+            kb_csr_mv<T><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, C_CORR, 1, SEL_W, 3, cap);
             trsv(want, C_CORR, 1, RHS_VEC, 3, 0, 4);  // L1^{-T} Y^T w -> vn4
             trsv(want, C_CORR, 0, RHS_SUB, 1, 4, 0);  // L1^{-1}(g2 - .) -> vn0
         }
@@ -821,7 +853,7 @@ struct Engine {
     void enqueue_start() {
         const unsigned ns = static_cast<unsigned>(nslots);
         kb_start<T><<<dim3(gx(max_m, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
-        kb_spmvt<T, true><<<dim3(gx(max_n, kBG_At), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmvt<T, true><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
         apply(1);
         kb_finish<T, true><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
         kb_update<T, true><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
@@ -830,8 +862,8 @@ struct Engine {
 
     void enqueue_iteration() {
         const unsigned ns = static_cast<unsigned>(nslots);
-        kb_spmv<T><<<dim3(gx(max_m, kBG_A), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
-        kb_spmvt<T, false><<<dim3(gx(max_n, kBG_At), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmv<T><<<dim3(gx(max_m, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmvt<T, false><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
         apply(2);
         kb_finish<T, false><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
         kb_update<T, false><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
@@ -842,9 +874,9 @@ struct Engine {
     void enqueue_tick() {
         const unsigned ns = static_cast<unsigned>(nslots);
         kb_start<T><<<dim3(gx(max_m, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
-        kb_spmv<T><<<dim3(gx(max_m, kBG_A), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
-        kb_spmvt<T, true><<<dim3(gx(max_n, kBG_At), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
-        kb_spmvt<T, false><<<dim3(gx(max_n, kBG_At), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmv<T><<<dim3(gx(max_m, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmvt<T, true><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
+        kb_spmvt<T, false><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
         apply(kPhaseActive);
         kb_finish<T, true><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);
         kb_finish<T, false><<<dim3(gx(max_n, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, cap);

@@ -1060,7 +1060,7 @@ void default_mapping(rlsq_problem_s* P) {
     }
 }
 
-void autotune(rlsq_problem_s* P);  // autotune.cu
+void autotune(rlsq_problem_s* P, int mode);  // autotune.cu
 
 // Times one standalone solve of system `which` with the current mapping
 // (used by the autotuner); inputs in vn[3], output in vn[4].
@@ -1386,7 +1386,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
             if (opts.trsv_rows > 0) h->map.G_tri[w] = std::min(h->map.G_tri[w], 8);
         }
         h->factored = true;
-        if (opts.autotune) autotune(h);
+        if (opts.autotune) autotune(h, opts.autotune == 2 ? 2 : 1);
         h->factor_seconds =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         return RLSQ_OK;

@@ -2,7 +2,7 @@
  * matrix and a right-hand side, then, through the C ABI alone,
  *   - rlsq_create + rlsq_factor (ILUP(10, 1e-2), mu = 1, CG(2) correction),
  *   - rlsq_solve (preconditioned LSMR to ||A^T r|| / (||A|| ||r||) < 1e-8),
- *   - rlsq_batch_solve of the same problem twice (b and 2 b),
+ *   - rlsq_batch_solve of two handles of the same matrix (b and 2 b),
  *   - a server: rlsq_server_create / register / submit / poll / get_stats /
  *     destroy, one request,
  * and prints each x in C99 hexadecimal with its status and iteration count.
@@ -69,11 +69,15 @@ int main(int argc, char **argv) {
     check(rlsq_solve(P, b, x, &so, &info), "rlsq_solve");
     print_x("solve", x, n, &info);
 
-    /* the same problem twice in one batch, with b and 2 b */
+    /* two handles of the same matrix in one batch (a handle holds its own
+       Krylov state, so it may appear once), with b and 2 b */
+    rlsq_problem P2 = NULL;
+    check(rlsq_create(m, n, rowptr, colidx, vals, RLSQ_HOST_PTRS, NULL, &P2), "rlsq_create");
+    check(rlsq_factor(P2, &fo), "rlsq_factor");
     double *b2 = malloc(sizeof(double) * (size_t)m);
     for (int64_t i = 0; i < m; ++i) b2[i] = 2.0 * b[i];
     double *x0 = malloc(sizeof(double) * (size_t)n), *x1 = malloc(sizeof(double) * (size_t)n);
-    rlsq_problem hs[2] = {P, P};
+    rlsq_problem hs[2] = {P, P2};
     const double *bs[2] = {b, b2};
     double *xs[2] = {x0, x1};
     rlsq_info infos[2];
@@ -111,6 +115,7 @@ int main(int argc, char **argv) {
     check(rlsq_create(m, n, rowptr, colidx, vals, RLSQ_HOST_PTRS, NULL, &Q), "rlsq_create");
     printf("unfactored %d\n", rlsq_solve(Q, b, x, &so, NULL));
     rlsq_destroy(Q);
+    rlsq_destroy(P2);
     rlsq_destroy(P);
     free(x);
     free(b2);

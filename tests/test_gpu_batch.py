@@ -1,8 +1,9 @@
 """Batched and served forms on the GPU.
 
 * rlsq_batch_solve: each problem of an uneven batch (sizes, nonzeros per row,
-  correction modes) matches the CPU oracle (x within 1e-6 relative, equal
-  iteration counts), and gives exactly the same bits alone and in the mix.
+  correction modes, lanes per row of its products chosen per problem)
+  matches the CPU oracle (x within 1e-6 relative, equal iteration counts),
+  and gives exactly the same bits alone and in the mix.
 * server: requests over shared resident matrices give exactly the bits of
   the same solve done alone, complete under a memory budget that admits one
   request at a time, and overlap on the device (continuous batching).
@@ -69,6 +70,34 @@ def test_batch_alone_equals_in_mix(batch):
     # a different mix (reversed order, subset) gives the same bits too
     sub = [4, 1, 2]
     xr, ir, _ = B.batch_solve([handles[k] for k in sub], [probs[k].b for k in sub])
+    for j, k in enumerate(sub):
+        assert np.array_equal(xr[j], xs[k])
+
+
+def test_batch_tuned_lanes_alone_equals_in_mix():
+    """Slots whose problems were autotuned (autotune = 2: lanes of the A, A^T,
+    L2, L2^T products, chosen per problem) run with their own lanes in the
+    batch: oracle parity, and the same bits alone and in any mix."""
+    # the last problem has 12 entries per row (wider lanes) and a strong diagonal (fast convergence)
+    probs = uneven_problems(count=5, seed=71) + [synth.sparse_problem(3000, 1500, 12, seed=72, diag_value=8.0)]
+    hs = []
+    for k, p in enumerate(probs):
+        P = B.Problem.from_problem(p)
+        P.factor(mu=MU, correction=B.CORR_CG, autotune=2 if k % 2 == 0 else 0)
+        hs.append(P)
+    xs, infos, code = B.batch_solve(hs, [p.b for p in probs])
+    assert code == 0
+    for k, (p, x, info) in enumerate(zip(probs, xs, infos)):
+        f = oracle.Factor(p.m, p.n, p.rowptr, p.colidx, p.vals, mu=MU)
+        f.set_correction(oracle.CG, 2)
+        ref = oracle.lsmr(f, p.m, p.n, p.rowptr, p.colidx, p.vals, p.b)
+        assert info["status"] == 0 and abs(info["iterations"] - ref.its) <= 1, (k, info["iterations"], ref.its)
+        assert rel(x, ref.x) <= 1e-6
+    for k in range(len(probs)):
+        xa, ia, _ = B.batch_solve([hs[k]], [probs[k].b])
+        assert np.array_equal(xa[0], xs[k]) and ia[0]["iterations"] == infos[k]["iterations"]
+    sub = [5, 2, 0]
+    xr, _, _ = B.batch_solve([hs[k] for k in sub], [probs[k].b for k in sub])
     for j, k in enumerate(sub):
         assert np.array_equal(xr[j], xs[k])
 
