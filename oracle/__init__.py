@@ -60,6 +60,9 @@ def _load():
         lib.orc_levels.argtypes = [i64, P, P, cint, P]
         lib.orc_correction.restype = cint
         lib.orc_correction.argtypes = [P, cint, cint]
+        lib.orc_cg_tolerance.argtypes = [P, dbl]
+        lib.orc_cg_last_steps.restype = cint
+        lib.orc_cg_last_steps.argtypes = [P]
         lib.orc_correction_dense.restype = cint
         lib.orc_correction_dense.argtypes = [P, P]
         for name in ("orc_apply", "orc_solve_L1", "orc_solve_L1t", "orc_solve_U",
@@ -172,11 +175,18 @@ class Factor:
         return csr, diag
 
     # --- correction and apply ---------------------------------------------
-    def set_correction(self, mode: int, cg_steps: int = 2):
+    def set_correction(self, mode: int, cg_steps: int = 2, cg_tol: float = 0.0):
+        """cg_tol > 0 (CG mode): stop the CG steps on S once ||r_j|| <= cg_tol ||r_0||,
+        at most cg_steps of them."""
         rc = _load().orc_correction(self._h, int(mode), int(cg_steps))
         if rc != 0:
             raise ValueError("dense S is not positive definite")
-        self.mode, self.cg_steps = mode, cg_steps
+        _load().orc_cg_tolerance(self._h, float(cg_tol))
+        self.mode, self.cg_steps, self.cg_tol = mode, cg_steps, cg_tol
+
+    def cg_last_steps(self) -> int:
+        """CG steps the last S solve (one apply) took."""
+        return int(_load().orc_cg_last_steps(self._h))
 
     def dense_cholesky(self):
         m2 = self.m - self.n

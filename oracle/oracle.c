@@ -23,6 +23,10 @@
  *                       (eq. 3.9): identity (S^ = I), k CG steps on the
  *                       implicit S (Sec. 3.2), or the dense S factorised by
  *                       Cholesky (Table 2 variant).
+ *   orc_cg_tolerance    the CG steps on S stopped adaptively (Sec. 3.2
+ *                       leaves their number open and Table 3 varies it):
+ *                       after the step that brings ||r_j|| to at most
+ *                       tol ||r_0||, or after k steps.
  *   orc_apply           t = M^{-1} s, with
  *                       M^{-1} = D U^{-1} L1^{-1} K L1^{-T} U^{-T} D,
  *                       K = I - Y^T S^-1 Y: Algorithm 3 (steps 1-4) applied to
@@ -208,7 +212,9 @@ typedef struct orc_factor {
     int64_t *Utp; int32_t *Uti; double *Utv;   /* its transpose (strictly lower) */
     /* correction */
     int mode;       /* 0 NONE, 1 SI, 2 CG, 3 DENSE */
-    int cg_steps;
+    int cg_steps;   /* CG: the number of steps, or their maximum when cg_tol > 0 */
+    double cg_tol;  /* CG: stop once ||r_j|| <= cg_tol ||r_0|| (0: always cg_steps steps) */
+    int cg_last;    /* CG: steps the last S solve took */
     double *G;      /* DENSE: Cholesky factor of S (row-major, lower), (m-n)^2 */
 } orc_factor;
 
@@ -677,6 +683,12 @@ int orc_correction(orc_factor *f, int mode, int cg_steps) {
     return 0;
 }
 
+/* Adaptive CG steps on S (mode 2): stop after the step that makes
+ * ||r_j||^2 <= tol^2 ||r_0||^2, at most cg_steps steps; tol = 0 restores the
+ * fixed count. */
+void orc_cg_tolerance(orc_factor *f, double tol) { f->cg_tol = tol; }
+int orc_cg_last_steps(const orc_factor *f) { return f->cg_last; }
+
 /* Export the dense Cholesky factor (row-major lower, (m-n)^2); 0 if none. */
 int orc_correction_dense(const orc_factor *f, double *out) {
     if (!f->G) return 0;
@@ -707,7 +719,8 @@ static void s_solve(const orc_factor *f, const double *e, double *w) {
         free(y);
         return;
     }
-    /* mode 2: conjugate gradients from w = 0, fixed number of steps */
+    /* mode 2: conjugate gradients from w = 0: cg_steps steps, or fewer when
+     * cg_tol > 0 and the residual has dropped to cg_tol times its start */
     double *r = (double *)xmalloc((size_t)m2 * sizeof(double));
     double *pv = (double *)xmalloc((size_t)m2 * sizeof(double));
     double *sp = (double *)xmalloc((size_t)m2 * sizeof(double));
@@ -715,6 +728,8 @@ static void s_solve(const orc_factor *f, const double *e, double *w) {
     double *wn2 = (double *)xmalloc((size_t)n * sizeof(double));
     for (int64_t i = 0; i < m2; i++) { w[i] = 0.0; r[i] = e[i]; pv[i] = e[i]; }
     double rr = dot(m2, r, r);
+    const double rr0 = rr;
+    int steps = 0;
     for (int it = 0; it < f->cg_steps; it++) {
         if (rr == 0.0) break;
         s_matvec(f, pv, sp, wn1, wn2);
@@ -724,11 +739,14 @@ static void s_solve(const orc_factor *f, const double *e, double *w) {
             w[i] = w[i] + a * pv[i];
             r[i] = r[i] - a * sp[i];
         }
+        steps = it + 1;
         double rrn = dot(m2, r, r);
+        if (f->cg_tol > 0.0 && rrn <= f->cg_tol * f->cg_tol * rr0) break;
         double bcg = rrn / rr;
         for (int64_t i = 0; i < m2; i++) pv[i] = r[i] + bcg * pv[i];
         rr = rrn;
     }
+    ((orc_factor *)f)->cg_last = steps; /* a record for the tests, not part of the arithmetic */
     free(r); free(pv); free(sp); free(wn1); free(wn2);
 }
 

@@ -319,6 +319,51 @@ def test_apply_matches_dense_definition(cfg0_factor, mode):
     assert np.dot(f.apply(a), b) == pytest.approx(np.dot(a, f.apply(b)), rel=1e-10)
 
 
+def test_cg_adaptive_steps_match_dense_cg(cfg0_factor):
+    """CG on S stopped adaptively (after the step that brings ||r_j|| to at
+    most tol ||r_0||, at most k steps): the number of steps and w equal CG
+    written on the dense S = I + Y Y^T; tol = 0 keeps k steps; a whole apply
+    with the adaptive rule equals the fixed-k apply with the steps it took."""
+    p, f = cfg0_factor
+    _, Y = _dense_minv(f, p, oracle.NONE)
+    S = np.eye(Y.shape[0]) + Y @ Y.T
+    kmax = 25
+    for tol in (0.5, 0.1, 1e-2, 1e-4, 0.0):
+        f.set_correction(oracle.CG, kmax, cg_tol=tol)
+        e = np.random.default_rng(int(1000 * tol) + 3).standard_normal(Y.shape[0])
+        w = np.zeros_like(e)
+        r = e.copy()
+        pv = e.copy()
+        rr = r @ r
+        rr0 = rr
+        steps = 0
+        for it in range(kmax):
+            sp_ = S @ pv
+            a = rr / (pv @ sp_)
+            w += a * pv
+            r -= a * sp_
+            steps = it + 1
+            rrn = r @ r
+            if tol > 0 and rrn <= tol * tol * rr0:
+                # not a borderline decision (the oracle's sums are ordered differently)
+                assert rrn < (1 - 1e-9) * tol * tol * rr0
+                break
+            pv = r + rrn / rr * pv
+            rr = rrn
+        got = f.s_solve(e)
+        assert f.cg_last_steps() == steps, (tol, f.cg_last_steps(), steps)
+        np.testing.assert_allclose(got, w, rtol=1e-9, atol=1e-11)
+        assert (tol > 0 and steps < kmax) or (tol == 0 and steps == kmax)
+    # the apply: adaptive == fixed with the same number of steps, bit for bit
+    s = np.random.default_rng(77).standard_normal(p.n)
+    f.set_correction(oracle.CG, 10, cg_tol=0.05)
+    t_adapt = f.apply(s)
+    k = f.cg_last_steps()
+    assert 1 <= k < 10
+    f.set_correction(oracle.CG, k)
+    assert np.array_equal(f.apply(s), t_adapt)
+
+
 def test_cg_mode_matches_dense_cg(cfg0_factor):
     """CG(k) on S = I + Y Y^T from zero: compare with CG written on the dense S."""
     p, f = cfg0_factor
