@@ -448,6 +448,18 @@ def run_ours(args):
             except Exception as e:  # recorded, so the headline line still prints
                 more[f"cg{k}"] = {"error": f"{type(e).__name__}: {e}"}
         out["time_to_tol"]["fp64_more_cg_steps"] = more
+        # CG steps on S stopped adaptively: once ||r_j|| <= eta ||r_0||, at most 8
+        adaptive = {}
+        for eta in (0.3, 0.1):
+            try:
+                P.factor(**{**FACTOR, "cg_steps": 8}, cg_tol=eta, precision=B.PREC_FP64, autotune=1)
+                r = P.solve(prob.b, allow_fail=True)
+                adaptive[f"eta{eta}"] = {"iterations": r.info["iterations"], "seconds": r.info["solve_seconds"],
+                                         "ratio": r.info["ratio"], "status": r.status,
+                                         "x_rel_diff_vs_cg2": float(np.linalg.norm(r.x - x64) / np.linalg.norm(x64))}
+            except Exception as e:  # recorded, so the headline line still prints
+                adaptive[f"eta{eta}"] = {"error": f"{type(e).__name__}: {e}"}
+        out["time_to_tol"]["fp64_adaptive_cg_steps"] = adaptive
     del P
     if rank == 0 and not args.no_extras:
         # the other forms, sampled so the default run stays within minutes

@@ -138,6 +138,10 @@ typedef struct {
                               rows from the ticket counter; 1, 2 or 4 = warps take chunks and
                               each group of lanes solves that many rows, loading all their
                               structure before it waits on an unknown */
+    double cg_tol;         /* RLSQ_CORR_CG: stop the CG iteration on S after the step that brings
+                              ||r_j|| to at most cg_tol ||r_0|| (cg_steps is then the largest
+                              count); 0 = always cg_steps steps.  Single-problem solves only:
+                              rlsq_batch_solve and rlsq_server_register refuse it (ARG) */
 } rlsq_factor_opts;
 
 /* Options of a solve. */

@@ -1254,6 +1254,9 @@ int rlsq_batch_solve(rlsq_problem const* hs, const double* const* bs, double* co
         for (int i = 0; i < count; ++i) {
             if (!hs[i] || !bs[i] || !xs[i]) throw ApiError(RLSQ_ERR_ARG, "null problem, b or x");
             if (!hs[i]->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "problem " + std::to_string(i) + " is not factored");
+            if (hs[i]->correction == RLSQ_CORR_CG && hs[i]->opts.cg_tol > 0.0)
+                throw ApiError(RLSQ_ERR_ARG, "problem " + std::to_string(i) +
+                                                 ": adaptive CG steps (cg_tol > 0) are for single-problem solves");
             if (hs[i]->precision != prec) throw ApiError(RLSQ_ERR_ARG, "all problems of a batch need the same precision");
             if (hs[i]->md > 0) throw ApiError(RLSQ_ERR_ARG, "batched solves take problems without dense rows");
             for (int j = 0; j < i; ++j)
@@ -1282,6 +1285,8 @@ int rlsq_server_register(rlsq_server s, rlsq_problem h, int32_t* matrix_id) {
     return guarded([&]() -> int {
         if (!s || !h || !matrix_id) throw ApiError(RLSQ_ERR_ARG, "null argument");
         if (!h->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "register a factored problem");
+        if (h->correction == RLSQ_CORR_CG && h->opts.cg_tol > 0.0)
+            throw ApiError(RLSQ_ERR_ARG, "adaptive CG steps (cg_tol > 0) are for single-problem solves");
         if (h->md > 0) throw ApiError(RLSQ_ERR_ARG, "served matrices must have no dense rows");
         const int64_t need = state_bytes(h->m, h->n, h->m - h->n, h->precision);
         if (need > s->opts.hbm_budget_bytes) throw ApiError(RLSQ_ERR_ADMISSION, "one request does not fit the budget");

@@ -34,6 +34,7 @@ struct LsmrState {
     double ts;                // <t, s>
     double sum_q, sum_r;      // partial sums carried between kernels
     double cg_rr, cg_a, cg_beta;
+    double cg_rr0;            // ||r_0||^2 of the CG iteration on S in the current apply
     int32_t k;                // index of the current iterate x_k
     int32_t maxit;
     int32_t done;
@@ -1307,7 +1308,7 @@ k_csr_mv(Csr<T> M, const T* __restrict__ x, T* __restrict__ y, const LsmrState* 
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock)
 k_l2_start(Csr<T> L2, const T* __restrict__ q1, T* __restrict__ r, LsmrState* S, double* part,
-           unsigned* counter) {
+           unsigned* counter, LsmrState* gate) {
     if (S->done) return;
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
@@ -1325,7 +1326,9 @@ k_l2_start(Csr<T> L2, const T* __restrict__ q1, T* __restrict__ r, LsmrState* S,
     double tot[1];
     if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0) {
         S->cg_rr = tot[0];
+        S->cg_rr0 = tot[0];
         S->cg_beta = 0.0;
+        if (gate) gate->done = 0;
     }
 }
 
@@ -1335,8 +1338,8 @@ k_l2_start(Csr<T> L2, const T* __restrict__ q1, T* __restrict__ r, LsmrState* S,
 template <typename T, int G, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
 k_l2t_cg(Csr<T> L2t, const T* __restrict__ r, const T* __restrict__ p, T* __restrict__ c1,
-         const LsmrState* S) {
-    if (S->done) return;
+         const LsmrState* S, const LsmrState* gate) {
+    if (S->done || (gate && gate->done)) return;
     const T beta = (T)S->cg_beta;
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
@@ -1354,8 +1357,8 @@ k_l2t_cg(Csr<T> L2t, const T* __restrict__ r, const T* __restrict__ p, T* __rest
 template <typename T, int G, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
 k_l2_sp(Csr<T> L2, const T* __restrict__ c3, const T* __restrict__ r, T* __restrict__ p,
-        T* __restrict__ sp, LsmrState* S, double* part, unsigned* counter) {
-    if (S->done) return;
+        T* __restrict__ sp, LsmrState* S, double* part, unsigned* counter, const LsmrState* gate) {
+    if (S->done || (gate && gate->done)) return;
     const T beta = (T)S->cg_beta;
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
@@ -1380,12 +1383,14 @@ k_l2_sp(Csr<T> L2, const T* __restrict__ c3, const T* __restrict__ r, T* __restr
     }
 }
 
-// w += a p (FIRST: w = a p); r -= a Sp; totals: beta = rr' / rr
+// w += a p (FIRST: w = a p); r -= a Sp; totals: beta = rr' / rr.  With a
+// gate (adaptive steps): once rr' <= tol2 rr_0 the gate is closed and the
+// kernels of the remaining CG steps return at once.
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
 k_cg_update(int m2, const T* __restrict__ p, const T* __restrict__ sp, T* __restrict__ r,
-            T* __restrict__ w, LsmrState* S, double* part, unsigned* counter) {
-    if (S->done) return;
+            T* __restrict__ w, LsmrState* S, double* part, unsigned* counter, LsmrState* gate, double tol2) {
+    if (S->done || (gate && gate->done)) return;
     const T a = (T)S->cg_a;
     double acc[1] = {0.0};
     for (int i = blockIdx.x * kBlock + threadIdx.x; i < m2; i += gridDim.x * kBlock) {
@@ -1400,6 +1405,7 @@ k_cg_update(int m2, const T* __restrict__ p, const T* __restrict__ sp, T* __rest
         const double rr = S->cg_rr;
         S->cg_beta = rr != 0.0 ? tot[0] / rr : 0.0;
         S->cg_rr = tot[0];
+        if (gate && tot[0] <= tol2 * S->cg_rr0) gate->done = 1;
     }
 }
 

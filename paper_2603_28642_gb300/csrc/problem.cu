@@ -348,10 +348,15 @@ static void coop_attributes() {
     set(k_trsv_coop<T, RHS_SCALED, 8>, 8);
 }
 
+// `gate` (optional): the state whose done word the kernels check instead of
+// S's (the CG steps' gate when their number is adaptive); errors still go to
+// S's error word.
 template <typename T>
 static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, Rhs<T> rhs, T* x,
-                        int slot, LsmrState* S, cudaStream_t st) {
+                        int slot, LsmrState* S, cudaStream_t st, const LsmrState* gate = nullptr) {
     const Tri<T> tri = F.tview(which);
+    int* const err = error_word(S);
+    const LsmrState* const G8 = gate ? gate : S;
     const int n = tri.n;
     const int G = P->map.G_tri[which];
     RecScope rs(P, RLSQ_KCLASS_TRSV_L1 + which, trsv_bytes<T>(P, which), st);
@@ -363,7 +368,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
             with_G(G, [&](auto g) {
                 with_rhs(rk, [&](auto k) {
                     k_trsv_level<T, decltype(g)::value, decltype(k)::value>
-                        <<<grid, kBlock, 0, st>>>(tri, rhs, x, lo, hi, S);
+                        <<<grid, kBlock, 0, st>>>(tri, rhs, x, lo, hi, G8);
                 });
             });
         }
@@ -382,7 +387,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
         for (int l = 0; l < lead; ++l) {
             const int grid = grid_rows(P, lp[l + 1] - lp[l], 1);
             with_rhs(rk, [&](auto k) {
-                k_trsv_level<T, 1, decltype(k)::value><<<grid, kBlock, 0, st>>>(tri, rhs, x, lp[l], lp[l + 1], S);
+                k_trsv_level<T, 1, decltype(k)::value><<<grid, kBlock, 0, st>>>(tri, rhs, x, lp[l], lp[l + 1], G8);
             });
         }
         const int nlev = nall - lead;
@@ -401,7 +406,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, F.level_ptr_d[which].p + lead, nlev,
-                                         P->barriers.p + slot, static_cast<const LsmrState*>(S), error_word(S)));
+                                         P->barriers.p + slot, G8, err));
         });
     } else if (P->map.sched[which] == RLSQ_TRSV_BINNED) {
         if (slot >= kMaxSlots) throw ApiError(RLSQ_ERR_ARG, "too many triangular solves in one apply");
@@ -419,8 +424,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, bt, rhs, x, P->barriers.p + slot, static_cast<const LsmrState*>(S),
-                                         error_word(S)));
+            RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, bt, rhs, x, P->barriers.p + slot, G8, err));
         });
     } else if (P->map.sched[which] == RLSQ_TRSV_WAVE) {
         // all-one bytes mark "not yet solved" (see k_trsv_wave)
@@ -441,8 +445,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
                 attr[0].val.cooperative = 1;
                 cfg.attrs = attr;
                 cfg.numAttrs = 1;
-                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, static_cast<const LsmrState*>(S),
-                                             error_word(S)));
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kern, tri, rhs, x, G8, err));
             };
             if (kp >= 8) run(k_trsv_wave<T, decltype(k)::value, 8>);
             else run(k_trsv_wave<T, decltype(k)::value, 4>);
@@ -466,7 +469,7 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
                     const int chunks = (n + chunk_rows - 1) / chunk_rows;
                     const int blocks_needed = (chunks + kBlock / 32 - 1) / (kBlock / 32);
                     const int grid = std::max(1, std::min(R > 0 ? blocks_needed : chunks, occ * P->num_sms));
-                    kern<<<grid, kBlock, 0, st>>>(tri, rhs, x, slot, P->tickets.p, S, error_word(S));
+                    kern<<<grid, kBlock, 0, st>>>(tri, rhs, x, slot, P->tickets.p, G8, err);
                 };
                 if (R >= 4) run(k_trsv_warp<T, GG, KK, 4>, (32 / GG) * 4);
                 else if (R == 2) run(k_trsv_warp<T, GG, KK, 2>, (32 / GG) * 2);
@@ -503,11 +506,14 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
         if (P->correction == RLSQ_CORR_CG) {
             T *rv = F.vm[0].p, *pv = F.vm[1].p, *sp = F.vm[2].p, *w = F.vm[3].p;
             T *c1 = F.vn[3].p, *c2 = F.vn[4].p, *c3 = F.vn[2].p;
+            // adaptive number of CG steps: a gate the remaining steps check
+            LsmrState* gate = P->opts.cg_tol > 0.0 ? state_ptr(P, 2) : nullptr;
+            const double tol2 = P->opts.cg_tol * P->opts.cg_tol;
             {
                 RecScope rs(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
                 with_G(P->map.G_L2, [&](auto g) {
                     k_l2_start<T, decltype(g)::value><<<gl2, kBlock, 0, st>>>(L2, q1, rv, S, P->part.p,
-                                                                              P->counter.p);
+                                                                              P->counter.p, gate);
                 });
             }
             for (int it = 0; it < P->opts.cg_steps; ++it) {
@@ -516,29 +522,29 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
                     RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, sizeof(T), sizeof(T)), st);
                     with_G(P->map.G_L2t, [&](auto g) {
                         constexpr int GG = decltype(g)::value;
-                        if (first) k_l2t_cg<T, GG, true><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S);
-                        else k_l2t_cg<T, GG, false><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S);
+                        if (first) k_l2t_cg<T, GG, true><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S, gate);
+                        else k_l2t_cg<T, GG, false><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S, gate);
                     });
                 }
-                launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{c1, nullptr, nullptr}, c2, slot++, S, st);
-                launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{c2, nullptr, nullptr}, c3, slot++, S, st);
+                launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{c1, nullptr, nullptr}, c2, slot++, S, st, gate);
+                launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{c2, nullptr, nullptr}, c3, slot++, S, st, gate);
                 RecScope rs2(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
                 with_G(P->map.G_L2, [&](auto g) {
                     constexpr int GG = decltype(g)::value;
                     if (first)
                         k_l2_sp<T, GG, true><<<gl2, kBlock, 0, st>>>(L2, c3, rv, pv, sp, S, P->part.p,
-                                                                     P->counter.p);
+                                                                     P->counter.p, gate);
                     else
                         k_l2_sp<T, GG, false><<<gl2, kBlock, 0, st>>>(L2, c3, rv, pv, sp, S, P->part.p,
-                                                                      P->counter.p);
+                                                                      P->counter.p, gate);
                 });
                 RecScope rs3(P, RLSQ_KCLASS_VEC, (first ? 4.0 : 5.0) * sizeof(T) * m2, st);
                 if (first)
                     k_cg_update<T, true><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, w, S, P->part.p,
-                                                                P->counter.p);
+                                                                P->counter.p, gate, tol2);
                 else
                     k_cg_update<T, false><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, w, S, P->part.p,
-                                                                 P->counter.p);
+                                                                 P->counter.p, gate, tol2);
             }
             wv = w;
         } else {
@@ -1214,7 +1220,7 @@ int rlsq_create(int64_t m, int64_t n, const int64_t* rowptr, const int32_t* coli
         P->tx.alloc(static_cast<size_t>(n));
         P->b.alloc(static_cast<size_t>(m));
         for (auto* v : {&P->s, &P->h, &P->hb}) v->alloc(static_cast<size_t>(n));
-        P->S.alloc(2);
+        P->S.alloc(3);  // the solve's state, a scratch state, the adaptive-CG gate
         P->part.alloc(static_cast<size_t>(max_grid(P.get())) * 2);
         P->counter.alloc(1);
         RLSQ_CUDA(cudaMemsetAsync(P->counter.p, 0, sizeof(unsigned), st));
@@ -1252,6 +1258,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         if (opts.cg_steps > 16) throw ApiError(RLSQ_ERR_ARG, "cg_steps must be <= 16");
         if (opts.trsv_rows != 0 && opts.trsv_rows != 1 && opts.trsv_rows != 2 && opts.trsv_rows != 4)
             throw ApiError(RLSQ_ERR_ARG, "trsv_rows must be 0, 1, 2 or 4");
+        if (!(opts.cg_tol >= 0.0 && opts.cg_tol < 1.0)) throw ApiError(RLSQ_ERR_ARG, "cg_tol must be in [0, 1)");
         const auto t0 = std::chrono::steady_clock::now();
         h->factored = false;
         drop_graphs(h);

@@ -443,3 +443,58 @@ def test_apply_and_solve_other_cg_step_counts(cfg0, steps):
     ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
     res = P.solve(cfg0.b)
     _check_solve(cfg0, res, ref)
+
+
+# ---------------------------------------------------------------------------
+# adaptive number of CG steps on S (stop once ||r_j|| <= tol ||r_0||)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("sched", [B.TRSV_SYNCFREE, B.TRSV_LEVEL, B.TRSV_COOP, B.TRSV_WAVE, B.TRSV_BINNED])
+@pytest.mark.parametrize("tol", [0.3, 0.05])
+def test_apply_adaptive_cg(cfg0, sched, tol):
+    """Each apply takes as many CG steps as the oracle's (at most 12) and
+    equals the oracle's apply within 1e-12; the steps the oracle took vary
+    between right-hand sides."""
+    P = make(cfg0, B.CORR_CG, sched=sched, cg_steps=12, cg_tol=tol)
+    f = oracle_factor(cfg0, oracle.CG, steps=12)
+    f.set_correction(oracle.CG, 12, cg_tol=tol)
+    rng = np.random.default_rng(60)
+    steps = set()
+    for _ in range(3):
+        s = rng.standard_normal(cfg0.n)
+        t = P.apply(s)
+        ref = f.apply(s)
+        steps.add(f.cg_last_steps())
+        assert close(t, ref, 1e-12), (rel(t, ref), f.cg_last_steps())
+    assert max(steps) < 12
+
+
+def test_apply_adaptive_cg_mid(mid):
+    P = make(mid, B.CORR_CG, cg_steps=10, cg_tol=0.1)
+    f = oracle_factor(mid, oracle.CG, steps=10)
+    f.set_correction(oracle.CG, 10, cg_tol=0.1)
+    s = np.random.default_rng(61).standard_normal(mid.n)
+    t = P.apply(s)
+    assert close(t, f.apply(s), 1e-12)
+    assert 1 <= f.cg_last_steps() < 10
+
+
+def test_solve_adaptive_cg(cfg0):
+    P = make(cfg0, B.CORR_CG, cg_steps=10, cg_tol=0.1)
+    f = oracle_factor(cfg0, oracle.CG, steps=10)
+    f.set_correction(oracle.CG, 10, cg_tol=0.1)
+    ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
+    _check_solve(cfg0, P.solve(cfg0.b), ref)
+
+
+def test_adaptive_cg_refused_in_batch_and_server(cfg0):
+    P = make(cfg0, B.CORR_CG, cg_steps=6, cg_tol=0.1)
+    with pytest.raises(B.RlsqError) as e:
+        B.batch_solve([P], [cfg0.b])
+    assert e.value.code == -1
+    srv = B.Server(hbm_budget_bytes=2**30, max_slots=2)
+    with pytest.raises(B.RlsqError) as e:
+        srv.register(P)
+    assert e.value.code == -1
+    srv.close()
+    with pytest.raises(B.RlsqError):
+        B.Problem.from_problem(cfg0).factor(mu=MU, cg_tol=1.5)
