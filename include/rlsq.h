@@ -142,6 +142,12 @@ typedef struct {
                               ||r_j|| to at most cg_tol ||r_0|| (cg_steps is then the largest
                               count); 0 = always cg_steps steps.  Single-problem solves only:
                               rlsq_batch_solve and rlsq_server_register refuse it (ARG) */
+    int32_t dense_host;    /* RLSQ_CORR_DENSE: 0 = form S^{-1} on the GPU (Z = L1^{-T} L2^T by a
+                              multi-right-hand-side solve, S = I + Z^T Z, Cholesky, inverse; Z
+                              must fit in 80% of the free device memory: OOM otherwise);
+                              1 = on the host threads, keeping S^{-1} (and Z within 2 GiB) so
+                              that rlsq_add_rows / rlsq_remove_rows update it by block
+                              inversion instead of forming it again */
 } rlsq_factor_opts;
 
 /* Options of a solve. */

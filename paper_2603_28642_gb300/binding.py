@@ -45,6 +45,7 @@ class FactorOpts(C.Structure):
         ("dense_cap", C.c_int64), ("precision", C.c_int32), ("trsv_schedule", C.c_int32),
         ("autotune", C.c_int32), ("dense_row_min", C.c_int64), ("host_threads", C.c_int32),
         ("level_merge", C.c_int32), ("trsv_rows", C.c_int32), ("cg_tol", C.c_double),
+        ("dense_host", C.c_int32),
     ]
 
 

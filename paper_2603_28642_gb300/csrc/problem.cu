@@ -1067,6 +1067,7 @@ void default_mapping(rlsq_problem_s* P) {
 }
 
 void autotune(rlsq_problem_s* P, int mode);  // autotune.cu
+void device_schur_inverse(const IlupResult& F, DevArray<double>& out, cudaStream_t st, int num_sms);  // schur.cu
 
 // Times one standalone solve of system `which` with the current mapping
 // (used by the autotuner); inputs in vn[3], output in vn[4].
@@ -1299,9 +1300,12 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
                        ? RLSQ_CORR_DENSE
                        : RLSQ_CORR_CG;
         std::vector<double> sinv;
+        bool sinv_on_device = false;
         if (corr == RLSQ_CORR_DENSE) {
             if (h->sinv_valid) {
                 sinv = h->sinv_host;  // formed for this factor, or updated with its rows
+            } else if (!opts.dense_host) {
+                sinv_on_device = true;  // formed below, once the factor is on the device
             } else {
                 int th = opts.host_threads > 0 ? opts.host_threads
                                                : static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
@@ -1373,6 +1377,21 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         h->f32.clear();
         if (opts.precision == RLSQ_PREC_FP32) h->f32.upload(*F, h->merged.data(), sinv, st);
         else h->f64.upload(*F, h->merged.data(), sinv, st);
+        if (sinv_on_device) {
+            DevArray<double> sd;
+            device_schur_inverse(*F, sd, st, h->num_sms);
+            const size_t cnt = static_cast<size_t>(m2) * static_cast<size_t>(m2);
+            if (opts.precision == RLSQ_PREC_FP32) {
+                h->f32.sinv.alloc(cnt);
+                const int grid = static_cast<int>(std::max<size_t>(1, std::min<size_t>((cnt + kBlock - 1) / kBlock, 4096)));
+                k_convert<float, double><<<grid, kBlock, 0, st>>>(static_cast<int>(cnt), sd.p, h->f32.sinv.p);
+                RLSQ_CUDA(cudaGetLastError());
+            } else {
+                h->f64.sinv.alloc(cnt);
+                RLSQ_CUDA(cudaMemcpyAsync(h->f64.sinv.p, sd.p, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
+            }
+            RLSQ_CUDA(cudaStreamSynchronize(st));
+        }
         if (opts.dense_row_min != 0) {
             // an explicit dense-row threshold (< 0: none) replaces the automatic one
             layout_A(h, opts.dense_row_min);

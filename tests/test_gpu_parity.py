@@ -498,3 +498,39 @@ def test_adaptive_cg_refused_in_batch_and_server(cfg0):
     srv.close()
     with pytest.raises(B.RlsqError):
         B.Problem.from_problem(cfg0).factor(mu=MU, cg_tol=1.5)
+
+
+# ---------------------------------------------------------------------------
+# the dense correction's S^{-1} formed on the device (Z, S = I + Z^T Z,
+# Cholesky, inverse) against the host formation and the oracle
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def quasi_square():
+    # 700 rows in A2: Z has 700 columns, the Cholesky 700 pivots
+    prob = synth.sparse_problem(12_700, 12_000, 6, seed=91, hidden_diag=True)
+    return prob, oracle_factor(prob, oracle.DENSE)
+
+
+@pytest.mark.parametrize("prec", [B.PREC_FP64, B.PREC_FP32])
+def test_dense_correction_formed_on_device(quasi_square, prec):
+    """The apply with S^{-1} formed on the GPU equals the one formed on the
+    host within 1e-12 (float64) and the oracle's dense Cholesky apply within
+    1e-12 (float64) or the float32 bound."""
+    prob, f = quasi_square
+    dev = make(prob, B.CORR_DENSE, prec=prec)
+    host = make(prob, B.CORR_DENSE, prec=prec, dense_host=1)
+    rng = np.random.default_rng(92)
+    for _ in range(2):
+        s = rng.standard_normal(prob.n)
+        td, th, ref = dev.apply(s), host.apply(s), f.apply(s)
+        if prec == B.PREC_FP64:
+            assert close(td, th, 1e-12) and close(td, ref, 1e-12), (rel(td, th), rel(td, ref))
+        else:
+            assert close(td, ref, 5e-6), rel(td, ref)
+
+
+def test_dense_correction_on_device_solves_cfg0(cfg0):
+    P = make(cfg0, B.CORR_DENSE)
+    f = oracle_factor(cfg0, oracle.DENSE)
+    ref = oracle.lsmr(f, cfg0.m, cfg0.n, cfg0.rowptr, cfg0.colidx, cfg0.vals, cfg0.b)
+    _check_solve(cfg0, P.solve(cfg0.b), ref)
