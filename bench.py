@@ -66,10 +66,12 @@ def parse():
 
 
 # DRAM bytes (read + write) of ONE launch of a kernel class's solve kernel,
-# from an ncu capture summarised under profiles/ (same kernel, same recipe),
-# keyed by (class, schedule the class ran with).  The bench reports it only
-# when its dominant class ran that way.
-MEASURED_TRAFFIC = {}
+# from an ncu capture of the same kernel on the same recipe, keyed by (class,
+# schedule the class ran with).  The bench reports it only when its dominant
+# class ran that way.  The binned L1 solve was captured at half size
+# (1M x 500k: 52.80 MB); its traffic grows with the rows and entries, so a
+# full-size launch moves twice that.
+MEASURED_TRAFFIC = {("trsv_L1", 5): 2 * 52.80e6}
 CLASS_SYSTEM = {"trsv_L1": 0, "trsv_L1t": 1, "trsv_U": 2, "trsv_Ut": 3}
 # solves per iteration of each triangular-solve class with CG(k): L1 and L1^T
 # once each around the correction and once per CG step; U and U^T once
@@ -544,6 +546,9 @@ def measure_dense_correction(n=100_000, m2=512):
 
     prob = synth.sparse_problem(n + m2, n, 8, seed=5, hidden_diag=True)
     kw = dict(p=10, tau=1e-2, mu=1.0, correction=B.CORR_DENSE)
+    # first use of the device formation (library handles, lazy module loads) kept out of the timing
+    small = synth.config_problem(0)
+    B.Problem.from_problem(small).factor(**kw)
     out = {"m": prob.m, "n": prob.n, "m_minus_n": m2}
     for name, host in (("device", 0), ("host", 1)):
         P = B.Problem.from_problem(prob)

@@ -8,10 +8,12 @@ part worth capturing inside an NVTX range named `timed`:
     python -m paper_2603_28642_gb300.cases trsv --system L1 --schedule binned --merge 0 --scale 0.5
     python -m paper_2603_28642_gb300.cases trsv --system L1 --schedule auto --merge 0 --autotune --scale 1
     python -m paper_2603_28642_gb300.cases iteration --scale 0.75
+    python -m paper_2603_28642_gb300.cases products --scale 0.5
 
     python -m paper_2603_28642_gb300.cases setup --scale 1 --threads 8
 
-`trsv` calls rlsq_trsv on one system a few times; `iteration` autotunes and
+`trsv` calls rlsq_trsv on one system a few times; `products` runs three LSMR
+iterations with the default mappings (the A and A^T products); `iteration` autotunes and
 profiles one preconditioned LSMR iteration; `setup` times the host-only set-up
 (ILUP, split, level sets; no GPU needed) with a given thread count and prints a
 checksum of the factor, which is the same for every thread count.  Everything
@@ -55,6 +57,8 @@ def main(argv=None) -> int:
     t.add_argument("--autotune", action="store_true", help="autotune the mapping as the bench does")
     t.add_argument("--repeat", type=int, default=3)
     t.add_argument("--scale", type=float, default=0.25)
+    pr = sub.add_parser("products")
+    pr.add_argument("--scale", type=float, default=0.5)
     it = sub.add_parser("iteration")
     it.add_argument("--scale", type=float, default=0.75)
     it.add_argument("--fp32", action="store_true")
@@ -92,6 +96,14 @@ def main(argv=None) -> int:
             x = P.trsv(SYSTEMS[args.system], b)
         _nvtx(False)
         print(f"trsv {args.system} ({args.schedule}, merge {args.merge}): |x| = {np.linalg.norm(x):.6e}")
+    elif args.case == "products":
+        # three LSMR iterations (the A and A^T products with the residual pair),
+        # default mappings, no autotuning
+        P.factor(**FACTOR)
+        _nvtx(True)
+        res = P.solve(prob.b, atol=0.0, maxit=3, check_every=1)
+        _nvtx(False)
+        print(f"products: {res.info['iterations']} iterations")
     else:
         info = P.factor(**FACTOR, precision=B.PREC_FP32 if args.fp32 else B.PREC_FP64, autotune=1)
         _nvtx(True)
