@@ -41,8 +41,27 @@ struct LsmrState {
     int32_t status;
     int32_t apply_count;      // number of finished preconditioner applications (flag epochs)
     int32_t error;            // device-side error word (wait timeout)
-    int32_t pad[2];
+    int32_t check;            // 1: this iteration forms the explicit residual pair (A x_k, A^T r_k)
+    int32_t pad1;
 };
+
+// When an iteration forms the explicit residual r_k = b - A x_k and A^T r_k
+// (half the float64 work of the two products) for the stopping ratio of x_k:
+// in the first kResidualFirst iterations, whenever the last explicit ratio is
+// below kResidualNear * atol, at the iteration limit, and otherwise every
+// kResidualEvery-th iteration.  A solve stops only on an explicit ratio, so
+// the returned x_k carries its exact ratio; a stop is found later than the
+// first k with ratio_k < atol only if the ratio fell by more than
+// kResidualNear within kResidualEvery - 1 iterations.
+constexpr int kResidualFirst = 4;
+constexpr int kResidualEvery = 4;
+constexpr double kResidualNear = 1000.0;
+
+__device__ __forceinline__ int residual_check_next(const LsmrState* S) {
+    const int kn = S->k + 1;
+    return (kn < kResidualFirst) || (S->ratio < kResidualNear * S->atol) || (kn % kResidualEvery == 0) ||
+           (kn >= S->maxit);
+}
 
 // ---------------------------------------------------------------------------
 // small device helpers
@@ -232,6 +251,25 @@ __device__ __forceinline__ void row_dot_pair(const Csr<TV>& a, int row, int lane
     }
 }
 
+// The first halves only: p[j].x (an 8-byte gather per entry).
+template <int G, typename TV>
+__device__ __forceinline__ void row_dot_first(const Csr<TV>& a, int row, int lane, const double2* __restrict__ p,
+                                              double& s1) {
+    const double* px = reinterpret_cast<const double*>(p);
+    const int e1 = a.ptr[row + 1];
+    int e = a.ptr[row] + lane;
+    for (; e + 3 * G < e1; e += 4 * G) {
+        const int j0 = a.idx[e], j1 = a.idx[e + G], j2 = a.idx[e + 2 * G], j3 = a.idx[e + 3 * G];
+        const double a0 = a.val[e], a1 = a.val[e + G], a2 = a.val[e + 2 * G], a3 = a.val[e + 3 * G];
+        const double p0 = px[2 * (size_t)j0], p1 = px[2 * (size_t)j1], p2 = px[2 * (size_t)j2], p3 = px[2 * (size_t)j3];
+        s1 = fma(a0, p0, s1);
+        s1 = fma(a1, p1, s1);
+        s1 = fma(a2, p2, s1);
+        s1 = fma(a3, p3, s1);
+    }
+    for (; e < e1; e += G) s1 += a.val[e] * px[2 * (size_t)a.idx[e]];
+}
+
 // tx[j] = (t_j, x_j): v^ = t * inv_alpha and the current iterate x_k.
 // qr[i] = (q_i, r_i) with u = q * inv_beta.
 // q <- A v^ - alpha u  (= beta_{k+2} u_{k+2}),  r <- b - A x_k
@@ -245,16 +283,18 @@ k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__
             int ms = 0, const double2* __restrict__ dense_av = nullptr) {
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, alpha = S->alpha, inv_beta = S->inv_beta;
+    const bool chk = S->check != 0;  // uniform: form r = b - A x_k as well
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
     const int groups = (gridDim.x * kBlock) / G;
     double acc[2] = {0.0, 0.0};
     for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < A.rows; row += groups) {
         double s1 = 0.0, s2 = 0.0;
-        row_dot_pair<G>(A, row, lane, tx, s1, s2);
+        if (chk) row_dot_pair<G>(A, row, lane, tx, s1, s2);
+        else row_dot_first<G>(A, row, lane, tx, s1);
         if (G > 1) {
             s1 = group_sum<G>(s1, mask);
-            s2 = group_sum<G>(s2, mask);
+            if (chk) s2 = group_sum<G>(s2, mask);
         }
         if (lane == 0) {
             if (dense_av && row >= ms) {
@@ -264,7 +304,7 @@ k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__
             }
             const double2 old = qr[row];
             const double qn = s1 * inv_alpha - alpha * (old.x * inv_beta);
-            const double rr = b[row] - s2;
+            const double rr = chk ? b[row] - s2 : old.y;
             qr[row] = make_double2(qn, rr);
             acc[0] += qn * qn;
             acc[1] += rr * rr;
@@ -275,7 +315,7 @@ k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__
         const double beta = sqrt(tot[0]);
         S->beta = beta;
         S->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
-        S->rnorm = sqrt(tot[1]);
+        if (chk) S->rnorm = sqrt(tot[1]);
     }
 }
 
@@ -290,16 +330,18 @@ k_spmvt_lsmr(Csr<double> At, const double2* __restrict__ qr, double* __restrict_
              double* part, unsigned* counter, const double2* __restrict__ dense_atv = nullptr) {
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, beta = S->beta, inv_beta = S->inv_beta;
+    const bool chk = FIRST || S->check != 0;  // uniform: form A^T r as well
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
     const int groups = (gridDim.x * kBlock) / G;
     double acc[1] = {0.0};
     for (int col = (blockIdx.x * kBlock + threadIdx.x) / G; col < At.rows; col += groups) {
         double s1 = 0.0, s2 = 0.0;
-        row_dot_pair<G>(At, col, lane, qr, s1, s2);
+        if (chk) row_dot_pair<G>(At, col, lane, qr, s1, s2);
+        else row_dot_first<G>(At, col, lane, qr, s1);
         if (G > 1) {
             s1 = group_sum<G>(s1, mask);
-            s2 = group_sum<G>(s2, mask);
+            if (chk) s2 = group_sum<G>(s2, mask);
         }
         if (lane == 0) {
             if (dense_atv) {
@@ -313,17 +355,20 @@ k_spmvt_lsmr(Csr<double> At, const double2* __restrict__ qr, double* __restrict_
     }
     double tot[1];
     if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0 && !FIRST) {
-        const double arn = sqrt(tot[0]);
-        S->arnorm = arn;
-        const double ratio = S->rnorm > 0.0 ? arn / (S->anorm * S->rnorm) : 0.0;
-        S->ratio = ratio;
-        if (ratio < S->atol) {
-            S->done = 1;
-            S->status = kOk;
-        } else if (S->k >= S->maxit) {
-            S->done = 1;
-            S->status = kErrMaxit;
+        if (chk) {
+            const double arn = sqrt(tot[0]);
+            S->arnorm = arn;
+            const double ratio = S->rnorm > 0.0 ? arn / (S->anorm * S->rnorm) : 0.0;
+            S->ratio = ratio;
+            if (ratio < S->atol) {
+                S->done = 1;
+                S->status = kOk;
+            } else if (S->k >= S->maxit) {
+                S->done = 1;
+                S->status = kErrMaxit;
+            }
         }
+        S->check = residual_check_next(S);
     }
 }
 

@@ -701,6 +701,7 @@ static LsmrState initial_state(const rlsq_problem_s* P, double atol, int maxit) 
     s.atol = atol;
     s.maxit = maxit;
     s.rho = s.rhobar = s.cbar = 1.0;
+    s.check = 1;
     return s;
 }
 
