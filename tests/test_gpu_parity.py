@@ -99,9 +99,12 @@ def test_anorm_matches_oracle(cfg0):
 # ---------------------------------------------------------------------------
 # structure through the GPU handle (bit-exact)
 # ---------------------------------------------------------------------------
-def test_structure_bitexact(cfg0):
-    P = make(cfg0, B.CORR_NONE)
-    f = oracle_factor(cfg0, oracle.NONE)
+@pytest.mark.parametrize("mu", [MU, 0.1])
+def test_structure_bitexact(cfg0, mu):
+    """Also at the paper's mu = 0.1 (Sec. 5.2), which the workloads replace
+    by mu = 1 (the factor is unstable on these matrices at 0.1)."""
+    P = make(cfg0, B.CORR_NONE, mu=mu)
+    f = oracle_factor(cfg0, oracle.NONE, mu=mu)
     prow, a2, d, ud = P.split()
     oprow, oa2 = f.perm()
     assert np.array_equal(prow, oprow) and np.array_equal(a2, oa2)
