@@ -66,6 +66,7 @@ struct BSlot {
     int32_t nlev[4];
     Csr<double> A, At;
     Tri<T> tri[4];
+    BinTri<T> bt[4];  // the binned form of each system (kb_trsv_bin)
     const int32_t* lp[4];
     Csr<T> L2, L2t;
     const T* d;
@@ -246,14 +247,9 @@ __device__ __forceinline__ const BSlot<T>* gate_s(const BSlot<T>* slots, const i
     return D;
 }
 
-// position t of triangular system `which` of one slot; the right-hand side is
-// selected as in the single-problem apply.  x is read through L2: in the
-// persistent solve other SMs wrote it during the same launch.
+// The right-hand side of a slot's solve, selected as in the single-problem apply.
 template <typename T, int K>
-__device__ __forceinline__ void kb_solve_row(const BSlot<T>& D, int which, int t, int ia, int ib, int io) {
-    // local copies: stores to x could otherwise alias the slot table, and
-    // every structure pointer would be reloaded inside the loops
-    const Tri<T> tri = D.tri[which];
+__device__ __forceinline__ Rhs<T> slot_rhs(const BSlot<T>& D, int ia, int ib) {
     Rhs<T> rhs;
     if (K == RHS_SCALED) {
         rhs.a = D.d;
@@ -264,62 +260,60 @@ __device__ __forceinline__ void kb_solve_row(const BSlot<T>& D, int which, int t
         rhs.b = (K == RHS_SUB) ? D.vn[ib] : nullptr;
         rhs.s = nullptr;
     }
-    T* const x = D.vn[io];
-    const int row = tri.order[t];
-    const T rv = rhs_full<T, K>(tri, rhs, t, row);
-    const T dg = tri.idiag ? tri.idiag[t] : (T)1;
-    T sum = (T)0;
-    const int e1 = tri.ptr[t + 1];
-    int e = tri.ptr[t];
-    for (; e + 3 < e1; e += 4) {
-        const int j0 = tri.idx[e], j1 = tri.idx[e + 1], j2 = tri.idx[e + 2], j3 = tri.idx[e + 3];
-        const T a0 = tri.val[e], a1 = tri.val[e + 1], a2 = tri.val[e + 2], a3 = tri.val[e + 3];
-        const T v0 = __ldcg(&x[j0]), v1 = __ldcg(&x[j1]), v2 = __ldcg(&x[j2]), v3 = __ldcg(&x[j3]);
-        sum += a0 * v0;
-        sum += a1 * v1;
-        sum += a2 * v2;
-        sum += a3 * v3;
-    }
-    for (; e < e1; ++e) sum += tri.val[e] * __ldcg(&x[tri.idx[e]]);
-    T v = rv - sum;
-    if (tri.idiag) v = v * dg;
-    x[row] = v;
+    return rhs;
 }
 
-// one level of a triangular solve for every slot (positions lp[level]..lp[level+1])
+// One fused level group of a triangular solve for every slot, one launch per
+// group (the path for more than kCoopBlock slots): the slot's blocks (blockIdx.y
+// = slot) deal its items of group g; rows are solved exactly as in kb_trsv_bin,
+// so the bits do not depend on the schedule or the mix.
 template <typename T, int K>
 __global__ void __launch_bounds__(kBlock)
-kb_trsv_level(const BSlot<T>* slots, const int32_t* phase, int want, int cond, int which, int level, int ia,
+kb_trsv_level(const BSlot<T>* slots, const int32_t* phase, int want, int cond, int which, int group, int ia,
               int ib, int io) {
     const BSlot<T>* D = gate(slots, phase, want, cond);
-    if (!D || level >= D->nlev[which]) return;
-    const int lo = D->lp[which][level], hi = D->lp[which][level + 1];
-    for (int t = lo + blockIdx.x * kBlock + threadIdx.x; t < hi; t += gridDim.x * kBlock)
-        kb_solve_row<T, K>(*D, which, t, ia, ib, io);
+    if (!D) return;
+    const BinTri<T> bt = D->bt[which];
+    if (group >= bt.ngroups) return;
+    const int lane = threadIdx.x & 31;
+    const int W = gridDim.x * (kBlock / 32);
+    const int gw = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+    const int s0 = __ldg(&bt.gseg[group]), s1 = __ldg(&bt.gseg[group + 1]);
+    const int items = __ldg(&bt.gitems[group]);
+    const Rhs<T> rhs = slot_rhs<T, K>(*D, ia, ib);
+    T* const x = D->vn[io];
+    for (int k = gw; k < items; k += W) {
+        const BinSeg sg = bt.seg[binned_seg(bt.seg, s0, s1, k)];
+        BinLane<T> L;
+        binned_prepare<T>(bt, sg, k - sg.item0, lane, L);
+        binned_finish<T, K>(bt, rhs, sg, lane, L, x);
+    }
 }
 
-// One persistent launch solves system `which` for every slot: the co-resident
-// grid walks the levels 0..nlev-1 with a grid barrier between them; inside a
-// level the rows of all taking-part slots form one index range (a prefix of
-// the slots' level widths, built in shared memory by every block) that the
-// threads stride over.  A row is solved exactly as in kb_trsv_level, so the
-// bits do not depend on the schedule or the mix.  At most kCoopBlock slots.
+// The binned solve (see k_trsv_binned) for every slot at once: one persistent
+// launch walks the fused level groups 0..ngroups-1; for group g every block
+// builds, in shared memory, the prefix over the slots (one per thread) of the
+// work items the taking-part slots have in g, and the warps of the grid deal
+// the union of those items.  A row's arithmetic is exactly the single-problem
+// binned solve's (its own segment, lanes and slot), so the bits do not depend
+// on the mix.  A grid barrier separates the groups (bounded waits).  At most
+// kCoopBlock slots.
 template <typename T, int K>
 __global__ void __launch_bounds__(kCoopBlock, 1)
-kb_trsv_coop(const BSlot<T>* slots, const int32_t* phase, int nslots, int want, int cond, int which, int nlev,
-             int ia, int ib, int io, unsigned* bar, int* err) {
+kb_trsv_bin(const BSlot<T>* slots, const int32_t* phase, int nslots, int want, int cond, int which, int ngroups,
+            int ia, int ib, int io, unsigned* bar, int* err) {
     __shared__ int pre[kCoopBlock + 1];
     __shared__ int wsum[kCoopBlock / 32];
-    const int nthreads = gridDim.x * kCoopBlock;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tid = ((warp * gridDim.x + blockIdx.x) << 5) + lane;
-    for (int l = 0; l < nlev; ++l) {
+    const int W = gridDim.x * (kCoopBlock / 32);
+    const int gw = blockIdx.x + gridDim.x * warp;
+    for (int g = 0; g < ngroups; ++g) {
         int w = 0;
         if ((int)threadIdx.x < nslots) {
             const BSlot<T>* D = gate_s(slots, phase, threadIdx.x, want, cond);
-            if (D && l < D->nlev[which]) w = D->lp[which][l + 1] - D->lp[which][l];
+            if (D && g < D->bt[which].ngroups) w = D->bt[which].gitems[g];
         }
-        // inclusive scan of the widths over the block (slot = thread)
+        // inclusive scan of the item counts over the block (slot = thread)
         int v = w;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -342,20 +336,28 @@ kb_trsv_coop(const BSlot<T>* slots, const int32_t* phase, int nslots, int want, 
         if (threadIdx.x == 0) pre[0] = 0;
         __syncthreads();
         const int total = pre[nslots];
-        for (int idx = tid; idx < total; idx += nthreads) {
-            // the last slot s with pre[s] <= idx (empty slots have pre[s] == pre[s + 1])
+        for (int k = gw; k < total; k += W) {
+            // the last slot s with pre[s] <= k (slots without items have pre[s] == pre[s + 1])
             int lo = 0, hi = nslots;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (pre[mid] <= idx) lo = mid;
+                if (pre[mid] <= k) lo = mid;
                 else hi = mid;
             }
             const BSlot<T>& D = slots[lo];
-            kb_solve_row<T, K>(D, which, D.lp[which][l] + (idx - pre[lo]), ia, ib, io);
+            const BinTri<T> bt = D.bt[which];
+            const int item = k - pre[lo];
+            const int sidx = binned_seg(bt.seg, __ldg(&bt.gseg[g]), __ldg(&bt.gseg[g + 1]), item);
+            const BinSeg sg = bt.seg[sidx];
+            const Rhs<T> rhs = slot_rhs<T, K>(D, ia, ib);
+            BinLane<T> L;
+            binned_prepare<T>(bt, sg, item - sg.item0, lane, L);
+            binned_finish<T, K>(bt, rhs, sg, lane, L, D.vn[io]);
         }
-        if (l + 1 < nlev) {
+        if (g + 1 < ngroups) {
             grid_arrive(bar);
-            grid_wait(bar, (unsigned)(l + 1) * gridDim.x, err);
+            grid_wait(bar, (unsigned)(g + 1) * gridDim.x, err);
+            if (*(volatile int*)err != 0) return;
         }
     }
 }
@@ -646,7 +648,7 @@ struct Engine {
     DevArray<unsigned> d_bars;        // grid-barrier counters of the persistent solves of one apply
     DevArray<int> d_err;              // set when a bounded device wait gave up
     int bar_next = 0;
-    int coop_grid = 0;                // co-resident blocks of kb_trsv_coop (0: level launches only)
+    int coop_grid = 0;                // co-resident blocks of kb_trsv_bin (0: level launches only)
     // maxima over everything the graphs must cover
     int maxlev[4] = {0, 0, 0, 0};
     int maxcg = 0;
@@ -677,9 +679,9 @@ struct Engine {
                 RLSQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kCoopBlock, 0));
                 occ = std::min(occ, o);
             };
-            prep(kb_trsv_coop<T, RHS_VEC>);
-            prep(kb_trsv_coop<T, RHS_SCALED>);
-            prep(kb_trsv_coop<T, RHS_SUB>);
+            prep(kb_trsv_bin<T, RHS_VEC>);
+            prep(kb_trsv_bin<T, RHS_SCALED>);
+            prep(kb_trsv_bin<T, RHS_SUB>);
             coop_grid = occ * num_sms;
         }
         h_slots.assign(static_cast<size_t>(slots), BSlot<T>{});
@@ -739,6 +741,7 @@ struct Engine {
         for (int w = 0; w < 4; ++w) {
             D.nlev[w] = static_cast<int32_t>(F.level_ptr[w].size()) - 1;
             D.tri[w] = F.tview(w);
+            D.bt[w] = F.bview(w);
             D.lp[w] = F.level_ptr_d[w].p;
         }
         D.A = P->dA.view();
@@ -789,13 +792,13 @@ struct Engine {
             const int32_t* ph = d_phase.p;
             const int nl = maxlev[which];
             if (kind == RHS_SCALED)
-                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_coop<T, RHS_SCALED>, sl, ph, nslots, want, cond, which, nl,
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_bin<T, RHS_SCALED>, sl, ph, nslots, want, cond, which, nl,
                                              ia, ib, io, bar, d_err.p));
             else if (kind == RHS_SUB)
-                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_coop<T, RHS_SUB>, sl, ph, nslots, want, cond, which, nl, ia,
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_bin<T, RHS_SUB>, sl, ph, nslots, want, cond, which, nl, ia,
                                              ib, io, bar, d_err.p));
             else
-                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_coop<T, RHS_VEC>, sl, ph, nslots, want, cond, which, nl, ia,
+                RLSQ_CUDA(cudaLaunchKernelEx(&cfg, kb_trsv_bin<T, RHS_VEC>, sl, ph, nslots, want, cond, which, nl, ia,
                                              ib, io, bar, d_err.p));
             return;
         }

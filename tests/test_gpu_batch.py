@@ -195,3 +195,26 @@ def test_server_rejects_bad_requests(served):
     assert e.value.code == -11
     srv.close()
     tiny.close()
+
+
+def test_batch_beyond_persistent_slots_same_bits():
+    """More slots than one block can scan (1,030 > 1,024): the batch falls back
+    to one launch per fused level group, with the same row arithmetic, so a
+    problem's bits equal those of its solve alone (persistent path)."""
+    n, m, d = synth.batch_problem_sizes(1030, master_seed=73, n_lo=20, n_hi=40)
+    probs = [synth.sparse_problem(int(m[k]), int(n[k]), int(d[k]), seed=7300 + k) for k in range(1030)]
+    hs = []
+    for p in probs:
+        P = B.Problem.from_problem(p)
+        P.factor(mu=MU, correction=B.CORR_CG, host_threads=1)
+        hs.append(P)
+    xs, infos, code = B.batch_solve(hs, [p.b for p in probs])
+    assert code == 0
+    for k in (0, 517, 1029):
+        xa, ia, _ = B.batch_solve([hs[k]], [probs[k].b])
+        assert ia[0]["iterations"] == infos[k]["iterations"] and np.array_equal(xa[0], xs[k])
+        p = probs[k]
+        f = oracle.Factor(p.m, p.n, p.rowptr, p.colidx, p.vals, mu=MU)
+        f.set_correction(oracle.CG, 2)
+        ref = oracle.lsmr(f, p.m, p.n, p.rowptr, p.colidx, p.vals, p.b)
+        assert rel(xs[k], ref.x) <= 1e-6
