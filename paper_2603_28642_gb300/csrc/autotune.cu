@@ -52,7 +52,7 @@ float time_median(cudaStream_t st, Body&& body, int reps = 5) {
 
 int grid_for(const rlsq_problem_s* P, int64_t rows, int G) {
     const int64_t g = (rows * G + kBlock - 1) / kBlock;
-    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * 32))));
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * kGridBlocksPerSm))));
 }
 
 template <typename T>

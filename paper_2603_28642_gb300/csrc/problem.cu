@@ -272,7 +272,7 @@ static void with_rhs(int k, F&& f) {
     }
 }
 
-static int max_grid(const rlsq_problem_s* P) { return std::max(1, P->num_sms * 32); }
+static int max_grid(const rlsq_problem_s* P) { return std::max(1, P->num_sms * kGridBlocksPerSm); }
 
 static int grid_rows(const rlsq_problem_s* P, int64_t rows, int G) {
     const int64_t g = (rows * G + kBlock - 1) / kBlock;
