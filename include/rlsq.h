@@ -85,8 +85,13 @@ extern "C" {
 /* Krylov solvers of rlsq_solve */
 #define RLSQ_SOLVER_LSMR 0  /* LSMR in x-space (the default) */
 #define RLSQ_SOLVER_CGLS 1  /* preconditioned CGLS (Algorithm 1) with h = M^{-1} A^T r; no dense-row
-                               problems.  The paper feeds Algorithm 3 the residual split instead,
-                               which stalls once entries are dropped (see the oracle's orc_cgls). */
+                               problems */
+#define RLSQ_SOLVER_CGLS_SPLIT 2 /* Algorithm 1 with h = Algorithm 3 applied to the residual split
+                               (r1, r2) of r, the paper's combination of the preconditioner with
+                               A^T (Sec. 3.2); no dense-row problems.  With exact factors and the
+                               dense S^ it is one step; once entries are dropped h no longer
+                               vanishes at the least-squares residual and the iteration stalls
+                               above small tolerances (ends with RLSQ_ERR_MAXIT). */
 
 /* triangular systems for rlsq_trsv */
 #define RLSQ_SYS_L1 0   /* L1 x = b   (unit lower)      */
@@ -250,6 +255,17 @@ int rlsq_batch_solve(rlsq_problem const *hs, const double *const *bs, double *co
 
 /* One application t = M^{-1} s (both length n, ptr_mode memory). */
 int rlsq_apply(rlsq_problem h, const double *s, double *t, int32_t ptr_mode, void *stream);
+
+/* Algorithm 3 (Sec. 3.2) fed the residual split of r: r1 = r[prow] (the rows
+   of A1), r2 = r[a2rows] (the rows of A2), u = r2 - L2 L1^{-1} r1, S^ w = u
+   (the handle's correction: none, S^ = I, CG steps or dense), y = r1 +
+   L1^{-T} L2^T w, L1 v = y, U h = v, t = D h.  r has length m (the rows in
+   the order given to rlsq_create), t length n; both follow ptr_mode (device
+   pointers are ordered after `stream`, the call returns when t is written).
+   The factor's apply precision is used.  RLSQ_ERR_ARG for dense-row problems,
+   RLSQ_ERR_NOT_FACTORED before rlsq_factor, RLSQ_ERR_DEVICE_TIMEOUT when a
+   bounded wait of a triangular solve ran out. */
+int rlsq_apply_residual(rlsq_problem h, const double *r, double *t, int32_t ptr_mode, void *stream);
 
 /* y = A x (trans = 0; x length n, y length m) or y = A^T x (trans = 1). */
 int rlsq_matvec(rlsq_problem h, int32_t trans, const double *x, double *y, int32_t ptr_mode,

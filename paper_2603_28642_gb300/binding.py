@@ -27,7 +27,7 @@ HOST_PTRS, DEVICE_PTRS = 0, 1
 CORR_NONE, CORR_SI, CORR_CG, CORR_DENSE, CORR_AUTO = 0, 1, 2, 3, 4
 PREC_FP64, PREC_FP32 = 0, 1
 TRSV_AUTO, TRSV_LEVEL, TRSV_SYNCFREE, TRSV_COOP, TRSV_WAVE, TRSV_BINNED = 0, 1, 2, 3, 4, 5
-SOLVER_LSMR, SOLVER_CGLS = 0, 1
+SOLVER_LSMR, SOLVER_CGLS, SOLVER_CGLS_SPLIT = 0, 1, 2
 SYS_L1, SYS_L1T, SYS_U, SYS_UT = 0, 1, 2, 3
 PART_L1, PART_L2, PART_U = 0, 1, 2
 
@@ -99,7 +99,7 @@ class ServerStats(C.Structure):
 # every symbol declared in include/rlsq.h
 EXPORTS = [
     "rlsq_factor_opts_default", "rlsq_solve_opts_default", "rlsq_create", "rlsq_factor",
-    "rlsq_solve", "rlsq_solve_plain", "rlsq_batch_solve", "rlsq_apply", "rlsq_matvec",
+    "rlsq_solve", "rlsq_solve_plain", "rlsq_batch_solve", "rlsq_apply", "rlsq_apply_residual", "rlsq_matvec",
     "rlsq_trsv", "rlsq_get_info", "rlsq_get_split", "rlsq_get_factor", "rlsq_get_levels",
     "rlsq_destroy", "rlsq_server_create", "rlsq_server_register", "rlsq_server_submit",
     "rlsq_server_poll", "rlsq_server_get_stats", "rlsq_server_destroy", "rlsq_last_error",
@@ -140,6 +140,7 @@ def load(build_if_missing: bool = True):
             "rlsq_solve_plain": (C.c_int, [P, P, P, P, P]),
             "rlsq_batch_solve": (C.c_int, [P, P, P, i32, P, P]),
             "rlsq_apply": (C.c_int, [P, P, P, i32, P]),
+            "rlsq_apply_residual": (C.c_int, [P, P, P, i32, P]),
             "rlsq_matvec": (C.c_int, [P, i32, P, P, i32, P]),
             "rlsq_trsv": (C.c_int, [P, i32, P, P, i32, P]),
             "rlsq_get_info": (C.c_int, [P, P]),
@@ -323,6 +324,16 @@ class Problem:
         t = self._out_like(s, self.n)
         pt, _ = _ptr(t)
         _check(load().rlsq_apply(self._h, ps, pt, mode, _stream_of(s)))
+        return t
+
+    def apply_residual(self, r):
+        """Algorithm 3 fed the residual split of r (length m): t (length n)."""
+        if isinstance(r, np.ndarray):
+            r = np.ascontiguousarray(r, dtype=np.float64)
+        pr, mode = _ptr(r)
+        t = self._out_like(r, self.n)
+        pt, _ = _ptr(t)
+        _check(load().rlsq_apply_residual(self._h, pr, pt, mode, _stream_of(r)))
         return t
 
     def matvec(self, x, trans: bool = False):

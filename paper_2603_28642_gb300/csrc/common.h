@@ -123,6 +123,7 @@ struct DevFactor {
     DevCsr<T> L2, L2t;
     DevArray<T> d;
     DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
+    DevArray<int32_t> prow, a2rows;  // rows of A1 (by position) and of A2: Algorithm 3's input split
     DevArray<T> vn[5], vm[4];  // work vectors
     void upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h, cudaStream_t s);
     void clear() {
@@ -137,7 +138,7 @@ struct DevFactor {
             bentries[w] = 0;
         }
         for (auto* c : {&L2, &L2t}) { c->ptr.release(); c->idx.release(); c->val.release(); }
-        d.release(); sinv.release();
+        d.release(); sinv.release(); prow.release(); a2rows.release();
         for (auto& v : vn) v.release();
         for (auto& v : vm) v.release();
     }
@@ -230,8 +231,9 @@ struct rlsq_problem_s {
     cudaEvent_t ev[2] = {nullptr, nullptr};
 
     rlsq::Recorder* rec = nullptr;                  // set while profiling one eager iteration
-    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // [plain + 2 cgls] iteration graphs
-    int graph_iters[4] = {0, 0, 0, 0};
+    // iteration graphs: [plain + 2 cgls], and 4 for CGLS with the split (residual) apply
+    cudaGraphExec_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int graph_iters[5] = {0, 0, 0, 0, 0};
 
     ~rlsq_problem_s();
 };

@@ -1339,10 +1339,11 @@ k_trsv_level(Tri<T> tri, Rhs<T> rhs, T* x, int lo, int hi, const LsmrState* S) {
 // correction pieces (precision T)
 // ---------------------------------------------------------------------------
 
-// y = M x for a CSR matrix (no state check when S == nullptr)
+// y = M x, or y = M x - sub when sub is given (no state check when S == nullptr)
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock)
-k_csr_mv(Csr<T> M, const T* __restrict__ x, T* __restrict__ y, const LsmrState* S) {
+k_csr_mv(Csr<T> M, const T* __restrict__ x, T* __restrict__ y, const LsmrState* S,
+         const T* __restrict__ sub = nullptr) {
     if (S && S->done) return;
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
@@ -1351,15 +1352,15 @@ k_csr_mv(Csr<T> M, const T* __restrict__ x, T* __restrict__ y, const LsmrState* 
         T s = (T)0;
         row_dot<G>(M, row, lane, x, s);
         s = group_sum<G>(s, mask);
-        if (lane == 0) y[row] = s;
+        if (lane == 0) y[row] = sub ? s - sub[row] : s;
     }
 }
 
-// e = L2 q1, CG start: r = e (and p = e implied), rr = <e, e>
+// e = L2 q1 (or L2 q1 - sub), CG start: r = e (and p = e implied), rr = <e, e>
 template <typename T, int G>
 __global__ void __launch_bounds__(kBlock)
 k_l2_start(Csr<T> L2, const T* __restrict__ q1, T* __restrict__ r, LsmrState* S, double* part,
-           unsigned* counter, LsmrState* gate) {
+           unsigned* counter, LsmrState* gate, const T* __restrict__ sub = nullptr) {
     if (S->done) return;
     const unsigned mask = group_mask<G>();
     const int lane = threadIdx.x & (G - 1);
@@ -1370,6 +1371,7 @@ k_l2_start(Csr<T> L2, const T* __restrict__ q1, T* __restrict__ r, LsmrState* S,
         row_dot<G>(L2, row, lane, q1, s);
         s = group_sum<G>(s, mask);
         if (lane == 0) {
+            if (sub) s -= sub[row];
             r[row] = s;
             acc[0] += (double)(s * s);
         }
@@ -1576,6 +1578,22 @@ k_finish_apply(int n, const T* __restrict__ d, const T* __restrict__ g5, const d
     if (!(last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0)) return;
     if (CGLS) cgls_scalar_step<INIT>(S, tot[0]);
     else lsmr_scalar_step<INIT>(S, tot[0]);
+}
+
+// Algorithm 3's input split of an m-vector r (user row order, stride
+// `stride` doubles between entries): r1 = r[prow] (the rows of A1), r2 =
+// r[a2rows] (the rows of A2), in the apply precision.
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+k_split_gather(int n, int m2, const int32_t* __restrict__ prow, const int32_t* __restrict__ a2rows,
+               const double* __restrict__ r, int stride, T* __restrict__ r1, T* __restrict__ r2,
+               const LsmrState* S) {
+    if (S->done) return;
+    const int len = n > m2 ? n : m2;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) {
+        if (i < n) r1[i] = (T)r[(size_t)prow[i] * stride];
+        if (i < m2) r2[i] = (T)r[(size_t)a2rows[i] * stride];
+    }
 }
 
 // ---- preconditioned CGLS (Algorithm 1) ------------------------------------

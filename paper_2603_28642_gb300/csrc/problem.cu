@@ -225,6 +225,9 @@ void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const st
     L2.upload(F.L2, s);
     L2t.upload(F.L2t, s);
     upload_vec(d, F.d, s);
+    prow.upload(F.prow.data(), F.prow.size(), s);
+    if (!F.a2rows.empty()) a2rows.upload(F.a2rows.data(), F.a2rows.size(), s);
+    else a2rows.release();
     if (!sinv_h.empty()) upload_vec(sinv, sinv_h, s);
     else sinv.release();
     const size_t n = static_cast<size_t>(F.n), m2 = static_cast<size_t>(F.m - F.n);
@@ -273,6 +276,12 @@ static void with_rhs(int k, F&& f) {
 }
 
 static int max_grid(const rlsq_problem_s* P) { return std::max(1, P->num_sms * kGridBlocksPerSm); }
+
+// kernels without a grid-wide reduction keep a wide grid (32 blocks per SM)
+static int grid_rows_wide(const rlsq_problem_s* P, int64_t rows, int G) {
+    const int64_t g = (rows * G + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * 32))));
+}
 
 static int grid_rows(const rlsq_problem_s* P, int64_t rows, int G) {
     const int64_t g = (rows * G + kBlock - 1) / kBlock;
@@ -483,24 +492,42 @@ static void launch_trsv(rlsq_problem_s* P, DevFactor<T>& F, int which, int rk, R
 // t = M^{-1} s for the float64 vector s, result in P->t; advances the LSMR
 // scalars (INIT: the first alpha), or the CGLS ones (CGLS), or only the apply
 // count (standalone).
+//
+// With split_r (an m-vector r, entries split_stride doubles apart) the apply
+// is Algorithm 3 fed the residual split instead: r1 = r[prow], r2 =
+// r[a2rows], u = r2 - L2 L1^{-1} r1, S^ w = u, y = r1 + L1^{-T} L2^T w,
+// t = D U^{-1} L1^{-1} y.  The correction runs on -u (the same steps as the
+// x-space form, whose right-hand side is +L2 q1), so it yields -w and
+// y = r1 - L1^{-T} L2^T (-w); negation is exact, so this is the same
+// arithmetic.  s then only enters the scalar step (<t, s>, s = A^T r).
 template <typename T, bool INIT, bool CGLS = false>
 static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, LsmrState* S,
-                          cudaStream_t st) {
+                          cudaStream_t st, const double* split_r = nullptr, int split_stride = 1) {
     const int n = static_cast<int>(P->n);
     const int m2 = static_cast<int>(P->m - P->n);
     RLSQ_CUDA(cudaMemsetAsync(P->tickets.p, 0, sizeof(unsigned) * kMaxSlots, st));
     RLSQ_CUDA(cudaMemsetAsync(P->barriers.p, 0, sizeof(unsigned) * kMaxSlots, st));
     int slot = 0;
-    T* g1 = F.vn[0].p;
-    T* g2 = F.vn[1].p;
-    launch_trsv<T>(P, F, 3, RHS_SCALED, Rhs<T>{F.d.p, nullptr, s}, g1, slot++, S, st);  // U^{-T} D s
-    launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{g1, nullptr, nullptr}, g2, slot++, S, st);  // L1^{-T}
+    T* g2 = F.vn[1].p;       // x-space: L1^{-T} U^{-T} D s; split: r1
+    const T* sub = nullptr;  // split: r2, subtracted from L2 q1
+    if (split_r) {
+        T* r2 = F.vm[2].p;
+        RecScope rs(P, RLSQ_KCLASS_VEC, (12.0 + sizeof(T)) * (static_cast<double>(n) + m2), st);
+        k_split_gather<T><<<grid_rows_wide(P, std::max(n, m2), 1), kBlock, 0, st>>>(
+            n, m2, F.prow.p, m2 > 0 ? F.a2rows.p : nullptr, split_r, split_stride, g2, r2, S);
+        sub = r2;
+    } else {
+        T* g1 = F.vn[0].p;
+        launch_trsv<T>(P, F, 3, RHS_SCALED, Rhs<T>{F.d.p, nullptr, s}, g1, slot++, S, st);  // U^{-T} D s
+        launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{g1, nullptr, nullptr}, g2, slot++, S, st);  // L1^{-T}
+    }
     T* g4 = F.vn[0].p;
     if (P->correction != RLSQ_CORR_NONE) {
         T* q1 = F.vn[2].p;
         launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{g2, nullptr, nullptr}, q1, slot++, S, st);  // L1^{-1}
         const Csr<T> L2 = F.L2.view(), L2t = F.L2t.view();
-        const int gl2 = grid_rows(P, m2, P->map.G_L2), gl2t = grid_rows(P, n, P->map.G_L2t);
+        const int gl2 = grid_rows(P, m2, P->map.G_L2), gl2t = grid_rows_wide(P, n, P->map.G_L2t);
+        const int gl2w = grid_rows_wide(P, m2, P->map.G_L2);
         const int gv = grid_rows(P, m2, 1);
         T* wv = nullptr;
         if (P->correction == RLSQ_CORR_CG) {
@@ -513,7 +540,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
                 RecScope rs(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
                 with_G(P->map.G_L2, [&](auto g) {
                     k_l2_start<T, decltype(g)::value><<<gl2, kBlock, 0, st>>>(L2, q1, rv, S, P->part.p,
-                                                                              P->counter.p, gate);
+                                                                              P->counter.p, gate, sub);
                 });
             }
             for (int it = 0; it < P->opts.cg_steps; ++it) {
@@ -552,7 +579,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
             {
                 RecScope rs(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
                 with_G(P->map.G_L2, [&](auto g) {
-                    k_csr_mv<T, decltype(g)::value><<<gl2, kBlock, 0, st>>>(L2, q1, e, S);
+                    k_csr_mv<T, decltype(g)::value><<<gl2w, kBlock, 0, st>>>(L2, q1, e, S, sub);
                 });
             }
             wv = e;
@@ -592,15 +619,17 @@ static void enqueue_identity_apply(rlsq_problem_s* P, const double* s, LsmrState
                                                                                     S, P->part.p, P->counter.p);
 }
 
+// split_r: Algorithm 3 on the residual split of split_r (see enqueue_apply);
+// with plain (M = I) it is ignored.
 template <bool INIT, bool CGLS = false>
 static void enqueue_apply_any(rlsq_problem_s* P, const double* s, LsmrState* S, cudaStream_t st,
-                              bool plain) {
+                              bool plain, const double* split_r = nullptr, int split_stride = 1) {
     if (plain) {
         enqueue_identity_apply<INIT, CGLS>(P, s, S, st);
     } else if (P->precision == RLSQ_PREC_FP32) {
-        enqueue_apply<float, INIT, CGLS>(P, P->f32, s, S, st);
+        enqueue_apply<float, INIT, CGLS>(P, P->f32, s, S, st, split_r, split_stride);
     } else {
-        enqueue_apply<double, INIT, CGLS>(P, P->f64, s, S, st);
+        enqueue_apply<double, INIT, CGLS>(P, P->f64, s, S, st, split_r, split_stride);
     }
 }
 
@@ -635,7 +664,7 @@ static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, 
     }
     enqueue_apply_any<false>(P, P->s.p, S, st, plain);
     RecScope rs(P, RLSQ_KCLASS_UPDATE, 56.0 * n, st);
-    k_lsmr_update<false><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, P->hb.p, S);
+    k_lsmr_update<false><<<grid_rows_wide(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, P->hb.p, S);
 }
 
 static void enqueue_start(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
@@ -654,8 +683,9 @@ static void enqueue_start(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool
 }
 
 // Preconditioned CGLS (Algorithm 1) with h = M^{-1} A^T r, M^{-1} the same
-// x-space operator LSMR uses.  Vectors: (q, r) in qr, (h, x) in tx, z in s,
-// p in h.  No dense-row block.
+// x-space operator LSMR uses, or (split) h = Algorithm 3 applied to the
+// residual split of r, as the paper combines the preconditioner with A^T.
+// Vectors: (q, r) in qr, (h, x) in tx, z in s, p in h.  No dense-row block.
 static void enqueue_cgls_z(rlsq_problem_s* P, LsmrState* S, cudaStream_t st) {
     const int n = static_cast<int>(P->n);
     RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 8.0, 8.0), st);
@@ -665,16 +695,22 @@ static void enqueue_cgls_z(rlsq_problem_s* P, LsmrState* S, cudaStream_t st) {
     });
 }
 
-static void enqueue_start_cgls(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
+// the residual r_i at r[2 i] of the interleaved (q, r) pairs
+static const double* cgls_residual(const rlsq_problem_s* P) {
+    return reinterpret_cast<const double*>(P->qr.p) + 1;
+}
+
+static void enqueue_start_cgls(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain, bool split) {
     const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
     k_cgls_begin<<<grid_rows(P, std::max(m, n), 1), kBlock, 0, st>>>(m, n, P->b.p, P->qr.p, P->tx.p, S, P->part.p,
                                                                      P->counter.p);
     enqueue_cgls_z(P, S, st);                                      // z0 = A^T r0, ratio_0
-    enqueue_apply_any<true, true>(P, P->s.p, S, st, plain);       // h0 = M^{-1} z0, rho0
+    // h0 = M^{-1} z0 (or Algorithm 3 on r0), rho0
+    enqueue_apply_any<true, true>(P, P->s.p, S, st, plain, split ? cgls_residual(P) : nullptr, 2);
     k_cgls_p<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, S);  // p0 = h0
 }
 
-static void enqueue_iteration_cgls(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain) {
+static void enqueue_iteration_cgls(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool plain, bool split) {
     const int m = static_cast<int>(P->m), n = static_cast<int>(P->n);
     {
         RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 8.0, 16.0), st);
@@ -689,7 +725,7 @@ static void enqueue_iteration_cgls(rlsq_problem_s* P, LsmrState* S, cudaStream_t
                                                                        P->part.p, P->counter.p);
     }
     enqueue_cgls_z(P, S, st);
-    enqueue_apply_any<false, true>(P, P->s.p, S, st, plain);
+    enqueue_apply_any<false, true>(P, P->s.p, S, st, plain, split ? cgls_residual(P) : nullptr, 2);
     RecScope rs(P, RLSQ_KCLASS_VEC, 24.0 * n, st);
     k_cgls_p<false><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, S);
 }
@@ -712,15 +748,16 @@ static void put_state(rlsq_problem_s* P, LsmrState* S, const LsmrState& h, cudaS
 }
 
 static void drop_graphs(rlsq_problem_s* P) {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
         if (P->graph[i]) cudaGraphExecDestroy(P->graph[i]);
         P->graph[i] = nullptr;
         P->graph_iters[i] = 0;
     }
 }
 
-static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain, bool cgls = false) {
-    const int gi = (plain ? 1 : 0) + (cgls ? 2 : 0);
+static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain, bool cgls = false,
+                                       bool split = false) {
+    const int gi = (cgls && split && !plain) ? 4 : (plain ? 1 : 0) + (cgls ? 2 : 0);
     if (P->graph[gi] && P->graph_iters[gi] == iters) return P->graph[gi];
     if (P->graph[gi]) cudaGraphExecDestroy(P->graph[gi]);
     P->graph[gi] = nullptr;
@@ -729,7 +766,7 @@ static cudaGraphExec_t iteration_graph(rlsq_problem_s* P, int iters, bool plain,
     RLSQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     try {
         for (int i = 0; i < iters; ++i) {
-            if (cgls) enqueue_iteration_cgls(P, S, st, plain);
+            if (cgls) enqueue_iteration_cgls(P, S, st, plain, split);
             else enqueue_iteration(P, S, st, plain);
         }
     } catch (...) {
@@ -836,8 +873,10 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
     if (!b || !x) throw ApiError(RLSQ_ERR_ARG, "null b or x");
     if (!(opts.atol >= 0.0) || opts.maxit < 0) throw ApiError(RLSQ_ERR_ARG, "bad atol or maxit");
     if (!plain && !P->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
-    if (opts.solver != RLSQ_SOLVER_LSMR && opts.solver != RLSQ_SOLVER_CGLS) throw ApiError(RLSQ_ERR_ARG, "bad solver");
-    const bool cgls = opts.solver == RLSQ_SOLVER_CGLS;
+    if (opts.solver != RLSQ_SOLVER_LSMR && opts.solver != RLSQ_SOLVER_CGLS && opts.solver != RLSQ_SOLVER_CGLS_SPLIT)
+        throw ApiError(RLSQ_ERR_ARG, "bad solver");
+    const bool cgls = opts.solver != RLSQ_SOLVER_LSMR;
+    const bool split = opts.solver == RLSQ_SOLVER_CGLS_SPLIT;
     if (cgls && P->md > 0) throw ApiError(RLSQ_ERR_ARG, "the CGLS solver does not take dense-row problems");
     const int iters = std::max(1, opts.check_every);
     cudaStream_t st = P->stream;
@@ -850,9 +889,9 @@ static int run_solve(rlsq_problem_s* P, const double* b, double* x, const rlsq_s
     upload_b(P, b, dev, st);
     LsmrState* S = state_ptr(P, 0);
     put_state(P, S, initial_state(P, opts.atol, opts.maxit), st);
-    if (cgls) enqueue_start_cgls(P, S, st, plain);
+    if (cgls) enqueue_start_cgls(P, S, st, plain, split);
     else enqueue_start(P, S, st, plain);
-    cudaGraphExec_t g = iteration_graph(P, iters, plain, cgls);
+    cudaGraphExec_t g = iteration_graph(P, iters, plain, cgls, split);
     const int64_t max_launches = static_cast<int64_t>(opts.maxit) / iters + 4;
     int64_t launches = 0;
     // two graphs in flight; read `done` of the older one
@@ -1571,6 +1610,38 @@ int rlsq_apply(rlsq_problem h, const double* s, double* t, int32_t ptr_mode, voi
         copy_half(t, h->tx.p, h->n, 0, dev, h->s.p, st);  // t_j lives at tx[j].x
         RLSQ_CUDA(cudaStreamSynchronize(st));
         hs = *h->pinned_state;
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], st));
+            RLSQ_CUDA(cudaStreamWaitEvent(user, h->ev[0], 0));
+        }
+        if (hs.error) throw ApiError(RLSQ_ERR_DEVICE_TIMEOUT, "a sync-free triangular solve timed out");
+        return RLSQ_OK;
+    });
+}
+
+int rlsq_apply_residual(rlsq_problem h, const double* r, double* t, int32_t ptr_mode, void* stream) {
+    return guarded([&]() -> int {
+        if (!h || !r || !t) throw ApiError(RLSQ_ERR_ARG, "null argument");
+        if (!h->factored) throw ApiError(RLSQ_ERR_NOT_FACTORED, "rlsq_factor has not succeeded");
+        if (h->md > 0) throw ApiError(RLSQ_ERR_ARG, "the split apply does not take dense-row problems");
+        cudaStream_t st = h->stream;
+        const bool dev = ptr_mode == RLSQ_DEVICE_PTRS;
+        cudaStream_t user = static_cast<cudaStream_t>(stream);
+        if (dev) {
+            RLSQ_CUDA(cudaEventRecord(h->ev[0], user));
+            RLSQ_CUDA(cudaStreamWaitEvent(st, h->ev[0], 0));
+        }
+        LsmrState* S = state_ptr(h, 1);
+        put_state(h, S, initial_state(h, 0.0, 0), st);
+        // r into b (length m); s = 0 only feeds the unused scalar step
+        RLSQ_CUDA(cudaMemcpyAsync(h->b.p, r, sizeof(double) * h->m,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        RLSQ_CUDA(cudaMemsetAsync(h->s.p, 0, sizeof(double) * h->n, st));
+        enqueue_apply_any<true, true>(h, h->s.p, S, st, false, h->b.p, 1);
+        RLSQ_CUDA(cudaMemcpyAsync(h->pinned_state, S, sizeof(LsmrState), cudaMemcpyDeviceToHost, st));
+        copy_half(t, h->tx.p, h->n, 0, dev, h->s.p, st);  // t_j lives at tx[j].x
+        RLSQ_CUDA(cudaStreamSynchronize(st));
+        const LsmrState hs = *h->pinned_state;
         if (dev) {
             RLSQ_CUDA(cudaEventRecord(h->ev[0], st));
             RLSQ_CUDA(cudaStreamWaitEvent(user, h->ev[0], 0));
