@@ -219,7 +219,19 @@ __device__ __forceinline__ void row_dot(const Csr<TV>& a, int row, int lane, con
         s = fma(a2, x2, s);
         s = fma(a3, x3, s);
     }
-    for (; e < e1; e += G) s += (TA)a.val[e] * (TA)x[a.idx[e]];
+    // the lane's last (< 4) entries: every load issued before the first
+    // multiply-add (an absent entry re-reads entry e), added in entry order
+    if (e < e1) {
+        const bool h1 = e + G < e1, h2 = e + 2 * G < e1;
+        const int j0 = a.idx[e];
+        const int j1 = h1 ? a.idx[e + G] : j0, j2 = h2 ? a.idx[e + 2 * G] : j0;
+        const TA a0 = (TA)a.val[e];
+        const TA a1 = h1 ? (TA)a.val[e + G] : a0, a2 = h2 ? (TA)a.val[e + 2 * G] : a0;
+        const TA x0 = (TA)x[j0], x1 = (TA)x[j1], x2 = (TA)x[j2];
+        s = fma(a0, x0, s);
+        if (h1) s = fma(a1, x1, s);
+        if (h2) s = fma(a2, x2, s);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -249,11 +261,23 @@ __device__ __forceinline__ void row_dot_pair(const Csr<TV>& a, int row, int lane
         s1 = fma(a3, p3.x, s1);
         s2 = fma(a3, p3.y, s2);
     }
-    for (; e < e1; e += G) {
-        const double2 pj = p[a.idx[e]];
-        const double av = a.val[e];
-        s1 += av * pj.x;
-        s2 += av * pj.y;
+    if (e < e1) {  // the lane's last (< 4) entries, loads first (as in row_dot)
+        const bool h1 = e + G < e1, h2 = e + 2 * G < e1;
+        const int j0 = a.idx[e];
+        const int j1 = h1 ? a.idx[e + G] : j0, j2 = h2 ? a.idx[e + 2 * G] : j0;
+        const double a0 = a.val[e];
+        const double a1 = h1 ? (double)a.val[e + G] : a0, a2 = h2 ? (double)a.val[e + 2 * G] : a0;
+        const double2 p0 = p[j0], p1 = p[j1], p2 = p[j2];
+        s1 = fma(a0, p0.x, s1);
+        s2 = fma(a0, p0.y, s2);
+        if (h1) {
+            s1 = fma(a1, p1.x, s1);
+            s2 = fma(a1, p1.y, s2);
+        }
+        if (h2) {
+            s1 = fma(a2, p2.x, s1);
+            s2 = fma(a2, p2.y, s2);
+        }
     }
 }
 
@@ -273,7 +297,17 @@ __device__ __forceinline__ void row_dot_first(const Csr<TV>& a, int row, int lan
         s1 = fma(a2, p2, s1);
         s1 = fma(a3, p3, s1);
     }
-    for (; e < e1; e += G) s1 += a.val[e] * px[2 * (size_t)a.idx[e]];
+    if (e < e1) {  // the lane's last (< 4) entries, loads first (as in row_dot)
+        const bool h1 = e + G < e1, h2 = e + 2 * G < e1;
+        const int j0 = a.idx[e];
+        const int j1 = h1 ? a.idx[e + G] : j0, j2 = h2 ? a.idx[e + 2 * G] : j0;
+        const double a0 = a.val[e];
+        const double a1 = h1 ? (double)a.val[e + G] : a0, a2 = h2 ? (double)a.val[e + 2 * G] : a0;
+        const double p0 = px[2 * (size_t)j0], p1 = px[2 * (size_t)j1], p2 = px[2 * (size_t)j2];
+        s1 = fma(a0, p0, s1);
+        if (h1) s1 = fma(a1, p1, s1);
+        if (h2) s1 = fma(a2, p2, s1);
+    }
 }
 
 // tx[j] = (t_j, x_j): v^ = t * inv_alpha and the current iterate x_k.
@@ -1643,7 +1677,17 @@ k_cgls_z(Csr<double> At, const double2* __restrict__ qr, double* __restrict__ z,
             sum = fma(a2, v2, sum);
             sum = fma(a3, v3, sum);
         }
-        for (; e < e1; e += G) sum = fma(At.val[e], r[2 * At.idx[e]], sum);
+        if (e < e1) {  // the lane's last (< 4) entries, loads first (as in row_dot)
+            const bool h1 = e + G < e1, h2 = e + 2 * G < e1;
+            const int j0 = At.idx[e];
+            const int j1 = h1 ? At.idx[e + G] : j0, j2 = h2 ? At.idx[e + 2 * G] : j0;
+            const double a0 = At.val[e];
+            const double a1 = h1 ? At.val[e + G] : a0, a2 = h2 ? At.val[e + 2 * G] : a0;
+            const double v0 = r[2 * j0], v1 = r[2 * j1], v2 = r[2 * j2];
+            sum = fma(a0, v0, sum);
+            if (h1) sum = fma(a1, v1, sum);
+            if (h2) sum = fma(a2, v2, sum);
+        }
         if (G > 1) sum = group_sum<G>(sum, mask);
         if (lane == 0) {
             z[col] = sum;
