@@ -446,6 +446,8 @@ def run_ours(args):
         "kernel_classes": {k: {"ms": v["ms"], "launches": v["launches"],
                                "GBps": v["bytes"] / (v["ms"] / 1000.0) / 1e9} for k, v in cls.items()},
         "gpu_launches": launches * args.steps,
+        # products in the sliced layout (bits: 1 A, 2 A^T, 4 L2, 8 L2^T), as the autotuner chose
+        "sliced_products": finfo["sliced_products"],
         "clocks": clocks,
     }
     if rank == 0 and not args.no_extras:

@@ -153,6 +153,12 @@ typedef struct {
                               1 = on the host threads, keeping S^{-1} (and Z within 2 GiB) so
                               that rlsq_add_rows / rlsq_remove_rows update it by block
                               inversion instead of forming it again */
+    int32_t sliced;        /* layout of the A, A^T, L2 and L2^T products: 1 = sliced (one lane
+                              per row; rows sorted by length within windows of 1024, slices of
+                              32 rows stored column-major), 0 = CSR with G lanes per row,
+                              -1 (default) = the autotuner times both per product (CSR without
+                              autotuning).  The sums are the same in both layouts when G = 1;
+                              the batched and served forms use CSR */
 } rlsq_factor_opts;
 
 /* Options of a solve. */
@@ -191,6 +197,8 @@ typedef struct {
     int64_t solve_entries[4]; /* stored entries the GPU reads per solve, per system, after level fusion
                                  (substituted and right-hand-side terms; the diagonal of U, U^T
                                  included); bytes_per_iter counts the factor's own entries */
+    int32_t sliced_products;  /* products running in the sliced layout: 1 = A, 2 = A^T, 4 = L2,
+                                 8 = L2^T (bits) */
 } rlsq_info;
 
 /* Server options and statistics (continuous batching of right-hand sides). */

@@ -46,6 +46,7 @@ class FactorOpts(C.Structure):
         ("autotune", C.c_int32), ("dense_row_min", C.c_int64), ("host_threads", C.c_int32),
         ("level_merge", C.c_int32), ("trsv_rows", C.c_int32), ("cg_tol", C.c_double),
         ("dense_host", C.c_int32),
+        ("sliced", C.c_int32),
     ]
 
 
@@ -69,6 +70,7 @@ class Info(C.Structure):
         ("bytes_per_iter", C.c_double), ("solve_levels", C.c_int32 * 4), ("level_merge", C.c_int32 * 4),
         ("trsv_schedule", C.c_int32 * 4), ("ilup_seconds", C.c_double), ("ilup_threads", C.c_int32),
         ("solve_entries", C.c_int64 * 4),
+        ("sliced_products", C.c_int32),
     ]
 
     def as_dict(self):

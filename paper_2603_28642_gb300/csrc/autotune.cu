@@ -55,8 +55,10 @@ int grid_for(const rlsq_problem_s* P, int64_t rows, int G) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * kGridBlocksPerSm))));
 }
 
+// Best CSR lanes for y = M x; with try_sliced, also the sliced layout (when
+// built): *sliced = 1 when it is faster than the best CSR mapping.
 template <typename T>
-int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y) {
+int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y, bool try_sliced, int* sliced) {
     static const int cands[] = {1, 2, 4, 8, 16, 32};
     int best = 8;
     float tbest = 1e30f;
@@ -72,6 +74,13 @@ int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y) {
             tbest = t;
             best = G;
         }
+    }
+    if (try_sliced && M.snpos > 0) {
+        const float t = time_median(P->stream, [&]() {
+            k_csr_mv<T, 0><<<grid_for(P, M.snpos, 1), kBlock, 0, P->stream>>>(M, x, y, nullptr);
+            RLSQ_CUDA(cudaGetLastError());
+        });
+        *sliced = t < tbest ? 1 : 0;
     }
     return best;
 }
@@ -89,8 +98,9 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F, bool schedules) {
     RLSQ_CUDA(cudaMemcpyAsync(F.vm[0].p, ones.data(), sizeof(T) * F.vm[0].n, cudaMemcpyHostToDevice, P->stream));
     RLSQ_CUDA(cudaStreamSynchronize(P->stream));
     if (P->correction != RLSQ_CORR_NONE) {
-        P->map.G_L2 = best_mv_lanes<T>(P, F.L2.view(), F.vn[3].p, F.vm[1].p);
-        P->map.G_L2t = best_mv_lanes<T>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p);
+        const bool try_sl = P->opts.sliced < 0;
+        P->map.G_L2 = best_mv_lanes<T>(P, F.L2.view(), F.vn[3].p, F.vm[1].p, try_sl, &P->map.sl_L2);
+        P->map.G_L2t = best_mv_lanes<T>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p, try_sl, &P->map.sl_L2t);
     }
     if (!schedules) return;
     static const int cands[] = {1, 2, 4, 8, 16, 32};
@@ -184,6 +194,23 @@ static void tune_products(rlsq_problem_s* P) {
             best_t = tt;
             P->map.G_At = G;
         }
+    }
+    if (P->opts.sliced >= 0) return;  // the layout was chosen by the caller
+    if (P->dA.snpos > 0) {
+        const float ta = time_median(P->stream, [&]() {
+            k_spmv_lsmr<0><<<grid_for(P, P->dA.snpos, 1), kBlock, 0, P->stream>>>(
+                P->dA.view(), P->tx.p, P->qr.p, P->b.p, S, P->part.p, P->counter.p);
+            RLSQ_CUDA(cudaGetLastError());
+        });
+        P->map.sl_A = ta < best_a ? 1 : 0;
+    }
+    if (P->dAt.snpos > 0) {
+        const float tt = time_median(P->stream, [&]() {
+            k_spmvt_lsmr<0, false><<<grid_for(P, P->dAt.snpos, 1), kBlock, 0, P->stream>>>(
+                P->dAt.view(), P->qr.p, P->s.p, S, P->part.p, P->counter.p);
+            RLSQ_CUDA(cudaGetLastError());
+        });
+        P->map.sl_At = tt < best_t ? 1 : 0;
     }
 }
 

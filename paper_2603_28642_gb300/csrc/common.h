@@ -77,14 +77,26 @@ struct DevArray {
     }
 };
 
+// Rows per window within which the sliced layout sorts rows by length.
+constexpr int kSliceWindow = 1024;
+
 template <typename T>
 struct DevCsr {
     int32_t rows = 0, cols = 0;
     int64_t nnz = 0;
     DevArray<int32_t> ptr, idx;
     DevArray<T> val;
-    Csr<T> view() const { return Csr<T>{rows, cols, ptr.p, idx.p, val.p}; }
-    void upload(const HostCSR& h, cudaStream_t s);
+    // the sliced layout (Csr::sperm ...), built on request
+    DevArray<int32_t> sperm, sbase, sidx;
+    DevArray<T> sval;
+    int32_t snpos = 0;
+    int64_t sentries = 0;  // stored entries of the sliced layout, padding included
+    Csr<T> view() const {
+        return Csr<T>{rows, cols, ptr.p, idx.p, val.p, sperm.p, sbase.p, sidx.p, sval.p, snpos};
+    }
+    // sliced: also build the sliced layout (kept off when its padded size
+    // would not fit 32-bit offsets)
+    void upload(const HostCSR& h, cudaStream_t s, bool sliced = false);
 };
 
 // Kernel mapping choices for one problem (set by heuristics or the autotuner).
@@ -93,6 +105,9 @@ struct Mapping {
     int G_tri[4] = {4, 4, 4, 4};        // lanes per row: L1, L1^T, U, U^T
     int sched[4] = {RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE, RLSQ_TRSV_SYNCFREE};
     int G_L2 = 4, G_L2t = 4;
+    // the products in the sliced layout (one lane per row) instead of CSR
+    // with G lanes: A, A^T, L2, L2^T
+    int sl_A = 0, sl_At = 0, sl_L2 = 0, sl_L2t = 0;
     int sf_blocks[4] = {2, 2, 2, 2};    // sync-free solve: resident blocks per SM (bounds the polling rows)
     int sf_rows[4] = {0, 0, 0, 0};      // sync-free solve: 0 = block tickets (k_trsv_sentinel); R = 1, 2, 4:
                                         // warp tickets, R rows per lane group (k_trsv_warp)

@@ -191,7 +191,110 @@ struct Csr {
     const int32_t* ptr;
     const int32_t* idx;
     const T* val;
+    // The same matrix sliced for one lane per row (null when not built): the
+    // rows in the order sperm (sorted by length within windows; -1 marks the
+    // padding positions up to snpos, a multiple of 32) form slices of 32
+    // positions; slice q stores its entries column-major from sbase[q]
+    // (entry k of position t at sbase[t / 32] + 32 k + t % 32), its width
+    // (sbase[q + 1] - sbase[q]) / 32 the longest of its rows, shorter rows
+    // padded with index -1.  Every row keeps its CSR entry order.
+    const int32_t* sperm;
+    const int32_t* sbase;
+    const int32_t* sidx;
+    const T* sval;
+    int32_t snpos;
 };
+
+// Dot product of position t's row in the sliced layout with x.  Entries are
+// added in their CSR order, as by one lane of row_dot<1>, so the sums equal
+// the one-lane CSR products bit for bit; a warp walks one slice, every load
+// of the 32 lanes one 128-byte (index) or 256-byte (value) line.
+template <typename TV, typename TX, typename TA>
+__device__ __forceinline__ void sliced_dot(const Csr<TV>& a, int t, const TX* __restrict__ x, TA& s) {
+    const int q = t >> 5;
+    const int e0 = a.sbase[q];
+    const int w = (a.sbase[q + 1] - e0) >> 5;
+    int e = e0 + (t & 31);
+    int k = 0;
+    for (; k + 4 <= w; k += 4, e += 128) {
+        const int j0 = a.sidx[e], j1 = a.sidx[e + 32], j2 = a.sidx[e + 64], j3 = a.sidx[e + 96];
+        const TA a0 = (TA)a.sval[e], a1 = (TA)a.sval[e + 32], a2 = (TA)a.sval[e + 64], a3 = (TA)a.sval[e + 96];
+        const TA x0 = j0 >= 0 ? (TA)x[j0] : (TA)0, x1 = j1 >= 0 ? (TA)x[j1] : (TA)0;
+        const TA x2 = j2 >= 0 ? (TA)x[j2] : (TA)0, x3 = j3 >= 0 ? (TA)x[j3] : (TA)0;
+        if (j0 >= 0) s = fma(a0, x0, s);
+        if (j1 >= 0) s = fma(a1, x1, s);
+        if (j2 >= 0) s = fma(a2, x2, s);
+        if (j3 >= 0) s = fma(a3, x3, s);
+    }
+    if (k < w) {  // the last (< 4) columns of the slice, loads first
+        const bool h1 = k + 1 < w, h2 = k + 2 < w;
+        const int j0 = a.sidx[e], j1 = h1 ? a.sidx[e + 32] : -1, j2 = h2 ? a.sidx[e + 64] : -1;
+        const TA a0 = (TA)a.sval[e], a1 = h1 ? (TA)a.sval[e + 32] : (TA)0, a2 = h2 ? (TA)a.sval[e + 64] : (TA)0;
+        const TA x0 = j0 >= 0 ? (TA)x[j0] : (TA)0, x1 = j1 >= 0 ? (TA)x[j1] : (TA)0;
+        const TA x2 = j2 >= 0 ? (TA)x[j2] : (TA)0;
+        if (j0 >= 0) s = fma(a0, x0, s);
+        if (j1 >= 0) s = fma(a1, x1, s);
+        if (j2 >= 0) s = fma(a2, x2, s);
+    }
+}
+
+// The same against both halves of an interleaved pair vector (p[j].x, p[j].y)
+// (PAIR), or its first halves only.
+template <bool PAIR, typename TV>
+__device__ __forceinline__ void sliced_dot_pair(const Csr<TV>& a, int t, const double2* __restrict__ p,
+                                                double& s1, double& s2) {
+    const double* px = reinterpret_cast<const double*>(p);
+    const int q = t >> 5;
+    const int e0 = a.sbase[q];
+    const int w = (a.sbase[q + 1] - e0) >> 5;
+    int e = e0 + (t & 31);
+    int k = 0;
+    for (; k + 4 <= w; k += 4, e += 128) {
+        int j[4];
+        double v[4];
+        double2 y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = a.sidx[e + 32 * u];
+            v[u] = a.sval[e + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (PAIR) y[u] = j[u] >= 0 ? p[j[u]] : make_double2(0.0, 0.0);
+            else y[u].x = j[u] >= 0 ? px[2 * (size_t)j[u]] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j[u] >= 0) {
+                s1 = fma(v[u], y[u].x, s1);
+                if (PAIR) s2 = fma(v[u], y[u].y, s2);
+            }
+        }
+    }
+    if (k < w) {  // the last (< 4) columns of the slice, loads first
+        int j[3];
+        double v[3];
+        double2 y[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const bool h = k + u < w;
+            j[u] = h ? a.sidx[e + 32 * u] : -1;
+            v[u] = h ? (double)a.sval[e + 32 * u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            if (PAIR) y[u] = j[u] >= 0 ? p[j[u]] : make_double2(0.0, 0.0);
+            else y[u].x = j[u] >= 0 ? px[2 * (size_t)j[u]] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            if (j[u] >= 0) {
+                s1 = fma(v[u], y[u].x, s1);
+                if (PAIR) s2 = fma(v[u], y[u].y, s2);
+            }
+        }
+    }
+}
 
 // group-of-G row dot products against two vectors
 template <int G, typename TV, typename TX, typename TA>
@@ -310,6 +413,32 @@ __device__ __forceinline__ void row_dot_first(const Csr<TV>& a, int row, int lan
     }
 }
 
+// Row epilogue of the A product (shared by the CSR and sliced kernels): s1 =
+// (A t)_row, s2 = (A x_k)_row (when chk); dense rows add their GEMV values.
+__device__ __forceinline__ void spmv_row_out(int row, double s1, double s2, bool chk, double inv_alpha,
+                                             double alpha, double inv_beta, double2* __restrict__ qr,
+                                             const double* __restrict__ b, int ms,
+                                             const double2* __restrict__ dense_av, double (&acc)[2]) {
+    if (dense_av && row >= ms) {
+        const double2 dv = dense_av[row - ms];
+        s1 += dv.x;
+        s2 += dv.y;
+    }
+    const double2 old = qr[row];
+    const double qn = s1 * inv_alpha - alpha * (old.x * inv_beta);
+    const double rr = chk ? b[row] - s2 : old.y;
+    qr[row] = make_double2(qn, rr);
+    acc[0] += qn * qn;
+    if (chk) acc[1] += rr * rr;
+}
+
+__device__ __forceinline__ void spmv_totals(LsmrState* S, const double (&tot)[2], bool chk) {
+    const double beta = sqrt(tot[0]);
+    S->beta = beta;
+    S->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+    if (chk) S->rnorm = sqrt(tot[1]);
+}
+
 // tx[j] = (t_j, x_j): v^ = t * inv_alpha and the current iterate x_k.
 // qr[i] = (q_i, r_i) with u = q * inv_beta.
 // q <- A v^ - alpha u  (= beta_{k+2} u_{k+2}),  r <- b - A x_k
@@ -324,39 +453,64 @@ k_spmv_lsmr(Csr<double> A, const double2* __restrict__ tx, double2* __restrict__
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, alpha = S->alpha, inv_beta = S->inv_beta;
     const bool chk = S->check != 0;  // uniform: form r = b - A x_k as well
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (gridDim.x * kBlock) / G;
     double acc[2] = {0.0, 0.0};
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < A.rows; row += groups) {
-        double s1 = 0.0, s2 = 0.0;
-        if (chk) row_dot_pair<G>(A, row, lane, tx, s1, s2);
-        else row_dot_first<G>(A, row, lane, tx, s1);
-        if (G > 1) {
-            s1 = group_sum<G>(s1, mask);
-            if (chk) s2 = group_sum<G>(s2, mask);
+    if constexpr (G == 0) {  // sliced layout, one lane per row
+        for (int t = blockIdx.x * kBlock + threadIdx.x; t < A.snpos; t += gridDim.x * kBlock) {
+            const int row = A.sperm[t];
+            double s1 = 0.0, s2 = 0.0;
+            if (chk) sliced_dot_pair<true>(A, t, tx, s1, s2);
+            else sliced_dot_pair<false>(A, t, tx, s1, s2);
+            if (row >= 0) spmv_row_out(row, s1, s2, chk, inv_alpha, alpha, inv_beta, qr, b, ms, dense_av, acc);
         }
-        if (lane == 0) {
-            if (dense_av && row >= ms) {
-                const double2 dv = dense_av[row - ms];
-                s1 += dv.x;
-                s2 += dv.y;
+    } else {
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (gridDim.x * kBlock) / G;
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < A.rows; row += groups) {
+            double s1 = 0.0, s2 = 0.0;
+            if (chk) row_dot_pair<G>(A, row, lane, tx, s1, s2);
+            else row_dot_first<G>(A, row, lane, tx, s1);
+            if (G > 1) {
+                s1 = group_sum<G>(s1, mask);
+                if (chk) s2 = group_sum<G>(s2, mask);
             }
-            const double2 old = qr[row];
-            const double qn = s1 * inv_alpha - alpha * (old.x * inv_beta);
-            const double rr = chk ? b[row] - s2 : old.y;
-            qr[row] = make_double2(qn, rr);
-            acc[0] += qn * qn;
-            acc[1] += rr * rr;
+            if (lane == 0) spmv_row_out(row, s1, s2, chk, inv_alpha, alpha, inv_beta, qr, b, ms, dense_av, acc);
         }
     }
     double tot[2];
-    if (last_block_total<2>(acc, part, counter, tot) && threadIdx.x == 0) {
-        const double beta = sqrt(tot[0]);
-        S->beta = beta;
-        S->inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
-        if (chk) S->rnorm = sqrt(tot[1]);
+    if (last_block_total<2>(acc, part, counter, tot) && threadIdx.x == 0) spmv_totals(S, tot, chk);
+}
+
+// Column epilogue of the A^T product (CSR and sliced kernels): s1 = (A^T q)_col,
+// s2 = (A^T r)_col (when chk).
+template <bool FIRST>
+__device__ __forceinline__ void spmvt_row_out(int col, double s1, double s2, bool chk, double inv_alpha,
+                                              double beta, double inv_beta, double* __restrict__ s,
+                                              const double2* __restrict__ dense_atv, double (&acc)[1]) {
+    if (dense_atv) {
+        const double2 dv = dense_atv[col];
+        s1 += dv.x;
+        s2 += dv.y;
     }
+    s[col] = FIRST ? s1 * inv_beta : s1 * inv_beta - beta * (s[col] * inv_alpha);
+    if (chk) acc[0] += s2 * s2;
+}
+
+__device__ __forceinline__ void spmvt_totals(LsmrState* S, const double (&tot)[1], bool chk) {
+    if (chk) {
+        const double arn = sqrt(tot[0]);
+        S->arnorm = arn;
+        const double ratio = S->rnorm > 0.0 ? arn / (S->anorm * S->rnorm) : 0.0;
+        S->ratio = ratio;
+        if (ratio < S->atol) {
+            S->done = 1;
+            S->status = kOk;
+        } else if (S->k >= S->maxit) {
+            S->done = 1;
+            S->status = kErrMaxit;
+        }
+    }
+    S->check = residual_check_next(S);
 }
 
 // s <- A^T q * inv_beta - beta * (s * inv_alpha)      [s of the next apply]
@@ -371,45 +525,32 @@ k_spmvt_lsmr(Csr<double> At, const double2* __restrict__ qr, double* __restrict_
     if (S->done) return;
     const double inv_alpha = S->inv_alpha, beta = S->beta, inv_beta = S->inv_beta;
     const bool chk = FIRST || S->check != 0;  // uniform: form A^T r as well
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (gridDim.x * kBlock) / G;
     double acc[1] = {0.0};
-    for (int col = (blockIdx.x * kBlock + threadIdx.x) / G; col < At.rows; col += groups) {
-        double s1 = 0.0, s2 = 0.0;
-        if (chk) row_dot_pair<G>(At, col, lane, qr, s1, s2);
-        else row_dot_first<G>(At, col, lane, qr, s1);
-        if (G > 1) {
-            s1 = group_sum<G>(s1, mask);
-            if (chk) s2 = group_sum<G>(s2, mask);
+    if constexpr (G == 0) {  // sliced layout, one lane per column
+        for (int t = blockIdx.x * kBlock + threadIdx.x; t < At.snpos; t += gridDim.x * kBlock) {
+            const int col = At.sperm[t];
+            double s1 = 0.0, s2 = 0.0;
+            if (chk) sliced_dot_pair<true>(At, t, qr, s1, s2);
+            else sliced_dot_pair<false>(At, t, qr, s1, s2);
+            if (col >= 0) spmvt_row_out<FIRST>(col, s1, s2, chk, inv_alpha, beta, inv_beta, s, dense_atv, acc);
         }
-        if (lane == 0) {
-            if (dense_atv) {
-                const double2 dv = dense_atv[col];
-                s1 += dv.x;
-                s2 += dv.y;
+    } else {
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (gridDim.x * kBlock) / G;
+        for (int col = (blockIdx.x * kBlock + threadIdx.x) / G; col < At.rows; col += groups) {
+            double s1 = 0.0, s2 = 0.0;
+            if (chk) row_dot_pair<G>(At, col, lane, qr, s1, s2);
+            else row_dot_first<G>(At, col, lane, qr, s1);
+            if (G > 1) {
+                s1 = group_sum<G>(s1, mask);
+                if (chk) s2 = group_sum<G>(s2, mask);
             }
-            s[col] = FIRST ? s1 * inv_beta : s1 * inv_beta - beta * (s[col] * inv_alpha);
-            acc[0] += s2 * s2;
+            if (lane == 0) spmvt_row_out<FIRST>(col, s1, s2, chk, inv_alpha, beta, inv_beta, s, dense_atv, acc);
         }
     }
     double tot[1];
-    if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0 && !FIRST) {
-        if (chk) {
-            const double arn = sqrt(tot[0]);
-            S->arnorm = arn;
-            const double ratio = S->rnorm > 0.0 ? arn / (S->anorm * S->rnorm) : 0.0;
-            S->ratio = ratio;
-            if (ratio < S->atol) {
-                S->done = 1;
-                S->status = kOk;
-            } else if (S->k >= S->maxit) {
-                S->done = 1;
-                S->status = kErrMaxit;
-            }
-        }
-        S->check = residual_check_next(S);
-    }
+    if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0 && !FIRST) spmvt_totals(S, tot, chk);
 }
 
 struct PowerState {
@@ -1379,14 +1520,23 @@ __global__ void __launch_bounds__(kBlock)
 k_csr_mv(Csr<T> M, const T* __restrict__ x, T* __restrict__ y, const LsmrState* S,
          const T* __restrict__ sub = nullptr) {
     if (S && S->done) return;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (gridDim.x * kBlock) / G;
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < M.rows; row += groups) {
-        T s = (T)0;
-        row_dot<G>(M, row, lane, x, s);
-        s = group_sum<G>(s, mask);
-        if (lane == 0) y[row] = sub ? s - sub[row] : s;
+    if constexpr (G == 0) {  // sliced layout
+        for (int t = blockIdx.x * kBlock + threadIdx.x; t < M.snpos; t += gridDim.x * kBlock) {
+            const int row = M.sperm[t];
+            T s = (T)0;
+            sliced_dot(M, t, x, s);
+            if (row >= 0) y[row] = sub ? s - sub[row] : s;
+        }
+    } else {
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (gridDim.x * kBlock) / G;
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < M.rows; row += groups) {
+            T s = (T)0;
+            row_dot<G>(M, row, lane, x, s);
+            s = group_sum<G>(s, mask);
+            if (lane == 0) y[row] = sub ? s - sub[row] : s;
+        }
     }
 }
 
@@ -1396,18 +1546,28 @@ __global__ void __launch_bounds__(kBlock)
 k_l2_start(Csr<T> L2, const T* __restrict__ q1, T* __restrict__ r, LsmrState* S, double* part,
            unsigned* counter, LsmrState* gate, const T* __restrict__ sub = nullptr) {
     if (S->done) return;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (gridDim.x * kBlock) / G;
     double acc[1] = {0.0};
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2.rows; row += groups) {
-        T s = (T)0;
-        row_dot<G>(L2, row, lane, q1, s);
-        s = group_sum<G>(s, mask);
-        if (lane == 0) {
-            if (sub) s -= sub[row];
-            r[row] = s;
-            acc[0] += (double)(s * s);
+    auto out = [&](int row, T s) {
+        if (sub) s -= sub[row];
+        r[row] = s;
+        acc[0] += (double)(s * s);
+    };
+    if constexpr (G == 0) {  // sliced layout
+        for (int t = blockIdx.x * kBlock + threadIdx.x; t < L2.snpos; t += gridDim.x * kBlock) {
+            const int row = L2.sperm[t];
+            T s = (T)0;
+            sliced_dot(L2, t, q1, s);
+            if (row >= 0) out(row, s);
+        }
+    } else {
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (gridDim.x * kBlock) / G;
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2.rows; row += groups) {
+            T s = (T)0;
+            row_dot<G>(L2, row, lane, q1, s);
+            s = group_sum<G>(s, mask);
+            if (lane == 0) out(row, s);
         }
     }
     double tot[1];
@@ -1428,14 +1588,23 @@ k_l2t_cg(Csr<T> L2t, const T* __restrict__ r, const T* __restrict__ p, T* __rest
          const LsmrState* S, const LsmrState* gate) {
     if (S->done || (gate && gate->done)) return;
     const T beta = (T)S->cg_beta;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (gridDim.x * kBlock) / G;
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2t.rows; row += groups) {
-        T s = (T)0;
-        row_dot<G>(L2t, row, lane, r, s);
-        s = group_sum<G>(s, mask);
-        if (lane == 0) c1[row] = FIRST ? s : s + beta * c1[row];
+    if constexpr (G == 0) {  // sliced layout
+        for (int t = blockIdx.x * kBlock + threadIdx.x; t < L2t.snpos; t += gridDim.x * kBlock) {
+            const int row = L2t.sperm[t];
+            T s = (T)0;
+            sliced_dot(L2t, t, r, s);
+            if (row >= 0) c1[row] = FIRST ? s : s + beta * c1[row];
+        }
+    } else {
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (gridDim.x * kBlock) / G;
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2t.rows; row += groups) {
+            T s = (T)0;
+            row_dot<G>(L2t, row, lane, r, s);
+            s = group_sum<G>(s, mask);
+            if (lane == 0) c1[row] = FIRST ? s : s + beta * c1[row];
+        }
     }
     (void)p;
 }
@@ -1447,20 +1616,30 @@ k_l2_sp(Csr<T> L2, const T* __restrict__ c3, const T* __restrict__ r, T* __restr
         T* __restrict__ sp, LsmrState* S, double* part, unsigned* counter, const LsmrState* gate) {
     if (S->done || (gate && gate->done)) return;
     const T beta = (T)S->cg_beta;
-    const unsigned mask = group_mask<G>();
-    const int lane = threadIdx.x & (G - 1);
-    const int groups = (gridDim.x * kBlock) / G;
     double acc[1] = {0.0};
-    for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2.rows; row += groups) {
-        T s = (T)0;
-        row_dot<G>(L2, row, lane, c3, s);
-        s = group_sum<G>(s, mask);
-        if (lane == 0) {
-            const T pv = FIRST ? r[row] : r[row] + beta * p[row];
-            const T spv = pv + s;
-            p[row] = pv;
-            sp[row] = spv;
-            acc[0] += (double)(pv * spv);
+    auto out = [&](int row, T s) {
+        const T pv = FIRST ? r[row] : r[row] + beta * p[row];
+        const T spv = pv + s;
+        p[row] = pv;
+        sp[row] = spv;
+        acc[0] += (double)(pv * spv);
+    };
+    if constexpr (G == 0) {  // sliced layout
+        for (int t = blockIdx.x * kBlock + threadIdx.x; t < L2.snpos; t += gridDim.x * kBlock) {
+            const int row = L2.sperm[t];
+            T s = (T)0;
+            sliced_dot(L2, t, c3, s);
+            if (row >= 0) out(row, s);
+        }
+    } else {
+        const unsigned mask = group_mask<G>();
+        const int lane = threadIdx.x & (G - 1);
+        const int groups = (gridDim.x * kBlock) / G;
+        for (int row = (blockIdx.x * kBlock + threadIdx.x) / G; row < L2.rows; row += groups) {
+            T s = (T)0;
+            row_dot<G>(L2, row, lane, c3, s);
+            s = group_sum<G>(s, mask);
+            if (lane == 0) out(row, s);
         }
     }
     double tot[1];

@@ -32,7 +32,7 @@ void throw_cuda(cudaError_t e, const char* what, int line) {
 }
 
 template <typename T>
-void DevCsr<T>::upload(const HostCSR& h, cudaStream_t s) {
+void DevCsr<T>::upload(const HostCSR& h, cudaStream_t s, bool sliced) {
     rows = static_cast<int32_t>(h.rows);
     cols = static_cast<int32_t>(h.cols);
     nnz = h.nnz();
@@ -45,6 +45,55 @@ void DevCsr<T>::upload(const HostCSR& h, cudaStream_t s) {
     } else {
         std::vector<T> v(h.val.begin(), h.val.end());
         val.upload(v.data(), v.size(), s);
+    }
+    sperm.release();
+    sbase.release();
+    sidx.release();
+    sval.release();
+    snpos = 0;
+    sentries = 0;
+    std::vector<int32_t> perm, base, si;
+    std::vector<T> sv;
+    if (sliced && h.rows > 0) {
+        // positions: rows by decreasing length (ties: lower row first) within
+        // windows of kSliceWindow rows, so that the 32 rows of a slice have
+        // about the same length; -1 pads the last slice
+        const int64_t R = h.rows, nsl = (R + 31) / 32;
+        auto len = [&](int64_t r) { return h.ptr[r + 1] - h.ptr[r]; };
+        perm.assign(static_cast<size_t>(nsl * 32), -1);
+        for (int64_t r = 0; r < R; ++r) perm[r] = static_cast<int32_t>(r);
+        for (int64_t w0 = 0; w0 < R; w0 += kSliceWindow) {
+            const int64_t w1 = std::min<int64_t>(R, w0 + kSliceWindow);
+            std::stable_sort(perm.begin() + w0, perm.begin() + w1,
+                             [&](int32_t a, int32_t b) { return len(a) > len(b); });
+        }
+        std::vector<int64_t> b64(static_cast<size_t>(nsl) + 1, 0);
+        for (int64_t q = 0; q < nsl; ++q) {
+            int64_t w = 0;
+            for (int64_t t = 32 * q; t < 32 * q + 32; ++t)
+                if (perm[t] >= 0) w = std::max(w, len(perm[t]));
+            b64[q + 1] = b64[q] + 32 * w;
+        }
+        if (b64[nsl] < (int64_t(1) << 31)) {
+            base.assign(b64.begin(), b64.end());
+            si.assign(static_cast<size_t>(b64[nsl]), -1);
+            sv.assign(static_cast<size_t>(b64[nsl]), (T)0);
+            for (int64_t t = 0; t < nsl * 32; ++t) {
+                const int32_t r = perm[t];
+                if (r < 0) continue;
+                const int64_t e0 = b64[t >> 5] + (t & 31);
+                for (int64_t k = 0; k < len(r); ++k) {
+                    si[e0 + 32 * k] = h.idx[h.ptr[r] + k];
+                    sv[e0 + 32 * k] = (T)h.val[h.ptr[r] + k];
+                }
+            }
+            sperm.upload(perm.data(), perm.size(), s);
+            sbase.upload(base.data(), base.size(), s);
+            sidx.upload(si.data(), si.size(), s);
+            sval.upload(sv.data(), sv.size(), s);
+            snpos = static_cast<int32_t>(nsl * 32);
+            sentries = b64[nsl];
+        }
     }
     // host vectors die at return: make the copies complete first
     RLSQ_CUDA(cudaStreamSynchronize(s));
@@ -222,8 +271,8 @@ void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const st
             upload_vec(diag[w], dl, s);
         }
     }
-    L2.upload(F.L2, s);
-    L2t.upload(F.L2t, s);
+    L2.upload(F.L2, s, true);
+    L2t.upload(F.L2t, s, true);
     upload_vec(d, F.d, s);
     prow.upload(F.prow.data(), F.prow.size(), s);
     if (!F.a2rows.empty()) a2rows.upload(F.a2rows.data(), F.a2rows.size(), s);
@@ -266,6 +315,25 @@ static void with_G(int G, F&& f) {
         default: f(std::integral_constant<int, 32>{}); break;
     }
 }
+// the same with 0: the sliced layout (products only)
+template <class F>
+static void with_Gp(int G, F&& f) {
+    if (G == 0) f(std::integral_constant<int, 0>{});
+    else with_G(G, f);
+}
+
+// Lanes of a product over M: 0 (sliced) when chosen and built, else the CSR
+// lanes G; and the threads it is launched for (rows x lanes, or the padded
+// positions of the slices).
+template <typename T>
+static int prod_G(int G, int sliced, const DevCsr<T>& M) {
+    return (sliced && M.snpos > 0) ? 0 : G;
+}
+template <typename T>
+static int64_t prod_threads(int G, const DevCsr<T>& M) {
+    return G == 0 ? static_cast<int64_t>(M.snpos) : static_cast<int64_t>(M.rows) * G;
+}
+
 template <class F>
 static void with_rhs(int k, F&& f) {
     switch (k) {
@@ -526,8 +594,11 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
         T* q1 = F.vn[2].p;
         launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{g2, nullptr, nullptr}, q1, slot++, S, st);  // L1^{-1}
         const Csr<T> L2 = F.L2.view(), L2t = F.L2t.view();
-        const int gl2 = grid_rows(P, m2, P->map.G_L2), gl2t = grid_rows_wide(P, n, P->map.G_L2t);
-        const int gl2w = grid_rows_wide(P, m2, P->map.G_L2);
+        // lanes of the L2 / L2^T products (0: sliced layout) and their grids
+        const int GL2 = prod_G(P->map.G_L2, P->map.sl_L2, F.L2), GL2t = prod_G(P->map.G_L2t, P->map.sl_L2t, F.L2t);
+        const int gl2 = grid_rows(P, prod_threads(GL2, F.L2), 1);
+        const int gl2t = grid_rows_wide(P, prod_threads(GL2t, F.L2t), 1);
+        const int gl2w = grid_rows_wide(P, prod_threads(GL2, F.L2), 1);
         const int gv = grid_rows(P, m2, 1);
         T* wv = nullptr;
         if (P->correction == RLSQ_CORR_CG) {
@@ -538,7 +609,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
             const double tol2 = P->opts.cg_tol * P->opts.cg_tol;
             {
                 RecScope rs(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
-                with_G(P->map.G_L2, [&](auto g) {
+                with_Gp(GL2, [&](auto g) {
                     k_l2_start<T, decltype(g)::value><<<gl2, kBlock, 0, st>>>(L2, q1, rv, S, P->part.p,
                                                                               P->counter.p, gate, sub);
                 });
@@ -547,7 +618,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
                 const bool first = (it == 0);
                 {
                     RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, sizeof(T), sizeof(T)), st);
-                    with_G(P->map.G_L2t, [&](auto g) {
+                    with_Gp(GL2t, [&](auto g) {
                         constexpr int GG = decltype(g)::value;
                         if (first) k_l2t_cg<T, GG, true><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S, gate);
                         else k_l2t_cg<T, GG, false><<<gl2t, kBlock, 0, st>>>(L2t, rv, pv, c1, S, gate);
@@ -556,7 +627,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
                 launch_trsv<T>(P, F, 1, RHS_VEC, Rhs<T>{c1, nullptr, nullptr}, c2, slot++, S, st, gate);
                 launch_trsv<T>(P, F, 0, RHS_VEC, Rhs<T>{c2, nullptr, nullptr}, c3, slot++, S, st, gate);
                 RecScope rs2(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
-                with_G(P->map.G_L2, [&](auto g) {
+                with_Gp(GL2, [&](auto g) {
                     constexpr int GG = decltype(g)::value;
                     if (first)
                         k_l2_sp<T, GG, true><<<gl2, kBlock, 0, st>>>(L2, c3, rv, pv, sp, S, P->part.p,
@@ -578,7 +649,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
             T* e = F.vm[0].p;
             {
                 RecScope rs(P, RLSQ_KCLASS_L2, mv_bytes(F.L2, sizeof(T), sizeof(T)), st);
-                with_G(P->map.G_L2, [&](auto g) {
+                with_Gp(GL2, [&](auto g) {
                     k_csr_mv<T, decltype(g)::value><<<gl2w, kBlock, 0, st>>>(L2, q1, e, S, sub);
                 });
             }
@@ -594,7 +665,7 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
         T* y = F.vn[4].p;
         {
             RecScope rs(P, RLSQ_KCLASS_L2T, mv_bytes(F.L2t, sizeof(T), sizeof(T)), st);
-            with_G(P->map.G_L2t, [&](auto g) {
+            with_Gp(GL2t, [&](auto g) {
                 k_csr_mv<T, decltype(g)::value><<<gl2t, kBlock, 0, st>>>(L2t, wv, f, S);
             });
         }
@@ -643,8 +714,9 @@ static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, 
     }
     {
         RecScope rs(P, RLSQ_KCLASS_SPMV, mv_bytes(P->dA, 8.0, 8.0), st);
-        with_G(P->map.G_A, [&](auto g) {
-            k_spmv_lsmr<decltype(g)::value><<<grid_rows(P, m, decltype(g)::value), kBlock, 0, st>>>(
+        const int GA = prod_G(P->map.G_A, P->map.sl_A, P->dA);
+        with_Gp(GA, [&](auto g) {
+            k_spmv_lsmr<decltype(g)::value><<<grid_rows(P, prod_threads(GA, P->dA), 1), kBlock, 0, st>>>(
                 P->dA.view(), P->tx.p, P->qr.p, P->b.p, S, P->part.p, P->counter.p, static_cast<int>(P->ms),
                 dense ? P->dense_av.p : nullptr);
         });
@@ -655,11 +727,12 @@ static void enqueue_iteration(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, 
     }
     {
         RecScope rs(P, RLSQ_KCLASS_SPMVT, mv_bytes(P->dAt, 8.0, 8.0), st);
-        with_G(P->map.G_At, [&](auto g) {
+        const int GAt = prod_G(P->map.G_At, P->map.sl_At, P->dAt);
+        with_Gp(GAt, [&](auto g) {
             k_spmvt_lsmr<decltype(g)::value, false>
-                <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
-                                                                        P->part.p, P->counter.p,
-                                                                        dense ? P->dense_atv.p : nullptr);
+                <<<grid_rows(P, prod_threads(GAt, P->dAt), 1), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p,
+                                                                               S, P->part.p, P->counter.p,
+                                                                               dense ? P->dense_atv.p : nullptr);
         });
     }
     enqueue_apply_any<false>(P, P->s.p, S, st, plain);
@@ -672,11 +745,12 @@ static void enqueue_start(rlsq_problem_s* P, LsmrState* S, cudaStream_t st, bool
     k_start_b<0><<<grid_rows(P, m, 1), kBlock, 0, st>>>(m, P->b.p, P->qr.p, S, P->part.p, P->counter.p);
     const bool dense = P->md > 0;
     if (dense) enqueue_dense_atv<true>(P, P->qr.p + P->ms, S, st);
-    with_G(P->map.G_At, [&](auto g) {
+    const int GAt = prod_G(P->map.G_At, P->map.sl_At, P->dAt);
+    with_Gp(GAt, [&](auto g) {
         k_spmvt_lsmr<decltype(g)::value, true>
-            <<<grid_rows(P, n, decltype(g)::value), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
-                                                                    P->part.p, P->counter.p,
-                                                                    dense ? P->dense_atv.p : nullptr);
+            <<<grid_rows(P, prod_threads(GAt, P->dAt), 1), kBlock, 0, st>>>(P->dAt.view(), P->qr.p, P->s.p, S,
+                                                                           P->part.p, P->counter.p,
+                                                                           dense ? P->dense_atv.p : nullptr);
     });
     enqueue_apply_any<true>(P, P->s.p, S, st, plain);
     k_lsmr_update<true><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, P->tx.p, P->h.p, P->hb.p, S);
@@ -849,6 +923,16 @@ static void fill_factor_info(const rlsq_problem_s* P, rlsq_info* info) {
         info->solve_entries[w] = P->merged[w].T.nnz() + P->merged[w].R.nnz() + (w >= 2 ? P->n : 0);
     }
     info->bytes_per_iter = algorithmic_bytes(P, !P->factored);
+    int sl = 0;
+    if (prod_G(1, P->map.sl_A, P->dA) == 0) sl |= 1;
+    if (prod_G(1, P->map.sl_At, P->dAt) == 0) sl |= 2;
+    if (P->factored) {
+        const bool f32 = P->precision == RLSQ_PREC_FP32;
+        const int32_t np2 = f32 ? P->f32.L2.snpos : P->f64.L2.snpos, np2t = f32 ? P->f32.L2t.snpos : P->f64.L2t.snpos;
+        if (P->map.sl_L2 && np2 > 0) sl |= 4;
+        if (P->map.sl_L2t && np2t > 0) sl |= 8;
+    }
+    info->sliced_products = sl;
 }
 
 // b (user row order) -> P->b (internal row order: dense rows last)
@@ -984,8 +1068,8 @@ static void layout_A(rlsq_problem_s* P, int64_t threshold) {
         P->row_perm.clear();
         P->row_perm_d.release();
         P->Ad.release();
-        P->dA.upload(A, st);
-        P->dAt.upload(transpose(A, ilup_threads(0, A.rows, A.cols)), st);
+        P->dA.upload(A, st, true);
+        P->dAt.upload(transpose(A, ilup_threads(0, A.rows, A.cols)), st, true);
         return;
     }
     std::vector<char> is_dense(static_cast<size_t>(m), 0);
@@ -1007,8 +1091,8 @@ static void layout_A(rlsq_problem_s* P, int64_t threshold) {
         S.ptr[i + 1] = static_cast<int64_t>(S.idx.size());
     }
     for (int64_t i = P->ms; i < m; ++i) S.ptr[i + 1] = S.ptr[i];
-    P->dA.upload(S, st);
-    P->dAt.upload(transpose(S, ilup_threads(0, S.rows, S.cols)), st);
+    P->dA.upload(S, st, true);
+    P->dAt.upload(transpose(S, ilup_threads(0, S.rows, S.cols)), st, true);
     std::vector<double> ad(static_cast<size_t>(P->md * n), 0.0);
     for (int64_t q = 0; q < P->md; ++q) {
         const int32_t r = dense[q];
@@ -1182,6 +1266,7 @@ void rlsq_factor_opts_default(rlsq_factor_opts* o) {
     o->dense_row_min = 0;
     o->host_threads = 0;
     o->level_merge = 0;
+    o->sliced = -1;
 }
 
 void rlsq_solve_opts_default(rlsq_solve_opts* o) {
@@ -1300,6 +1385,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         if (opts.trsv_rows != 0 && opts.trsv_rows != 1 && opts.trsv_rows != 2 && opts.trsv_rows != 4)
             throw ApiError(RLSQ_ERR_ARG, "trsv_rows must be 0, 1, 2 or 4");
         if (!(opts.cg_tol >= 0.0 && opts.cg_tol < 1.0)) throw ApiError(RLSQ_ERR_ARG, "cg_tol must be in [0, 1)");
+        if (opts.sliced < -1 || opts.sliced > 1) throw ApiError(RLSQ_ERR_ARG, "sliced must be -1, 0 or 1");
         const auto t0 = std::chrono::steady_clock::now();
         h->factored = false;
         drop_graphs(h);
@@ -1442,6 +1528,7 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         h->correction = corr;
         h->precision = opts.precision;
         default_mapping(h);
+        h->map.sl_A = h->map.sl_At = h->map.sl_L2 = h->map.sl_L2t = (opts.sliced == 1) ? 1 : 0;
         if (opts.trsv_schedule == RLSQ_TRSV_LEVEL || opts.trsv_schedule == RLSQ_TRSV_SYNCFREE ||
             opts.trsv_schedule == RLSQ_TRSV_COOP || opts.trsv_schedule == RLSQ_TRSV_WAVE ||
             opts.trsv_schedule == RLSQ_TRSV_BINNED)
