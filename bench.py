@@ -77,7 +77,7 @@ MEASURED_TRAFFIC = {("trsv_L1", 5): 2 * 52.80e6}
 CLASS_SYSTEM = {"trsv_L1": 0, "trsv_L1t": 1, "trsv_U": 2, "trsv_Ut": 3}
 # solves per iteration of each triangular-solve class with CG(k): L1 and L1^T
 # once each around the correction and once per CG step; U and U^T once
-CLASS_SOLVES = {"trsv_L1": FACTOR["cg_steps"] + 2, "trsv_L1t": FACTOR["cg_steps"] + 2, "trsv_U": 1, "trsv_Ut": 1}
+CLASS_SOLVES = {"trsv_L1": FACTOR["cg_steps"] + 1, "trsv_L1t": FACTOR["cg_steps"] + 1, "trsv_U": 1, "trsv_Ut": 1}
 
 
 def finfo_ms_per_iter(P, prob):

@@ -77,7 +77,7 @@ struct BSlot {
     double* s;
     double* h;
     double* hb;
-    T* vn[5];
+    T* vn[6];
     T* vm[4];
     LsmrState* S;
     double* part;
@@ -462,7 +462,7 @@ kb_l2_sp(const BSlot<T>* slots, const int32_t* phase, int want, int it, int cap)
         const unsigned mask = group_mask<G>();
         const int lane = threadIdx.x & (G - 1);
         const int groups = (own * kBlock) / G;
-        const T* c3 = D->vn[2];
+        const T* c3 = D->vn[5];
         const T* r = D->vm[0];
         T* p = D->vm[1];
         T* sp = D->vm[2];
@@ -492,21 +492,31 @@ __global__ void __launch_bounds__(kBlock)
 kb_cg_update(const BSlot<T>* slots, const int32_t* phase, int want, int it, int cap) {
     const BSlot<T>* D = gate(slots, phase, want, C_CG);
     if (!D || it >= D->cg_steps) return;
-    const int own = own_blocks(D->m2, 1, cap);
+    const int len = D->m2 > D->n ? D->m2 : D->n;
+    const int own = own_blocks(len, 1, cap);
     if ((int)blockIdx.x >= own) return;
     LsmrState* S = D->S;
     const T a = (T)S->cg_a;
     const T* p = D->vm[1];
     const T* sp = D->vm[2];
     T* r = D->vm[0];
-    T* w = D->vm[3];
+    // z = sum_j a_j c3_j in vn[0] (as k_cg_update); after the last step vn[0]
+    // holds q1 - z, the input of the U solve
+    const T* c3 = D->vn[5];
+    const T* q1 = D->vn[2];
+    T* z = D->vn[0];
+    const bool last = it + 1 == D->cg_steps;
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < D->m2; i += own * kBlock) {
-        const T pi = p[i];
-        w[i] = FIRST ? a * pi : w[i] + a * pi;
-        const T ri = r[i] - a * sp[i];
-        r[i] = ri;
-        acc[0] += (double)(ri * ri);
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += own * kBlock) {
+        if (i < D->m2) {
+            const T ri = r[i] - a * sp[i];
+            r[i] = ri;
+            acc[0] += (double)(ri * ri);
+        }
+        if (i < D->n) {
+            const T zi = FIRST ? a * c3[i] : z[i] + a * c3[i];
+            z[i] = last ? q1[i] - zi : zi;
+        }
     }
     double tot[1];
     if (last_block_total_ctx<1>(acc, D->part, D->counter, tot, blockIdx.x, own) && threadIdx.x == 0) {
@@ -607,7 +617,7 @@ template <typename T>
 struct SlotBuffers {
     DevArray<double2> qr, tx;
     DevArray<double> b, s, h, hb, part;
-    DevArray<T> vn[5], vm[4];
+    DevArray<T> vn[6], vm[4];
     DevArray<LsmrState> S;
     DevArray<unsigned> counter;
     int64_t cap_m = 0, cap_n = 0, cap_m2 = 0;
@@ -752,12 +762,12 @@ struct Engine {
         D.sinv = F.sinv.p;
         if (own) {
             D.qr = own->qr.p; D.tx = own->tx.p; D.b = own->b.p; D.s = own->s.p; D.h = own->h.p; D.hb = own->hb.p;
-            for (int i = 0; i < 5; ++i) D.vn[i] = own->vn[i].p;
+            for (int i = 0; i < 6; ++i) D.vn[i] = own->vn[i].p;
             for (int i = 0; i < 4; ++i) D.vm[i] = own->vm[i].p;
             D.S = own->S.p; D.part = own->part.p; D.counter = own->counter.p;
         } else {
             D.qr = P->qr.p; D.tx = P->tx.p; D.b = P->b.p; D.s = P->s.p; D.h = P->h.p; D.hb = P->hb.p;
-            for (int i = 0; i < 5; ++i) D.vn[i] = F.vn[i].p;
+            for (int i = 0; i < 6; ++i) D.vn[i] = F.vn[i].p;
             for (int i = 0; i < 4; ++i) D.vm[i] = F.vm[i].p;
             D.S = P->S.p; D.part = P->part.p; D.counter = P->counter.p;
         }
@@ -830,13 +840,13 @@ struct Engine {
                     else
                         kb_l2t_cg<T, false><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                     trsv(want, C_CG, 1, RHS_VEC, 3, 0, 4);
-                    trsv(want, C_CG, 0, RHS_VEC, 4, 0, 2);
+                    trsv(want, C_CG, 0, RHS_VEC, 4, 0, 5);
                     if (it == 0) {
                         kb_l2_sp<T, true><<<dim3(gx(max_m2, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
-                        kb_cg_update<T, true><<<dim3(gx(max_m2, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
+                        kb_cg_update<T, true><<<dim3(gx(std::max(max_m2, max_n), 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                     } else {
                         kb_l2_sp<T, false><<<dim3(gx(max_m2, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
-                        kb_cg_update<T, false><<<dim3(gx(max_m2, 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
+                        kb_cg_update<T, false><<<dim3(gx(std::max(max_m2, max_n), 1), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, it, cap);
                     }
                 }
             }
@@ -845,9 +855,13 @@ struct Engine {
                 if (any_dense)
                     kb_dense_gemv<T><<<dim3(gx(max_m2, 32), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want);
             }
-            kb_csr_mv<T><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, C_CORR, 1, SEL_W, 3, cap);
-            trsv(want, C_CORR, 1, RHS_VEC, 3, 0, 4);  // L1^{-T} Y^T w -> vn4
-            trsv(want, C_CORR, 0, RHS_SUB, 1, 4, 0);  // L1^{-1}(g2 - .) -> vn0
+            // S^ = I or dense: Algorithm 3's steps 3-4; the CG slots already hold
+            // L1^{-1}(g2 - L1^{-T} L2^T w) = q1 - z in vn0 (kb_cg_update)
+            if (any_e) {
+                kb_csr_mv<T><<<dim3(gx(max_n, kBG_Max), ns), kBlock, 0, st>>>(d_slots.p, d_phase.p, want, C_E, 1, SEL_W, 3, cap);
+                trsv(want, C_E, 1, RHS_VEC, 3, 0, 4);  // L1^{-T} Y^T w -> vn4
+                trsv(want, C_E, 0, RHS_SUB, 1, 4, 0);  // L1^{-1}(g2 - .) -> vn0
+            }
         }
         if (any_none) trsv(want, C_NOCORR, 0, RHS_VEC, 1, 0, 0);
         trsv(want, C_ALL, 2, RHS_VEC, 0, 0, 2);  // U^{-1} -> vn2

@@ -139,7 +139,7 @@ struct DevFactor {
     DevArray<T> d;
     DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
     DevArray<int32_t> prow, a2rows;  // rows of A1 (by position) and of A2: Algorithm 3's input split
-    DevArray<T> vn[5], vm[4];  // work vectors
+    DevArray<T> vn[6], vm[4];  // work vectors
     void upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h, cudaStream_t s);
     void clear() {
         for (int w = 0; w < 4; ++w) {

@@ -1652,19 +1652,32 @@ k_l2_sp(Csr<T> L2, const T* __restrict__ c3, const T* __restrict__ r, T* __restr
 // w += a p (FIRST: w = a p); r -= a Sp; totals: beta = rr' / rr.  With a
 // gate (adaptive steps): once rr' <= tol2 rr_0 the gate is closed and the
 // kernels of the remaining CG steps return at once.
+//
+// With z (n entries): z += a c3 (FIRST: z = a c3) instead of the w update,
+// c3 = L1^{-1} L1^{-T} L2^T p being this step's direction carried through
+// both solves.  Since w = sum_j a_j p_j, z = L1^{-1} L1^{-T} L2^T w, the
+// term Algorithm 3 forms from w with one more L2^T product and two more
+// solves (steps 3-4); w itself is then not needed (w == nullptr).
 template <typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock)
 k_cg_update(int m2, const T* __restrict__ p, const T* __restrict__ sp, T* __restrict__ r,
-            T* __restrict__ w, LsmrState* S, double* part, unsigned* counter, LsmrState* gate, double tol2) {
+            T* __restrict__ w, LsmrState* S, double* part, unsigned* counter, LsmrState* gate, double tol2,
+            int n = 0, const T* __restrict__ c3 = nullptr, T* __restrict__ z = nullptr) {
     if (S->done || (gate && gate->done)) return;
     const T a = (T)S->cg_a;
     double acc[1] = {0.0};
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < m2; i += gridDim.x * kBlock) {
-        const T pi = p[i];
-        w[i] = FIRST ? a * pi : w[i] + a * pi;
-        const T ri = r[i] - a * sp[i];
-        r[i] = ri;
-        acc[0] += (double)(ri * ri);
+    const int len = m2 > n ? m2 : n;
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < len; i += gridDim.x * kBlock) {
+        if (i < m2) {
+            if (w) {
+                const T pi = p[i];
+                w[i] = FIRST ? a * pi : w[i] + a * pi;
+            }
+            const T ri = r[i] - a * sp[i];
+            r[i] = ri;
+            acc[0] += (double)(ri * ri);
+        }
+        if (i < n) z[i] = FIRST ? a * c3[i] : z[i] + a * c3[i];
     }
     double tot[1];
     if (last_block_total<1>(acc, part, counter, tot) && threadIdx.x == 0) {

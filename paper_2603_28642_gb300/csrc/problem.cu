@@ -599,11 +599,16 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
         const int gl2 = grid_rows(P, prod_threads(GL2, F.L2), 1);
         const int gl2t = grid_rows_wide(P, prod_threads(GL2t, F.L2t), 1);
         const int gl2w = grid_rows_wide(P, prod_threads(GL2, F.L2), 1);
-        const int gv = grid_rows(P, m2, 1);
+        const int gv = grid_rows(P, std::max(m2, n), 1);
         T* wv = nullptr;
         if (P->correction == RLSQ_CORR_CG) {
-            T *rv = F.vm[0].p, *pv = F.vm[1].p, *sp = F.vm[2].p, *w = F.vm[3].p;
-            T *c1 = F.vn[3].p, *c2 = F.vn[4].p, *c3 = F.vn[2].p;
+            // CG(k) on S^ w = e.  Each step carries its direction p through L2^T,
+            // L1^{-T} and L1^{-1} (c3); z = sum_j a_j c3_j is then L1^{-1}
+            // L1^{-T} L2^T w, so L1^{-1}(g2 - L1^{-T} L2^T w) = q1 - z and the
+            // apply ends with U^{-1}(q1 - z): Algorithm 3's steps 3-4 without
+            // their L2^T product and two solves (linearity in w; w is not formed).
+            T *rv = F.vm[0].p, *pv = F.vm[1].p, *sp = F.vm[2].p;
+            T *c1 = F.vn[3].p, *c2 = F.vn[4].p, *c3 = F.vn[5].p, *z = F.vn[0].p;
             // adaptive number of CG steps: a gate the remaining steps check
             LsmrState* gate = P->opts.cg_tol > 0.0 ? state_ptr(P, 2) : nullptr;
             const double tol2 = P->opts.cg_tol * P->opts.cg_tol;
@@ -636,15 +641,21 @@ static void enqueue_apply(rlsq_problem_s* P, DevFactor<T>& F, const double* s, L
                         k_l2_sp<T, GG, false><<<gl2, kBlock, 0, st>>>(L2, c3, rv, pv, sp, S, P->part.p,
                                                                       P->counter.p, gate);
                 });
-                RecScope rs3(P, RLSQ_KCLASS_VEC, (first ? 4.0 : 5.0) * sizeof(T) * m2, st);
+                RecScope rs3(P, RLSQ_KCLASS_VEC, sizeof(T) * (4.0 * m2 + (first ? 2.0 : 3.0) * n), st);
                 if (first)
-                    k_cg_update<T, true><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, w, S, P->part.p,
-                                                                P->counter.p, gate, tol2);
+                    k_cg_update<T, true><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, nullptr, S, P->part.p,
+                                                                P->counter.p, gate, tol2, n, c3, z);
                 else
-                    k_cg_update<T, false><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, w, S, P->part.p,
-                                                                 P->counter.p, gate, tol2);
+                    k_cg_update<T, false><<<gv, kBlock, 0, st>>>(m2, pv, sp, rv, nullptr, S, P->part.p,
+                                                                 P->counter.p, gate, tol2, n, c3, z);
             }
-            wv = w;
+            // U^{-1}(q1 - z), then t = D g5
+            T* g5 = F.vn[1].p;
+            launch_trsv<T>(P, F, 2, RHS_SUB, Rhs<T>{q1, z, nullptr}, g5, slot++, S, st);
+            RecScope rs(P, RLSQ_KCLASS_FINISH, (2.0 * sizeof(T) + 16.0) * n, st);
+            k_finish_apply<T, INIT, false, CGLS><<<grid_rows(P, n, 1), kBlock, 0, st>>>(n, F.d.p, g5, s, P->tx.p,
+                                                                                        S, P->part.p, P->counter.p);
+            return;
         } else {
             T* e = F.vm[0].p;
             {
@@ -888,8 +899,10 @@ static double algorithmic_bytes(const rlsq_problem_s* P, bool plain) {
         c_l2 = 2;
         if (P->correction == RLSQ_CORR_DENSE) dense = wv * m2 * m2;
     } else if (P->correction == RLSQ_CORR_CG) {
-        c_l1 = 4 + 2 * k;
-        c_l2 = 2 + 2 * k;
+        // L1^{-T}, L1^{-1} before the correction and two per CG step; L2 once,
+        // then L2^T and L2 per step (the apply ends with U^{-1}(q1 - z))
+        c_l1 = 2 + 2 * k;
+        c_l2 = 1 + 2 * k;
     }
     return bytes + 2.0 * tri_u + c_l1 * tri_l1 + c_l2 * l2 + dense;
 }
