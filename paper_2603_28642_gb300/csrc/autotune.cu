@@ -55,18 +55,32 @@ int grid_for(const rlsq_problem_s* P, int64_t rows, int G) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * kGridBlocksPerSm))));
 }
 
-// Best CSR lanes for y = M x; with try_sliced, also the sliced layout (when
-// built): *sliced = 1 when it is faster than the best CSR mapping.
-template <typename T>
-int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y, bool try_sliced, int* sliced) {
+// the grid of kernels without a grid-wide reduction (as the apply launches them)
+int grid_for_wide(const rlsq_problem_s* P, int64_t rows, int G) {
+    const int64_t g = (rows * G + kBlock - 1) / kBlock;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(g, std::max(1, P->num_sms * 32))));
+}
+
+// Best CSR lanes of the L2 (L2T = false) or L2^T product, timed with the
+// CG kernels the apply runs (k_l2_start, with its epilogue and reduction,
+// for L2; k_l2t_cg for L2^T) on a scratch state; with try_sliced, also the
+// sliced layout (when built): *sliced = 1 when it beats the best CSR lanes.
+template <typename T, bool L2T>
+int best_l2_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y, LsmrState* S, bool try_sliced,
+                  int* sliced) {
     static const int cands[] = {1, 2, 4, 8, 16, 32};
+    auto launch = [&](auto g, int grid) {
+        constexpr int GG = decltype(g)::value;
+        if (L2T) k_l2t_cg<T, GG, false><<<grid, kBlock, 0, P->stream>>>(M, x, nullptr, y, S, nullptr);
+        else k_l2_start<T, GG><<<grid, kBlock, 0, P->stream>>>(M, x, y, S, P->part.p, P->counter.p, nullptr);
+    };
     int best = 8;
     float tbest = 1e30f;
     for (int G : cands) {
         const float t = time_median(P->stream, [&]() {
             with_lanes(G, [&](auto g) {
-                k_csr_mv<T, decltype(g)::value><<<grid_for(P, M.rows, decltype(g)::value), kBlock, 0, P->stream>>>(
-                    M, x, y, nullptr);
+                constexpr int GG = decltype(g)::value;
+                launch(g, L2T ? grid_for_wide(P, M.rows, GG) : grid_for(P, M.rows, GG));
             });
             RLSQ_CUDA(cudaGetLastError());
         });
@@ -77,12 +91,25 @@ int best_mv_lanes(rlsq_problem_s* P, const Csr<T>& M, const T* x, T* y, bool try
     }
     if (try_sliced && M.snpos > 0) {
         const float t = time_median(P->stream, [&]() {
-            k_csr_mv<T, 0><<<grid_for(P, M.snpos, 1), kBlock, 0, P->stream>>>(M, x, y, nullptr);
+            launch(std::integral_constant<int, 0>{}, L2T ? grid_for_wide(P, M.snpos, 1) : grid_for(P, M.snpos, 1));
             RLSQ_CUDA(cudaGetLastError());
         });
         *sliced = t < tbest ? 1 : 0;
     }
     return best;
+}
+
+// A scratch LSMR state that no kernel stops on (for timing).
+static LsmrState* scratch_state(rlsq_problem_s* P) {
+    LsmrState* S = P->S.p + 1;
+    LsmrState h;
+    std::memset(&h, 0, sizeof(h));
+    h.alpha = h.inv_alpha = h.beta = h.inv_beta = 1.0;
+    h.anorm = 1.0;
+    h.atol = -1.0;  // the stopping test never fires while timing
+    h.maxit = 0x7fffffff;
+    RLSQ_CUDA(cudaMemcpy(S, &h, sizeof(h), cudaMemcpyHostToDevice));
+    return S;
 }
 
 }  // namespace
@@ -99,8 +126,9 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F, bool schedules) {
     RLSQ_CUDA(cudaStreamSynchronize(P->stream));
     if (P->correction != RLSQ_CORR_NONE) {
         const bool try_sl = P->opts.sliced < 0;
-        P->map.G_L2 = best_mv_lanes<T>(P, F.L2.view(), F.vn[3].p, F.vm[1].p, try_sl, &P->map.sl_L2);
-        P->map.G_L2t = best_mv_lanes<T>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p, try_sl, &P->map.sl_L2t);
+        LsmrState* S = scratch_state(P);
+        P->map.G_L2 = best_l2_lanes<T, false>(P, F.L2.view(), F.vn[3].p, F.vm[1].p, S, try_sl, &P->map.sl_L2);
+        P->map.G_L2t = best_l2_lanes<T, true>(P, F.L2t.view(), F.vm[0].p, F.vn[4].p, S, try_sl, &P->map.sl_L2t);
     }
     if (!schedules) return;
     static const int cands[] = {1, 2, 4, 8, 16, 32};
@@ -157,14 +185,7 @@ static void tune_factor(rlsq_problem_s* P, DevFactor<T>& F, bool schedules) {
 // kernels write only the work vectors, which a solve re-initialises).
 static void tune_products(rlsq_problem_s* P) {
     static const int cands[] = {1, 2, 4, 8, 16, 32};
-    LsmrState* S = P->S.p + 1;
-    LsmrState h;
-    std::memset(&h, 0, sizeof(h));
-    h.alpha = h.inv_alpha = h.beta = h.inv_beta = 1.0;
-    h.anorm = 1.0;
-    h.atol = -1.0;             // the stopping test never fires while timing
-    h.maxit = 0x7fffffff;
-    RLSQ_CUDA(cudaMemcpy(S, &h, sizeof(h), cudaMemcpyHostToDevice));
+    LsmrState* S = scratch_state(P);
     RLSQ_CUDA(cudaMemsetAsync(P->tx.p, 0, sizeof(double2) * P->n, P->stream));
     RLSQ_CUDA(cudaMemsetAsync(P->qr.p, 0, sizeof(double2) * P->m, P->stream));
     RLSQ_CUDA(cudaMemsetAsync(P->b.p, 0, sizeof(double) * P->m, P->stream));
