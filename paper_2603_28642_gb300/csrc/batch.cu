@@ -642,7 +642,7 @@ struct SlotBuffers {
 // per-slot footprint of the LSMR state (vectors and scratch) in bytes
 int64_t state_bytes(int64_t m, int64_t n, int64_t m2, int prec) {
     const int64_t w = prec == RLSQ_PREC_FP32 ? 4 : 8;
-    return 16 * m + 16 * n + 8 * m + 24 * n + 5 * w * n + 4 * w * std::max<int64_t>(m2, 1) + 4096;
+    return 16 * m + 16 * n + 8 * m + 24 * n + 6 * w * n + 4 * w * std::max<int64_t>(m2, 1) + 4096;
 }
 
 template <typename T>

@@ -171,7 +171,7 @@ def test_server_admission_under_small_budget(served):
     probs, hs = served
     # a budget for one request of the largest matrix at a time
     big = max(probs, key=lambda p: p.n)
-    budget = 16 * big.m + 16 * big.n + 8 * big.m + 24 * big.n + 40 * big.n + 32 * (big.m - big.n) + 8192
+    budget = 16 * big.m + 16 * big.n + 8 * big.m + 24 * big.n + 48 * big.n + 32 * (big.m - big.n) + 8192
     srv = B.Server(hbm_budget_bytes=budget, max_slots=4)
     ids = [srv.register(P) for P in hs]
     jobs = [(ids[k % 3], synth.serving_rhs(probs[k % 3], 100 + k)) for k in range(6)]
