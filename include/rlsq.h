@@ -168,8 +168,8 @@ typedef struct {
     int32_t ptr_mode;    /* RLSQ_HOST_PTRS or RLSQ_DEVICE_PTRS for b and x */
     void *stream;        /* cudaStream_t */
     int32_t check_every; /* iterations per captured CUDA graph between host checks (>= 1) */
-    int32_t solver;      /* RLSQ_SOLVER_*; stopping test the same for both (the CGLS residual is the
-                            recurrence one of Algorithm 1) */
+    int32_t solver;      /* RLSQ_SOLVER_*; the same stopping test for every solver (the CGLS forms use
+                            the recurrence residual of Algorithm 1) */
 } rlsq_solve_opts;
 
 /* Result and statistics of a factorisation / solve. */
