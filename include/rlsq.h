@@ -157,8 +157,8 @@ typedef struct {
                               per row; rows sorted by length within windows of 1024, slices of
                               32 rows stored column-major), 0 = CSR with G lanes per row,
                               -1 (default) = the autotuner times both per product (CSR without
-                              autotuning).  The sums are the same in both layouts when G = 1;
-                              the batched and served forms use CSR */
+                              autotuning; the sliced copies are then not built).  The sums are the
+                              same in both layouts when G = 1; the batched and served forms use CSR */
 } rlsq_factor_opts;
 
 /* Options of a solve. */

@@ -140,7 +140,9 @@ struct DevFactor {
     DevArray<T> sinv;          // dense S^{-1} (DENSE mode)
     DevArray<int32_t> prow, a2rows;  // rows of A1 (by position) and of A2: Algorithm 3's input split
     DevArray<T> vn[6], vm[4];  // work vectors
-    void upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h, cudaStream_t s);
+    // sliced: also the sliced layout of L2 and L2^T
+    void upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h, cudaStream_t s,
+                bool sliced = false);
     void clear() {
         for (int w = 0; w < 4; ++w) {
             tri[w].ptr.release(); tri[w].idx.release(); tri[w].val.release();
@@ -206,6 +208,7 @@ struct rlsq_problem_s {
     // Dense rows (sparse-dense problems): rows with many nonzeros sit at the end
     // of the internal row order (empty in dA) and are kept row-major in Ad.
     int64_t ms = 0, md = 0;          // sparse and dense row counts (ms + md = m)
+    int64_t layout_threshold = 0;    // the dense-row threshold A's device layout was built with
     std::vector<int32_t> row_perm;   // internal row i holds user row row_perm[i] (empty: identity)
     rlsq::DevArray<int32_t> row_perm_d;
     rlsq::DevArray<double> Ad;       // md x n

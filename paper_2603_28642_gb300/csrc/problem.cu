@@ -217,7 +217,7 @@ static void upload_binned(DevFactor<T>& D, int w, const IlupResult& F, const Mer
 
 template <typename T>
 void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const std::vector<double>& sinv_h,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool sliced) {
     for (int w = 0; w < 4; ++w) {
         upload_binned<T>(*this, w, F, merged[w], s);
         // rows permuted into solve order so each level is contiguous
@@ -271,8 +271,8 @@ void DevFactor<T>::upload(const IlupResult& F, const MergedTri* merged, const st
             upload_vec(diag[w], dl, s);
         }
     }
-    L2.upload(F.L2, s, true);
-    L2t.upload(F.L2t, s, true);
+    L2.upload(F.L2, s, sliced);
+    L2t.upload(F.L2t, s, sliced);
     upload_vec(d, F.d, s);
     prow.upload(F.prow.data(), F.prow.size(), s);
     if (!F.a2rows.empty()) a2rows.upload(F.a2rows.data(), F.a2rows.size(), s);
@@ -1060,7 +1060,9 @@ static int64_t auto_dense_threshold(const HostCSR& A) {
     return std::max<int64_t>(64, 16 * std::max<int64_t>(med, 1));
 }
 
-static void layout_A(rlsq_problem_s* P, int64_t threshold) {
+// sliced: also the sliced layout of A and A^T (the products may run on it)
+static void layout_A(rlsq_problem_s* P, int64_t threshold, bool sliced = false) {
+    P->layout_threshold = threshold;
     const HostCSR& A = P->A;
     const int64_t m = A.rows, n = A.cols;
     std::vector<int32_t> dense;
@@ -1081,8 +1083,8 @@ static void layout_A(rlsq_problem_s* P, int64_t threshold) {
         P->row_perm.clear();
         P->row_perm_d.release();
         P->Ad.release();
-        P->dA.upload(A, st, true);
-        P->dAt.upload(transpose(A, ilup_threads(0, A.rows, A.cols)), st, true);
+        P->dA.upload(A, st, sliced);
+        P->dAt.upload(transpose(A, ilup_threads(0, A.rows, A.cols)), st, sliced);
         return;
     }
     std::vector<char> is_dense(static_cast<size_t>(m), 0);
@@ -1104,8 +1106,8 @@ static void layout_A(rlsq_problem_s* P, int64_t threshold) {
         S.ptr[i + 1] = static_cast<int64_t>(S.idx.size());
     }
     for (int64_t i = P->ms; i < m; ++i) S.ptr[i + 1] = S.ptr[i];
-    P->dA.upload(S, st, true);
-    P->dAt.upload(transpose(S, ilup_threads(0, S.rows, S.cols)), st, true);
+    P->dA.upload(S, st, sliced);
+    P->dAt.upload(transpose(S, ilup_threads(0, S.rows, S.cols)), st, sliced);
     std::vector<double> ad(static_cast<size_t>(P->md * n), 0.0);
     for (int64_t q = 0; q < P->md; ++q) {
         const int32_t r = dense[q];
@@ -1514,8 +1516,10 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         }
         h->f64.clear();
         h->f32.clear();
-        if (opts.precision == RLSQ_PREC_FP32) h->f32.upload(*F, h->merged.data(), sinv, st);
-        else h->f64.upload(*F, h->merged.data(), sinv, st);
+        // the sliced copies of the products' matrices only where they may run
+        const bool want_sliced = opts.sliced == 1 || (opts.sliced < 0 && opts.autotune != 0);
+        if (opts.precision == RLSQ_PREC_FP32) h->f32.upload(*F, h->merged.data(), sinv, st, want_sliced);
+        else h->f64.upload(*F, h->merged.data(), sinv, st, want_sliced);
         if (sinv_on_device) {
             DevArray<double> sd;
             device_schur_inverse(*F, sd, st, h->num_sms);
@@ -1533,8 +1537,10 @@ int rlsq_factor(rlsq_problem h, const rlsq_factor_opts* o) {
         }
         if (opts.dense_row_min != 0) {
             // an explicit dense-row threshold (< 0: none) replaces the automatic one
-            layout_A(h, opts.dense_row_min);
+            layout_A(h, opts.dense_row_min, want_sliced);
             h->anorm = power_norm(h, 50);
+        } else if (want_sliced && (h->dA.snpos == 0 || h->dAt.snpos == 0)) {
+            layout_A(h, h->layout_threshold, true);
         }
         h->F = std::move(F);
         h->opts = opts;
